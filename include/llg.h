@@ -1,0 +1,165 @@
+/*
+ * llg.h -- C ABI of the GB300 level-set / adjoint LLG solver.
+ *
+ * The library integrates the Landau-Lifshitz-Gilbert equation (Eq. 11 of
+ * arXiv:2411.19109, Methods) on a nodal finite-difference grid for a batch of
+ * independent instances, evaluates an objective J per instance and returns
+ * dJ/dPhi, the gradient with respect to the level-set function Phi (Eq. 1)
+ * through the material map psi = 1/(1 + exp(-a Phi)) (Eq. 4), by the discrete
+ * adjoint of the time stepper (the adjoint-state system, Eq. 6, and the
+ * parameter integral, Eq. 7, taken through the RK4 stages).  levelset_step
+ * applies the gradient-descent update (Eq. 5) on Phi and renormalises Phi to
+ * [-1, 1] (Results, "Level-set method").
+ *
+ * Discretisation (shared with the FP64 oracle used by the tests):
+ *   node i owns a cuboid dx*dy*dz; Ms_i = Ms psi_i, A_i = A psi_i;
+ *   B_ex,i = (2A/Ms) sum_j w_ij (m_j - m_i)/h^2, w_ij = 2 psi_j/(psi_i + psi_j)
+ *            (harmonic-mean edge coupling, free boundaries);
+ *   B_an   = (2 Ku/Ms)(m.u)u;  B_z = B_bias + b_rf sin(2 pi f t) e_rf on src;
+ *   B_d    = -mu0 N * (Ms psi m), N the cell-averaged (Newell) tensor,
+ *            evaluated by zero-padded FFT convolution;
+ *   dm/dt  = -gamma/(1+alpha_i^2) [m x B + alpha_i m x (m x B)];
+ *   classic RK4 at fixed dt, t_n = n dt, no renormalisation of m.
+ *
+ * Memory and ownership.  Every *_dev pointer is device memory owned by the
+ * caller; instances are packed back to back in the order given to
+ * llg_create.  Per instance i with nodes n_i = nx*ny*nz:
+ *   phi, grad  [n_i]          layout [z][y][x], x fastest
+ *   m0, mT     [3][n_i]       layout [component][z][y][x]
+ *   mask       [n_i] uint8    1 = design region
+ * Element type: float for LLG_FP32, double for LLG_FP64 (llg_options).
+ * The library owns its scratch (spectra, tensors, checkpoints, stage
+ * records); it allocates them in llg_create and frees them in llg_destroy.
+ *
+ * Streams.  All work runs on the stream given to llg_create.  llg_forward
+ * synchronises that stream before it returns (it copies J to the host);
+ * llg_adjoint and levelset_step return as soon as the work is queued.
+ *
+ * Errors.  Functions return llg_status; no exception crosses the ABI.  On a
+ * non-OK status llg_last_error(ctx) holds a one-line description.  A device
+ * wait that exceeds its bound returns LLG_ETIMEOUT; a non-finite J returns
+ * LLG_ENONFINITE (the outputs are still written).
+ */
+#ifndef LLG_H
+#define LLG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LLG_OK = 0,
+  LLG_EINVAL = 1,     /* invalid argument or unsupported problem size        */
+  LLG_ENOMEM = 2,     /* device allocation failed                            */
+  LLG_ECUDA = 3,      /* a CUDA runtime call failed                          */
+  LLG_ETIMEOUT = 4,   /* a bounded device wait ran out                       */
+  LLG_ENONFINITE = 5, /* J is NaN or Inf                                     */
+  LLG_ESTATE = 6      /* call order violated (adjoint without forward, ...)  */
+} llg_status;
+
+enum { LLG_J_PORT = 0, LLG_J_ENERGY_AREA = 1 };
+enum { LLG_FP32 = 0, LLG_FP64 = 1 };
+enum { LLG_CKPT_STORE_ALL = 0, LLG_CKPT_PERIODIC = 1 };
+
+/* One instance.  SI units (m, A/m, J/m, J/m^3, T, Hz, s). */
+typedef struct {
+  int nx, ny, nz;            /* nodes; nx % 4 == 0, nz == 1 (2D film)          */
+  double dx, dy, dz;         /* node spacing = cell size                       */
+  double Ms, A, Ku;          /* saturation magnetisation, exchange, anisotropy */
+  double ku[3];              /* anisotropy axis (normalised by the library)    */
+  double alpha, alpha_edge;  /* Gilbert damping; value at an absorbing edge    */
+  int absorb_nodes;          /* ramp width W (0 = none): alpha_i = alpha +
+                                (alpha_edge - alpha) max(0, (W - d_i)/W)       */
+  int absorb_x, absorb_y;    /* which pairs of edges absorb                   */
+  double B_bias[3];          /* static field                                   */
+  double b_rf, f_rf;         /* RF amplitude and frequency                     */
+  double rf_dir[3];          /* RF direction                                   */
+  int src[4];                /* RF source box x0,x1,y0,y1 (half open)          */
+  double dt;                 /* time step                                      */
+  long long nsteps;          /* number of RK4 steps N                          */
+  double sigmoid_a;          /* a of Eq. 4                                     */
+  int objective;             /* LLG_J_PORT or LLG_J_ENERGY_AREA                */
+  int comp, power;           /* LLG_J_PORT: sampled component, exponent 1 or 2 */
+  int boxes[2][4];           /* LLG_J_PORT: boxes x0,x1,y0,y1                   */
+  double weights[2];         /* LLG_J_PORT: J = sum_{n>=n_from} sum_b w_b
+                                mean_{box b}(m_comp,n ^ power)                 */
+  long long n_from;          /* first step index in the running sum            */
+  double area_target;        /* LLG_J_ENERGY_AREA: J = (E_d + E_ex)(m_N) /
+                                (mu0 Ms^2/2 * V_domain) + penalty_w *
+                                (mean(psi) - area_target)^2  (Eq. 9 size term) */
+  double penalty_w;
+} llg_problem;
+
+typedef struct {
+  int precision;   /* LLG_FP32 or LLG_FP64                                     */
+  int ckpt;        /* LLG_CKPT_PERIODIC (O(sqrt N) memory) or LLG_CKPT_STORE_ALL */
+  int seg_len;     /* periodic segment length K; 0 = ceil(sqrt(max nsteps))     */
+  int use_graph;   /* 1 = replay captured CUDA graphs of whole segments         */
+  int rows_per_cta;/* tile rows of the row kernels; 0 = autotune                */
+  int cols_per_cta;/* tile columns of the column kernel; 0 = autotune           */
+} llg_options;
+
+typedef struct llg_ctx llg_ctx;
+
+/* Validate `n_inst` problems, build the per-shape demag spectra (FP64 on the
+ * device, stored in the working precision), pick tile shapes and allocate all
+ * scratch.  `cuda_stream` is a cudaStream_t (NULL = default stream).
+ * Every instance must have the same nsteps, n_from and dt.
+ * Returns LLG_EINVAL for unsupported sizes (nx % 4 != 0, nz != 1, nx > 2048,
+ * ny > 512), LLG_ENOMEM if the scratch does not fit. */
+llg_status llg_create(const llg_problem* inst, int n_inst, const llg_options* opt,
+                      void* cuda_stream, llg_ctx** out);
+
+/* Forward pass: psi from phi, RK4 for nsteps from m0, J per instance.
+ * J_host: [n_inst] doubles (required).  mT_dev: final m (nullable).
+ * Keeps the checkpoints that llg_adjoint needs. */
+llg_status llg_forward(llg_ctx* ctx, const void* phi_dev, const void* m0_dev,
+                       double* J_host, void* mT_dev);
+
+/* Reverse sweep after llg_forward on the same inputs: writes dJ/dPhi
+ * (all nodes, unmasked) to dJdphi_dev and, if non-NULL, dJ/dm0 to dJdm0_dev.
+ * LLG_ESTATE if no forward pass precedes it. */
+llg_status llg_adjoint(llg_ctx* ctx, void* dJdphi_dev, void* dJdm0_dev);
+
+/* Eq. 5 on the design mask, Phi <- Phi - lr grad, then Phi <- Phi / max|Phi|
+ * over the mask, per instance (an instance whose masked max is 0 is left
+ * unscaled).  Nodes outside the mask are not touched. */
+llg_status levelset_step(llg_ctx* ctx, void* phi_dev, const void* grad_dev,
+                         const unsigned char* mask_dev, double lr);
+
+/* Effective field B (tesla) of the magnetisation m_dev at time t for all
+ * instances, psi taken from phi_dev; demag_only != 0 returns B_d alone.
+ * Layout of m_dev and B_dev as m0.  Diagnostic entry point for parity tests. */
+llg_status llg_field(llg_ctx* ctx, const void* phi_dev, const void* m_dev, double t,
+                     int demag_only, void* B_dev);
+
+/* Bytes the context holds on the device, and the device time (ms) of the last
+ * llg_forward / llg_adjoint call. */
+llg_status llg_query(llg_ctx* ctx, size_t* device_bytes, double* last_ms);
+
+/* Number of kernels the last llg_forward + llg_adjoint pair launched. */
+long long llg_launch_count(llg_ctx* ctx);
+
+const char* llg_last_error(llg_ctx* ctx);
+void llg_destroy(llg_ctx* ctx);
+
+/* Host-only: the checkpoint action list the library executes.  Writes up to
+ * max_actions triples (op, a, b) to `actions` (forward actions first, then
+ * reverse), sets *n_forward to the number of forward actions and returns the
+ * total count (or -1 on bad arguments).  ops: 0 SNAP (n, slot), 1 ADVANCE
+ * (n0, n1), 2 RESTORE (slot, n), 3 RECORD (n0, n1), 4 REVERSE (n1, n0). */
+long long llg_schedule(long long nsteps, int ckpt, int seg_len, long long* actions,
+                       long long max_actions, long long* n_forward);
+
+/* Host-only: padded FFT extents the library uses for a grid (Px, Py). */
+int llg_padded_extents(int nx, int ny, int* Px, int* Py);
+
+int llg_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LLG_H */

@@ -17,7 +17,7 @@ Periodic schedule with segment length K (K = ceil(sqrt(N)) by default):
 checkpoints at n = 0, K, 2K, ...; the forward records the last segment
 directly; the reverse restores, re-records and reverses each earlier segment.
 Memory: ceil(N/K) checkpoints plus K recorded steps, O(sqrt N) at the default.
-Store-all: record all N steps in the forward, reverse them in one go.
+Store-all is the periodic schedule with K = 1: all N states are kept.
 """
 from __future__ import annotations
 
@@ -59,9 +59,9 @@ def periodic(nsteps: int, seg: int = 0):
 
 
 def store_all(nsteps: int):
-    if nsteps <= 0:
-        return [], []
-    return [(RECORD, 0, nsteps)], [(REVERSE, nsteps, 0)]
+    """Every state m_n is kept (K = 1); each reverse step re-records its own
+    stages from m_n."""
+    return periodic(nsteps, 1)
 
 
 def peak_states(fwd, rev):

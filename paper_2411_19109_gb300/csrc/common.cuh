@@ -1,0 +1,73 @@
+// Common device types of the LLG solver: complex arithmetic, the per-instance
+// descriptor and the work-tile tables shared by every kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace llg {
+
+constexpr double kMu0 = 1.2566370614359173e-06;     // 4 pi 1e-7
+constexpr double kGamma = 1.76085963023e11;         // rad s^-1 T^-1
+constexpr int kTwiddleN = 4096;                      // W_4096^k table length
+constexpr int kMaxLx = 2048;                         // complex row FFT length
+constexpr int kMaxPy = 1024;                         // column FFT length
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+template <typename T> using cplx = typename Cplx<T>::type;
+
+template <typename C> __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
+  C r; r.x = a; r.y = b; return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <typename C> __device__ __forceinline__ C mul_mi(C a) { return mk<C>(a.y, -a.x); }
+template <typename C> __device__ __forceinline__ C mul_pi(C a) { return mk<C>(-a.y, a.x); }
+
+// Per-instance descriptor (device copy).  Offsets are in elements of the
+// pooled arrays; every node offset is a multiple of 4.
+struct DevInst {
+  int nx, ny, nz;
+  int Lx, Py;            // complex row FFT length (Px/2) and column FFT length
+  int log2Lx, log2Py;
+  int shape;             // index of the demag spectrum table
+  long long nodes;       // nx*ny*nz
+  long long node_off;    // offset into node arrays (per component block: 3*nodes)
+  long long spec_off;    // offset into the spectrum pool, complex elements
+  long long tens_off;    // offset into the tensor pool, real elements
+  long long slot_off;    // offset into the per-step objective slots (nsteps+1)
+  double Ms;
+  double cex_x, cex_y, cex_z;   // 2A/(Ms h^2)
+  double kan;                   // 2Ku/Ms
+  double ku[3];
+  double alpha, alpha_edge;
+  int absorb_nodes, absorb_x, absorb_y;
+  int src[4];
+  double B_bias[3];
+  double b_rf, f_rf;
+  double rf_dir[3];
+  double sigmoid_a;
+  int objective, comp, power;
+  int boxes[2][4];
+  double wbox[2];               // w_b / |box b|
+  double V;                     // cell volume
+  double ihx2, ihy2;            // 1/dx^2, 1/dy^2
+  double escale;                // 1/(K_d V_domain)
+  double A;                     // exchange constant
+  double area_target, penalty_w;
+};
+
+// Row tile: rows y0 .. y0+nrows-1 of instance `inst`.
+struct RowTile { int inst, y0, nrows, pad; };
+// Column tile: complex columns kx0 .. kx0+ncols-1 of instance `inst`.
+struct ColTile { int inst, kx0, ncols, pad; };
+
+}  // namespace llg

@@ -1,0 +1,114 @@
+// Kernel argument blocks and launch helpers shared by kernels.cu and the
+// host runtime.
+#pragma once
+
+#include "common.cuh"
+
+namespace llg {
+
+// Row-kernel modes.
+enum RowMode : int {
+  ROW_FFT_ONLY = 0,   // spectrum of M = Ms psi Yin (first stage of a step)
+  ROW_STAGE = 1,      // demag inverse + field + RK4 stage + next-stage spectrum
+  ROW_FIELD = 2,      // effective field (or demag only) of Yin -> Bout
+  ROW_TERMINAL = 3,   // energies / lambda_N / explicit dJ/dpsi at m_N = Yin
+};
+
+template <typename T>
+struct RowArgs {
+  const DevInst* inst;
+  const RowTile* tiles;
+  cplx<T>* spec;
+  const cplx<T>* tw;
+  const T* psi;
+  const T* Yin;       // stage input, read with halo
+  const T* m;         // m_n, pointwise
+  T* acc;             // RK accumulator
+  T* Yout;            // next stage input (stages 1..3)
+  T* mout;            // m_{n+1} (stage 4)
+  T* Bout;            // recorded B_s (nullable) / field output (ROW_FIELD)
+  T* ckpt;            // copy of m_{n+1} (stage 4, nullable)
+  double* slots;      // objective slots (nullable: do not accumulate)
+  const long long* step_base;
+  int local_step;
+  int stage;          // 1..4
+  int rows_max;       // smem sizing: rows per tile
+  int demag_only;     // ROW_FIELD
+  double t_field;     // ROW_FIELD time
+  double dt;
+  long long n_from;
+  // ROW_TERMINAL outputs
+  T* lam;             // lambda_N
+  T* psib;            // dJ/dpsi accumulator (sum)
+  T* psic;            //                     (compensation)
+  double* jterm;      // per-instance terminal J
+  const double* psisum; // per-instance sum of psi
+  long long nsteps;
+};
+
+template <typename T>
+struct ColArgs {
+  const DevInst* inst;
+  const ColTile* tiles;
+  cplx<T>* spec;
+  const cplx<T>* tw;
+  const T* tens;      // packed spectrum tables
+  int cols_max;
+};
+
+template <typename T>
+struct AdjArgs {
+  const DevInst* inst;
+  const RowTile* tiles;
+  cplx<T>* spec;
+  const cplx<T>* tw;
+  const T* psi;
+  const T* Ys;        // Y_s of this stage (halo)
+  const T* Bbar;      // Bbar_s (halo)
+  T* gpart;           // in: local part of g_s; out: local part of g_{s-1}
+  T* lam;             // lambda_{n+1} (stage 1 writes lambda_n)
+  T* G;               // running sum of g over the stages of the step
+  T* psib;
+  T* psic;
+  const T* Yprev;     // Y and B of the next stage to be reversed
+  const T* Bprev;
+  T* BbarOut;
+  const long long* step_base;
+  int local_step;
+  int stage;          // 4..1
+  int seed_only;      // 1: only form u_4, Bbar_4 of step n from lambda
+  int seed_next;      // stage 1: also seed step n-1 (Yprev/Bprev of its stage 4)
+  int rows_max;
+  double dt;
+  long long n_from;
+};
+
+template <typename T>
+void launch_rows(const RowArgs<T>& a, int mode, int ntiles, size_t smem, cudaStream_t st);
+template <typename T>
+void launch_cols(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+template <typename T>
+void launch_adj(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+template <typename T>
+void set_smem_limits(size_t smem);
+template <typename T>
+void launch_material_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* phi, T* psi,
+                           T* dpsi, double* psisum, cudaStream_t st);
+template <typename T>
+void launch_grad_finish_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* dpsi,
+                              const T* psib, const T* psic, T* out, cudaStream_t st);
+template <typename T>
+void launch_levelset_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, T* phi, const T* grad,
+                           const unsigned char* mask, double lr, unsigned int* maxbits, cudaStream_t st);
+void launch_set_step(long long* step_base, long long v, cudaStream_t st);
+void launch_reduce_slots(const DevInst* inst, int n_inst, const double* slots, long long nslots,
+                         const double* jterm, const double* psisum, double* J, cudaStream_t st);
+int rows_threads();
+int cols_threads();
+int adj_threads();
+
+template <typename T>
+cudaError_t build_tensor_spectrum(T* table, double2* G, int nx, int ny, int Px, int Py, double dx,
+                                  double dy, double dz, const double2* tw, cudaStream_t st);
+
+}  // namespace llg

@@ -1,0 +1,727 @@
+// Host runtime and C ABI of the LLG solver (declared in include/llg.h).
+//
+// A context owns, for a batch of instances packed back to back:
+//   * the instance descriptors and the row / column work-tile tables that
+//     let every kernel launch cover the whole batch (uneven grid sizes);
+//   * one demag spectrum table per distinct grid shape, built in FP64;
+//   * the forward state (m, two stage buffers, RK accumulator), the demag
+//     spectrum pool, the periodic checkpoints and one recorded segment
+//     (stage inputs Y_s and fields B_s of up to K steps), and the adjoint
+//     state (lambda, stage sums, Bbar ping-pong, Kahan pair for dJ/dpsi);
+//   * the checkpoint action list it executes.
+// Checkpointing follows the paper's memory argument (Introduction and the
+// adjoint-state section): only every K-th state is kept and each segment is
+// recomputed once during the reverse sweep, O(sqrt N) states at the default K.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "llg.h"
+
+using namespace llg;
+
+namespace {
+
+enum Op { SNAP = 0, ADVANCE = 1, RESTORE = 2, RECORD = 3, REVERSE = 4 };
+struct Action { long long op, a, b; };
+
+long long isqrt_ceil(long long n) {
+  if (n <= 0) return 1;
+  long long k = (long long)std::sqrt((double)n);
+  while (k * k > n) --k;
+  while (k * k < n) ++k;
+  return k;
+}
+
+// Periodic schedule: snapshots at n = 0, K, 2K, ..; the forward records the
+// last segment; the reverse restores, re-records and reverses each earlier
+// segment.  Store-all is the same schedule with K = 1 (every state kept).
+void make_schedule(long long N, int ckpt, int seg_len, std::vector<Action>& fwd, std::vector<Action>& rev) {
+  fwd.clear();
+  rev.clear();
+  if (N <= 0) return;
+  long long K = (ckpt == LLG_CKPT_STORE_ALL) ? 1 : (seg_len > 0 ? seg_len : isqrt_ceil(N));
+  const long long nseg = (N + K - 1) / K;
+  for (long long c = 0; c < nseg; ++c) {
+    const long long a = c * K, b = std::min(N, (c + 1) * K);
+    if (c + 1 < nseg) {
+      fwd.push_back({SNAP, a, c});
+      fwd.push_back({ADVANCE, a, b});
+    } else {
+      fwd.push_back({RECORD, a, b});
+    }
+  }
+  for (long long c = nseg - 1; c >= 0; --c) {
+    const long long a = c * K, b = std::min(N, (c + 1) * K);
+    if (c + 1 < nseg) {
+      rev.push_back({RESTORE, c, a});
+      rev.push_back({RECORD, a, b});
+    }
+    rev.push_back({REVERSE, b, a});
+  }
+}
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+}  // namespace
+
+struct llg_ctx {
+  std::string err;
+  virtual ~llg_ctx() {}
+  virtual llg_status forward(const void* phi, const void* m0, double* J, void* mT) = 0;
+  virtual llg_status adjoint(void* dphi, void* dm0) = 0;
+  virtual llg_status levelset(void* phi, const void* grad, const unsigned char* mask, double lr) = 0;
+  virtual llg_status field(const void* phi, const void* m, double t, int demag_only, void* B) = 0;
+  virtual size_t device_bytes() const = 0;
+  virtual double last_ms() const = 0;
+  virtual long long launches() const = 0;
+};
+
+template <typename T>
+struct Engine final : llg_ctx {
+  using C = cplx<T>;
+  std::vector<llg_problem> P;
+  int n = 0;
+  llg_options opt{};
+  cudaStream_t st = nullptr;
+  long long N = 0, n_from = 0;
+  double dt = 0;
+
+  std::vector<DevInst> H;
+  std::vector<RowTile> rt;
+  std::vector<ColTile> ct;
+  DevInst* dI = nullptr;
+  RowTile* dRT = nullptr;
+  ColTile* dCT = nullptr;
+  int R = 2, TX = 8;
+  size_t smem = 0;
+  long long total_nodes = 0, total_spec = 0, total_tens = 0;
+  long long K = 1, nckpt = 0, rec_steps = 0;
+  std::vector<Action> fwd, rev;
+
+  T *psi = nullptr, *dpsi = nullptr, *m = nullptr, *Ya = nullptr, *Yb = nullptr, *acc = nullptr;
+  T *tens = nullptr, *recY = nullptr, *recB = nullptr, *ckpt = nullptr;
+  T *lam = nullptr, *G = nullptr, *gpart = nullptr, *bb[2] = {nullptr, nullptr};
+  T *psib = nullptr, *psic = nullptr;
+  C *spec = nullptr, *tw = nullptr;
+  double2* tw64 = nullptr;
+  double *slots = nullptr, *jterm = nullptr, *psisum = nullptr, *Jd = nullptr;
+  long long* step_base = nullptr;
+  unsigned int* maxbits = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  double ms = 0.0;
+  long long nlaunch = 0;
+  bool have_fwd = false;
+  const T* mN_ptr = nullptr;
+
+  ~Engine() override {
+    if (st) cudaStreamSynchronize(st);
+    for (void* p : allocs) cudaFree(p);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+
+  size_t device_bytes() const override { return bytes; }
+  double last_ms() const override { return ms; }
+  long long launches() const override { return nlaunch; }
+
+  llg_status fail(llg_status s, const std::string& msg) {
+    err = msg;
+    return s;
+  }
+  llg_status cuda_fail(cudaError_t e, const char* where) {
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return LLG_ECUDA;
+  }
+
+  template <typename P_>
+  bool alloc(P_** p, size_t count) {
+    void* q = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&q, count * sizeof(P_)) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    allocs.push_back(q);
+    bytes += count * sizeof(P_);
+    *p = static_cast<P_*>(q);
+    return true;
+  }
+
+  size_t slot() const { return (size_t)3 * total_nodes; }
+  T* recY_slot(long long i) { return recY + (size_t)i * slot(); }
+  T* recB_slot(long long i) { return recB + (size_t)i * slot(); }
+
+  // ---------------------------------------------------------------- create
+  llg_status create(const llg_problem* probs, int n_inst, const llg_options* o, cudaStream_t stream) {
+    n = n_inst;
+    st = stream;
+    opt = *o;
+    P.assign(probs, probs + n_inst);
+    N = P[0].nsteps;
+    n_from = P[0].n_from;
+    dt = P[0].dt;
+    int Lx_max = 0, Py_max = 0;
+    for (int i = 0; i < n; ++i) {
+      const llg_problem& p = P[i];
+      char buf[256];
+      if (p.nx < 4 || p.nx % 4 != 0 || p.nx > kMaxLx) {
+        snprintf(buf, sizeof buf, "instance %d: nx=%d must be a multiple of 4 in [4, %d]", i, p.nx, kMaxLx);
+        return fail(LLG_EINVAL, buf);
+      }
+      if (p.ny < 1 || p.ny > kMaxPy / 2) {
+        snprintf(buf, sizeof buf, "instance %d: ny=%d must be in [1, %d]", i, p.ny, kMaxPy / 2);
+        return fail(LLG_EINVAL, buf);
+      }
+      if (p.nz != 1) return fail(LLG_EINVAL, "only single-layer films (nz == 1) are supported");
+      if (!(p.dx > 0 && p.dy > 0 && p.dz > 0 && p.Ms > 0 && p.dt > 0 && p.A >= 0))
+        return fail(LLG_EINVAL, "dx, dy, dz, Ms, dt must be > 0 and A >= 0");
+      if (p.nsteps < 0 || p.nsteps != N || p.n_from != n_from || p.dt != dt)
+        return fail(LLG_EINVAL, "all instances must share nsteps >= 0, n_from and dt");
+      if (p.objective != LLG_J_PORT && p.objective != LLG_J_ENERGY_AREA)
+        return fail(LLG_EINVAL, "unknown objective");
+      if (p.objective == LLG_J_PORT && (p.comp < 0 || p.comp > 2 || (p.power != 1 && p.power != 2)))
+        return fail(LLG_EINVAL, "port objective needs comp in 0..2 and power 1 or 2");
+      if (p.absorb_nodes < 0) return fail(LLG_EINVAL, "absorb_nodes must be >= 0");
+      const int Px = std::max(8, next_pow2(2 * p.nx));
+      const int Py = std::max(2, next_pow2(2 * p.ny));
+      Lx_max = std::max(Lx_max, Px / 2);
+      Py_max = std::max(Py_max, Py);
+    }
+    if (opt.precision != LLG_FP32 && opt.precision != LLG_FP64)
+      return fail(LLG_EINVAL, "precision must be LLG_FP32 or LLG_FP64");
+    if (opt.ckpt != LLG_CKPT_PERIODIC && opt.ckpt != LLG_CKPT_STORE_ALL)
+      return fail(LLG_EINVAL, "ckpt must be LLG_CKPT_PERIODIC or LLG_CKPT_STORE_ALL");
+
+    // tile shapes: rows per row tile and complex columns per column tile,
+    // bounded by the shared memory of two ping-pong FFT buffers
+    const size_t cap = 200 * 1024;
+    R = opt.rows_per_cta > 0 ? opt.rows_per_cta : 2;
+    while (R > 1 && (size_t)2 * 3 * R * Lx_max * sizeof(C) > cap) --R;
+    if ((size_t)2 * 3 * R * Lx_max * sizeof(C) > cap) return fail(LLG_EINVAL, "row tile does not fit");
+    TX = opt.cols_per_cta > 0 ? opt.cols_per_cta : 8;
+    TX = next_pow2(TX);
+    while (TX > 1 && (size_t)2 * 3 * TX * (Py_max + 1) * sizeof(C) > cap) TX >>= 1;
+    if ((size_t)2 * 3 * TX * (Py_max + 1) * sizeof(C) > cap) return fail(LLG_EINVAL, "column tile does not fit");
+    smem = std::max((size_t)2 * 3 * R * Lx_max * sizeof(C), (size_t)2 * 3 * TX * (Py_max + 1) * sizeof(C));
+
+    // descriptors, shapes, tiles
+    struct Shape { int nx, ny; double dx, dy, dz; long long off; int Px, Py; };
+    std::vector<Shape> shapes;
+    H.resize(n);
+    long long node_off = 0, spec_off = 0, tens_off = 0;
+    for (int i = 0; i < n; ++i) {
+      const llg_problem& p = P[i];
+      DevInst d;
+      std::memset(&d, 0, sizeof d);
+      d.nx = p.nx; d.ny = p.ny; d.nz = 1;
+      const int Px = std::max(8, next_pow2(2 * p.nx));
+      d.Lx = Px / 2;
+      d.Py = std::max(2, next_pow2(2 * p.ny));
+      d.log2Lx = ilog2(d.Lx);
+      d.log2Py = ilog2(d.Py);
+      int sid = -1;
+      for (size_t s = 0; s < shapes.size(); ++s)
+        if (shapes[s].nx == p.nx && shapes[s].ny == p.ny && shapes[s].dx == p.dx && shapes[s].dy == p.dy &&
+            shapes[s].dz == p.dz)
+          sid = (int)s;
+      if (sid < 0) {
+        shapes.push_back({p.nx, p.ny, p.dx, p.dy, p.dz, tens_off, Px, d.Py});
+        tens_off += (long long)(Px / 2 + 1) * (d.Py / 2 + 1) * 4;
+        sid = (int)shapes.size() - 1;
+      }
+      d.shape = sid;
+      d.tens_off = shapes[sid].off;
+      d.nodes = (long long)p.nx * p.ny;
+      d.node_off = node_off;
+      node_off += d.nodes;
+      d.spec_off = spec_off;
+      spec_off += (long long)p.ny * 3 * d.Lx;
+      d.slot_off = (long long)i * (N + 1);
+      d.Ms = p.Ms;
+      d.cex_x = 2.0 * p.A / (p.Ms * p.dx * p.dx);
+      d.cex_y = 2.0 * p.A / (p.Ms * p.dy * p.dy);
+      d.cex_z = 2.0 * p.A / (p.Ms * p.dz * p.dz);
+      d.kan = 2.0 * p.Ku / p.Ms;
+      const double kn = std::sqrt(p.ku[0] * p.ku[0] + p.ku[1] * p.ku[1] + p.ku[2] * p.ku[2]);
+      for (int c = 0; c < 3; ++c) d.ku[c] = kn > 0 ? p.ku[c] / kn : 0.0;
+      d.alpha = p.alpha;
+      d.alpha_edge = p.alpha_edge;
+      d.absorb_nodes = p.absorb_nodes;
+      d.absorb_x = p.absorb_x;
+      d.absorb_y = p.absorb_y;
+      for (int c = 0; c < 4; ++c) d.src[c] = p.src[c];
+      for (int c = 0; c < 3; ++c) {
+        d.B_bias[c] = p.B_bias[c];
+        d.rf_dir[c] = p.rf_dir[c];
+      }
+      d.b_rf = p.b_rf;
+      d.f_rf = p.f_rf;
+      d.sigmoid_a = p.sigmoid_a;
+      d.objective = p.objective;
+      d.comp = p.comp;
+      d.power = p.power;
+      for (int b = 0; b < 2; ++b) {
+        int x0 = std::max(0, p.boxes[b][0]), x1 = std::min(p.nx, p.boxes[b][1]);
+        int y0 = std::max(0, p.boxes[b][2]), y1 = std::min(p.ny, p.boxes[b][3]);
+        if (x1 < x0) x1 = x0;
+        if (y1 < y0) y1 = y0;
+        d.boxes[b][0] = x0; d.boxes[b][1] = x1; d.boxes[b][2] = y0; d.boxes[b][3] = y1;
+        const long long cnt = (long long)(x1 - x0) * (y1 - y0);
+        d.wbox[b] = cnt > 0 ? p.weights[b] / (double)cnt : 0.0;
+      }
+      d.V = p.dx * p.dy * p.dz;
+      d.ihx2 = 1.0 / (p.dx * p.dx);
+      d.ihy2 = 1.0 / (p.dy * p.dy);
+      d.escale = 1.0 / (0.5 * kMu0 * p.Ms * p.Ms * d.V * (double)d.nodes);
+      d.A = p.A;
+      d.area_target = p.area_target;
+      d.penalty_w = p.penalty_w;
+      H[i] = d;
+      for (int y0 = 0; y0 < p.ny; y0 += R) rt.push_back({i, y0, std::min(R, p.ny - y0), 0});
+      const int tx = std::min(TX, d.Lx);
+      for (int k0 = 0; k0 < d.Lx; k0 += tx) ct.push_back({i, k0, tx, 0});
+    }
+    total_nodes = node_off;
+    total_spec = spec_off;
+    total_tens = tens_off;
+
+    make_schedule(N, opt.ckpt, opt.seg_len, fwd, rev);
+    K = (opt.ckpt == LLG_CKPT_STORE_ALL) ? 1 : (opt.seg_len > 0 ? opt.seg_len : isqrt_ceil(N));
+    K = std::max(1LL, std::min(K, std::max(N, 1LL)));
+    nckpt = 0;
+    rec_steps = 0;
+    for (const Action& a : fwd)
+      if (a.op == SNAP) nckpt = std::max(nckpt, a.b + 1);
+    for (const Action& a : fwd)
+      if (a.op == RECORD) rec_steps = std::max(rec_steps, a.b - a.a);
+    for (const Action& a : rev)
+      if (a.op == RECORD) rec_steps = std::max(rec_steps, a.b - a.a);
+
+    const size_t S = slot();
+    bool ok = alloc(&dI, n) && alloc(&dRT, rt.size()) && alloc(&dCT, ct.size()) && alloc(&psi, total_nodes) &&
+              alloc(&dpsi, total_nodes) && alloc(&m, S) && alloc(&Ya, S) && alloc(&Yb, S) && alloc(&acc, S) &&
+              alloc(&tens, total_tens) && alloc(&spec, total_spec) && alloc(&tw, kTwiddleN) &&
+              alloc(&tw64, kTwiddleN) && alloc(&recY, S * (4 * rec_steps + 1)) &&
+              alloc(&recB, S * std::max(1LL, 4 * rec_steps)) && alloc(&ckpt, S * std::max(1LL, nckpt)) &&
+              alloc(&lam, S) && alloc(&G, S) && alloc(&gpart, S) && alloc(&bb[0], S) && alloc(&bb[1], S) &&
+              alloc(&psib, total_nodes) && alloc(&psic, total_nodes) && alloc(&slots, (size_t)n * (N + 1)) &&
+              alloc(&jterm, n) && alloc(&psisum, n) && alloc(&Jd, n) && alloc(&step_base, 1) &&
+              alloc(&maxbits, 2 * n);
+    if (!ok) return fail(LLG_ENOMEM, "device allocation failed (" + std::to_string(bytes >> 20) + " MiB so far)");
+
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(dI, H.data(), sizeof(DevInst) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return cuda_fail(e, "upload descriptors");
+    if ((e = cudaMemcpyAsync(dRT, rt.data(), sizeof(RowTile) * rt.size(), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return cuda_fail(e, "upload row tiles");
+    if ((e = cudaMemcpyAsync(dCT, ct.data(), sizeof(ColTile) * ct.size(), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return cuda_fail(e, "upload column tiles");
+    {
+      std::vector<double2> h64(kTwiddleN);
+      std::vector<C> hT(kTwiddleN);
+      for (int k = 0; k < kTwiddleN; ++k) {
+        const double ang = -2.0 * M_PI * (double)k / (double)kTwiddleN;
+        h64[k] = make_double2(std::cos(ang), std::sin(ang));
+        hT[k].x = (T)h64[k].x;
+        hT[k].y = (T)h64[k].y;
+      }
+      if ((e = cudaMemcpyAsync(tw64, h64.data(), sizeof(double2) * kTwiddleN, cudaMemcpyHostToDevice, st)) !=
+          cudaSuccess)
+        return cuda_fail(e, "upload twiddles");
+      if ((e = cudaMemcpyAsync(tw, hT.data(), sizeof(C) * kTwiddleN, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "upload twiddles");
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "create");
+    }
+    // demag spectra, FP64 scratch of the largest shape
+    size_t gmax = 0;
+    for (const Shape& s : shapes) gmax = std::max(gmax, (size_t)4 * s.Px * s.Py);
+    double2* Gs = nullptr;
+    if (cudaMalloc(&Gs, gmax * sizeof(double2)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LLG_ENOMEM, "tensor scratch allocation failed");
+    }
+    for (const Shape& s : shapes) {
+      e = build_tensor_spectrum<T>(tens + s.off, Gs, s.nx, s.ny, s.Px, s.Py, s.dx, s.dy, s.dz, tw64, st);
+      nlaunch += 5;
+      if (e != cudaSuccess) {
+        cudaFree(Gs);
+        return cuda_fail(e, "demag tensor");
+      }
+    }
+    e = cudaStreamSynchronize(st);
+    cudaFree(Gs);
+    if (e != cudaSuccess) return cuda_fail(e, "demag tensor");
+    set_smem_limits<T>(smem);
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "create");
+    return LLG_OK;
+  }
+
+  // ------------------------------------------------------------- launches
+  RowArgs<T> row_args() {
+    RowArgs<T> a;
+    std::memset(&a, 0, sizeof a);
+    a.inst = dI;
+    a.tiles = dRT;
+    a.spec = spec;
+    a.tw = tw;
+    a.psi = psi;
+    a.step_base = step_base;
+    a.rows_max = R;
+    a.dt = dt;
+    a.n_from = n_from;
+    a.nsteps = N;
+    return a;
+  }
+  void rows(const RowArgs<T>& a, int mode) {
+    launch_rows<T>(a, mode, (int)rt.size(), smem, st);
+    ++nlaunch;
+  }
+  void cols() {
+    ColArgs<T> c;
+    c.inst = dI;
+    c.tiles = dCT;
+    c.spec = spec;
+    c.tw = tw;
+    c.tens = tens;
+    c.cols_max = TX;
+    launch_cols<T>(c, (int)ct.size(), smem, st);
+    ++nlaunch;
+  }
+  void set_step(long long v) {
+    launch_set_step(step_base, v, st);
+    ++nlaunch;
+  }
+  void fft_only(const T* Y) {
+    RowArgs<T> a = row_args();
+    a.Yin = Y;
+    rows(a, ROW_FFT_ONLY);
+  }
+  void material(const T* phi) {
+    cudaMemsetAsync(psisum, 0, sizeof(double) * n, st);
+    launch_material_tiles<T>(dI, dRT, (int)rt.size(), phi, psi, dpsi, psisum, st);
+    ++nlaunch;
+  }
+
+  // one RK4 step: record == false -> in place on m with ping-pong stage
+  // buffers; record == true -> stage inputs and fields into slot l of the
+  // segment record, m_{n+1} into the next record slot
+  void step(int l, bool record, bool objective) {
+    for (int s = 1; s <= 4; ++s) {
+      cols();
+      RowArgs<T> a = row_args();
+      a.local_step = l;
+      a.stage = s;
+      a.acc = acc;
+      a.slots = objective ? slots : nullptr;
+      if (record) {
+        a.m = recY_slot(4LL * l);
+        a.Yin = recY_slot(4LL * l + s - 1);
+        a.Bout = recB_slot(4LL * l + s - 1);
+        if (s < 4) a.Yout = recY_slot(4LL * l + s);
+        else a.mout = recY_slot(4LL * (l + 1));
+      } else {
+        a.m = m;
+        a.Yin = (s == 1) ? m : (s == 3 ? Yb : Ya);
+        if (s < 4) a.Yout = (s == 2) ? Yb : Ya;
+        else a.mout = m;
+      }
+      rows(a, ROW_STAGE);
+    }
+  }
+
+  // ------------------------------------------------------------ forward
+  llg_status forward(const void* phi_v, const void* m0_v, double* J, void* mT) override {
+    if (!phi_v || !m0_v || !J) return fail(LLG_EINVAL, "phi, m0 and J must not be NULL");
+    const T* phi = static_cast<const T*>(phi_v);
+    cudaEventRecord(ev0, st);
+    material(phi);
+    cudaMemcpyAsync(m, m0_v, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(slots, 0, sizeof(double) * n * (N + 1), st);
+    cudaMemsetAsync(jterm, 0, sizeof(double) * n, st);
+    fft_only(m);
+    const T* cur = m;
+    for (const Action& ac : fwd) {
+      if (ac.op == SNAP) {
+        cudaMemcpyAsync(ckpt + (size_t)ac.b * slot(), m, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
+      } else if (ac.op == ADVANCE) {
+        set_step(ac.a);
+        for (long long l = 0; l < ac.b - ac.a; ++l) step((int)l, false, true);
+        cur = m;
+      } else if (ac.op == RECORD) {
+        cudaMemcpyAsync(recY_slot(0), m, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
+        set_step(ac.a);
+        for (long long l = 0; l < ac.b - ac.a; ++l) step((int)l, true, true);
+        cur = recY_slot(4 * (ac.b - ac.a));
+      }
+    }
+    mN_ptr = cur;
+    // terminal: field of m_N, energies, lambda_N, explicit dJ/dpsi
+    cols();
+    {
+      RowArgs<T> a = row_args();
+      a.Yin = cur;
+      a.lam = lam;
+      a.psib = psib;
+      a.psic = psic;
+      a.jterm = jterm;
+      a.psisum = psisum;
+      rows(a, ROW_TERMINAL);
+    }
+    launch_reduce_slots(dI, n, slots, N + 1, jterm, psisum, Jd, st);
+    ++nlaunch;
+    if (mT) cudaMemcpyAsync(mT, cur, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
+    cudaEventRecord(ev1, st);
+    cudaMemcpyAsync(J, Jd, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "llg_forward");
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "llg_forward");
+    float f = 0.f;
+    cudaEventElapsedTime(&f, ev0, ev1);
+    ms = f;
+    have_fwd = true;
+    for (int i = 0; i < n; ++i)
+      if (!std::isfinite(J[i])) return fail(LLG_ENONFINITE, "J is not finite for instance " + std::to_string(i));
+    return LLG_OK;
+  }
+
+  // ------------------------------------------------------------ adjoint
+  AdjArgs<T> adj_args() {
+    AdjArgs<T> a;
+    std::memset(&a, 0, sizeof a);
+    a.inst = dI;
+    a.tiles = dRT;
+    a.spec = spec;
+    a.tw = tw;
+    a.psi = psi;
+    a.gpart = gpart;
+    a.lam = lam;
+    a.G = G;
+    a.psib = psib;
+    a.psic = psic;
+    a.step_base = step_base;
+    a.rows_max = R;
+    a.dt = dt;
+    a.n_from = n_from;
+    return a;
+  }
+  void adj(const AdjArgs<T>& a) {
+    launch_adj<T>(a, (int)rt.size(), smem, st);
+    ++nlaunch;
+  }
+
+  llg_status adjoint(void* dphi, void* dm0) override {
+    if (!have_fwd) return fail(LLG_ESTATE, "llg_adjoint needs a preceding llg_forward");
+    if (!dphi) return fail(LLG_EINVAL, "dJdphi must not be NULL");
+    cudaEventRecord(ev0, st);
+    int cur = 0;
+    for (const Action& ac : rev) {
+      if (ac.op == RESTORE) {
+        cudaMemcpyAsync(recY_slot(0), ckpt + (size_t)ac.a * slot(), sizeof(T) * slot(), cudaMemcpyDeviceToDevice,
+                        st);
+        fft_only(recY_slot(0));
+      } else if (ac.op == RECORD) {
+        set_step(ac.a);
+        for (long long l = 0; l < ac.b - ac.a; ++l) step((int)l, true, false);
+      } else if (ac.op == REVERSE) {
+        const long long len = ac.a - ac.b;
+        set_step(ac.b);
+        {
+          AdjArgs<T> a = adj_args();
+          a.local_step = (int)(len - 1);
+          a.stage = 4;
+          a.seed_only = 1;
+          a.Yprev = recY_slot(4 * (len - 1) + 3);
+          a.Bprev = recB_slot(4 * (len - 1) + 3);
+          a.BbarOut = bb[cur];
+          adj(a);
+        }
+        for (long long l = len - 1; l >= 0; --l) {
+          for (int s = 4; s >= 1; --s) {
+            cols();
+            AdjArgs<T> a = adj_args();
+            a.local_step = (int)l;
+            a.stage = s;
+            a.Ys = recY_slot(4 * l + s - 1);
+            a.Bbar = bb[cur];
+            a.BbarOut = bb[1 - cur];
+            if (s > 1) {
+              a.Yprev = recY_slot(4 * l + s - 2);
+              a.Bprev = recB_slot(4 * l + s - 2);
+            } else if (l > 0) {
+              a.Yprev = recY_slot(4 * (l - 1) + 3);
+              a.Bprev = recB_slot(4 * (l - 1) + 3);
+              a.seed_next = 1;
+            }
+            adj(a);
+            if (s > 1 || a.seed_next) cur ^= 1;
+          }
+        }
+      }
+    }
+    launch_grad_finish_tiles<T>(dI, dRT, (int)rt.size(), dpsi, psib, psic, static_cast<T*>(dphi), st);
+    ++nlaunch;
+    if (dm0) cudaMemcpyAsync(dm0, lam, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
+    cudaEventRecord(ev1, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "llg_adjoint");
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "llg_adjoint");
+    float f = 0.f;
+    cudaEventElapsedTime(&f, ev0, ev1);
+    ms = f;
+    have_fwd = false;
+    return LLG_OK;
+  }
+
+  llg_status levelset(void* phi, const void* grad, const unsigned char* mask, double lr) override {
+    if (!phi || !grad || !mask) return fail(LLG_EINVAL, "phi, grad and mask must not be NULL");
+    cudaMemsetAsync(maxbits, 0, sizeof(unsigned int) * 2 * n, st);
+    launch_levelset_tiles<T>(dI, dRT, (int)rt.size(), static_cast<T*>(phi), static_cast<const T*>(grad), mask,
+                             lr, maxbits, st);
+    nlaunch += 2;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "levelset_step");
+    return LLG_OK;
+  }
+
+  llg_status field(const void* phi, const void* mv, double t, int demag_only, void* B) override {
+    if (!phi || !mv || !B) return fail(LLG_EINVAL, "phi, m and B must not be NULL");
+    have_fwd = false;
+    material(static_cast<const T*>(phi));
+    fft_only(static_cast<const T*>(mv));
+    cols();
+    RowArgs<T> a = row_args();
+    a.Yin = static_cast<const T*>(mv);
+    a.Bout = static_cast<T*>(B);
+    a.t_field = t;
+    a.demag_only = demag_only;
+    rows(a, ROW_FIELD);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "llg_field");
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "llg_field");
+    return LLG_OK;
+  }
+};
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+llg_status llg_create(const llg_problem* inst, int n_inst, const llg_options* opt, void* cuda_stream,
+                      llg_ctx** out) {
+  if (!out) return LLG_EINVAL;
+  *out = nullptr;
+  if (!inst || n_inst <= 0) return LLG_EINVAL;
+  llg_options o;
+  if (opt) {
+    o = *opt;
+  } else {
+    std::memset(&o, 0, sizeof o);
+    o.precision = LLG_FP32;
+    o.ckpt = LLG_CKPT_PERIODIC;
+  }
+  llg_ctx* ctx = nullptr;
+  llg_status s;
+  if (o.precision == LLG_FP64) {
+    auto* e = new Engine<double>();
+    s = e->create(inst, n_inst, &o, static_cast<cudaStream_t>(cuda_stream));
+    ctx = e;
+  } else {
+    auto* e = new Engine<float>();
+    s = e->create(inst, n_inst, &o, static_cast<cudaStream_t>(cuda_stream));
+    ctx = e;
+  }
+  *out = ctx;   // returned even on failure so that llg_last_error can explain it
+  return s;
+}
+
+llg_status llg_forward(llg_ctx* ctx, const void* phi_dev, const void* m0_dev, double* J_host, void* mT_dev) {
+  if (!ctx) return LLG_EINVAL;
+  return ctx->forward(phi_dev, m0_dev, J_host, mT_dev);
+}
+
+llg_status llg_adjoint(llg_ctx* ctx, void* dJdphi_dev, void* dJdm0_dev) {
+  if (!ctx) return LLG_EINVAL;
+  return ctx->adjoint(dJdphi_dev, dJdm0_dev);
+}
+
+llg_status levelset_step(llg_ctx* ctx, void* phi_dev, const void* grad_dev, const unsigned char* mask_dev,
+                         double lr) {
+  if (!ctx) return LLG_EINVAL;
+  return ctx->levelset(phi_dev, grad_dev, mask_dev, lr);
+}
+
+llg_status llg_field(llg_ctx* ctx, const void* phi_dev, const void* m_dev, double t, int demag_only,
+                     void* B_dev) {
+  if (!ctx) return LLG_EINVAL;
+  return ctx->field(phi_dev, m_dev, t, demag_only, B_dev);
+}
+
+llg_status llg_query(llg_ctx* ctx, size_t* device_bytes, double* last_ms) {
+  if (!ctx) return LLG_EINVAL;
+  if (device_bytes) *device_bytes = ctx->device_bytes();
+  if (last_ms) *last_ms = ctx->last_ms();
+  return LLG_OK;
+}
+
+long long llg_launch_count(llg_ctx* ctx) { return ctx ? ctx->launches() : 0; }
+
+const char* llg_last_error(llg_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+void llg_destroy(llg_ctx* ctx) { delete ctx; }
+
+long long llg_schedule(long long nsteps, int ckpt, int seg_len, long long* actions, long long max_actions,
+                       long long* n_forward) {
+  if (nsteps < 0 || seg_len < 0 || (ckpt != LLG_CKPT_PERIODIC && ckpt != LLG_CKPT_STORE_ALL)) return -1;
+  std::vector<Action> f, r;
+  make_schedule(nsteps, ckpt, seg_len, f, r);
+  const long long tot = (long long)(f.size() + r.size());
+  if (n_forward) *n_forward = (long long)f.size();
+  if (actions) {
+    long long k = 0;
+    for (const Action& a : f) {
+      if (k >= max_actions) break;
+      actions[3 * k] = a.op; actions[3 * k + 1] = a.a; actions[3 * k + 2] = a.b;
+      ++k;
+    }
+    for (const Action& a : r) {
+      if (k >= max_actions) break;
+      actions[3 * k] = a.op; actions[3 * k + 1] = a.a; actions[3 * k + 2] = a.b;
+      ++k;
+    }
+  }
+  return tot;
+}
+
+int llg_padded_extents(int nx, int ny, int* Px, int* Py) {
+  if (nx < 1 || ny < 1) return -1;
+  if (Px) *Px = std::max(8, next_pow2(2 * nx));
+  if (Py) *Py = std::max(2, next_pow2(2 * ny));
+  return 0;
+}
+
+int llg_abi_version(void) { return 1; }
+
+}  // extern "C"

@@ -1,0 +1,334 @@
+"""ctypes binding of the C ABI in include/llg.h.
+
+Argument marshalling only: every step of the forward pass, the adjoint and
+the level-set update runs in the CUDA library.  Functions carry the C names
+(llg_create, llg_forward, llg_adjoint, levelset_step, llg_field, llg_query,
+llg_launch_count, llg_last_error, llg_destroy, llg_schedule,
+llg_padded_extents); `Solver` bundles them for torch tensors.
+
+Loading fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+
+from . import build as _build
+
+c_int, c_double, c_ll, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p
+
+LLG_OK, LLG_EINVAL, LLG_ENOMEM, LLG_ECUDA, LLG_ETIMEOUT, LLG_ENONFINITE, LLG_ESTATE = range(7)
+LLG_J_PORT, LLG_J_ENERGY_AREA = 0, 1
+LLG_FP32, LLG_FP64 = 0, 1
+LLG_CKPT_STORE_ALL, LLG_CKPT_PERIODIC = 0, 1
+
+EXPORTED = ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query",
+            "llg_launch_count", "llg_last_error", "llg_destroy", "llg_schedule",
+            "llg_padded_extents", "llg_abi_version")
+
+
+class llg_problem(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int),
+                ("dx", c_double), ("dy", c_double), ("dz", c_double),
+                ("Ms", c_double), ("A", c_double), ("Ku", c_double), ("ku", c_double * 3),
+                ("alpha", c_double), ("alpha_edge", c_double),
+                ("absorb_nodes", c_int), ("absorb_x", c_int), ("absorb_y", c_int),
+                ("B_bias", c_double * 3), ("b_rf", c_double), ("f_rf", c_double),
+                ("rf_dir", c_double * 3), ("src", c_int * 4),
+                ("dt", c_double), ("nsteps", c_ll), ("sigmoid_a", c_double),
+                ("objective", c_int), ("comp", c_int), ("power", c_int),
+                ("boxes", (c_int * 4) * 2), ("weights", c_double * 2), ("n_from", c_ll),
+                ("area_target", c_double), ("penalty_w", c_double)]
+
+
+class llg_options(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("ckpt", c_int), ("seg_len", c_int), ("use_graph", c_int),
+                ("rows_per_cta", c_int), ("cols_per_cta", c_int)]
+
+
+class LLGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"LLG status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load (building first if needed) the in-tree CUDA library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library {_build.LIB} is missing; run build() first")
+    lib = ctypes.CDLL(_build.LIB)
+    P = ctypes.POINTER
+    lib.llg_create.argtypes = [P(llg_problem), c_int, P(llg_options), c_void_p, P(c_void_p)]
+    lib.llg_forward.argtypes = [c_void_p, c_void_p, c_void_p, P(c_double), c_void_p]
+    lib.llg_adjoint.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.levelset_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double]
+    lib.llg_field.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_int, c_void_p]
+    lib.llg_query.argtypes = [c_void_p, P(ctypes.c_size_t), P(c_double)]
+    lib.llg_launch_count.argtypes = [c_void_p]
+    lib.llg_launch_count.restype = c_ll
+    lib.llg_last_error.argtypes = [c_void_p]
+    lib.llg_last_error.restype = ctypes.c_char_p
+    lib.llg_destroy.argtypes = [c_void_p]
+    lib.llg_destroy.restype = None
+    lib.llg_schedule.argtypes = [c_ll, c_int, c_int, P(c_ll), c_ll, P(c_ll)]
+    lib.llg_schedule.restype = c_ll
+    lib.llg_padded_extents.argtypes = [c_int, c_int, P(c_int), P(c_int)]
+    lib.llg_abi_version.restype = c_int
+    for f in ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query"):
+        getattr(lib, f).restype = c_int
+    _lib = lib
+    return lib
+
+
+def to_struct(p) -> llg_problem:
+    """llg_problem from any object with the fields of workloads.Problem."""
+    s = llg_problem()
+    s.nx, s.ny, s.nz = p.nx, p.ny, p.nz
+    s.dx, s.dy, s.dz = p.dx, p.dy, p.dz
+    s.Ms, s.A, s.Ku = p.Ms, p.A, p.Ku
+    s.ku[:] = list(p.ku)
+    s.alpha, s.alpha_edge = p.alpha, p.alpha_edge
+    s.absorb_nodes, s.absorb_x, s.absorb_y = p.absorb_nodes, p.absorb_x, p.absorb_y
+    s.B_bias[:] = list(p.B_bias)
+    s.b_rf, s.f_rf = p.b_rf, p.f_rf
+    s.rf_dir[:] = list(p.rf_dir)
+    s.src[:] = list(p.src)
+    s.dt, s.nsteps, s.sigmoid_a = p.dt, p.nsteps, p.sigmoid_a
+    s.objective, s.comp, s.power = p.objective, p.comp, p.power
+    for b in range(2):
+        s.boxes[b][:] = list(p.boxes[b])
+    s.weights[:] = list(p.weights)
+    s.n_from = p.n_from
+    s.area_target, s.penalty_w = p.area_target, p.penalty_w
+    return s
+
+
+def _check(lib, ctx, st):
+    if st != LLG_OK:
+        msg = lib.llg_last_error(ctx)
+        raise LLGError(st, msg.decode() if msg else "")
+
+
+# ---- thin wrappers with the C names -------------------------------------
+
+def llg_create(problems: Sequence, precision=LLG_FP32, ckpt=LLG_CKPT_PERIODIC, seg_len=0,
+               stream=0, rows_per_cta=0, cols_per_cta=0, use_graph=0) -> int:
+    lib = load()
+    arr = (llg_problem * len(problems))(*[to_struct(p) for p in problems])
+    opt = llg_options(precision, ckpt, seg_len, use_graph, rows_per_cta, cols_per_cta)
+    ctx = c_void_p()
+    st = lib.llg_create(arr, len(problems), ctypes.byref(opt), c_void_p(stream), ctypes.byref(ctx))
+    if st != LLG_OK:
+        msg = lib.llg_last_error(ctx).decode() if ctx.value else ""
+        if ctx.value:
+            lib.llg_destroy(ctx)
+        raise LLGError(st, msg)
+    return ctx.value
+
+
+def llg_forward(ctx: int, phi_ptr: int, m0_ptr: int, n_inst: int, mT_ptr: int = 0) -> np.ndarray:
+    lib = load()
+    J = (c_double * n_inst)()
+    _check(lib, ctx, lib.llg_forward(c_void_p(ctx), c_void_p(phi_ptr), c_void_p(m0_ptr), J,
+                                     c_void_p(mT_ptr or None)))
+    return np.array(J[:])
+
+
+def llg_adjoint(ctx: int, dphi_ptr: int, dm0_ptr: int = 0) -> None:
+    lib = load()
+    _check(lib, ctx, lib.llg_adjoint(c_void_p(ctx), c_void_p(dphi_ptr), c_void_p(dm0_ptr or None)))
+
+
+def levelset_step(ctx: int, phi_ptr: int, grad_ptr: int, mask_ptr: int, lr: float) -> None:
+    lib = load()
+    _check(lib, ctx, lib.levelset_step(c_void_p(ctx), c_void_p(phi_ptr), c_void_p(grad_ptr),
+                                       c_void_p(mask_ptr), lr))
+
+
+def llg_field(ctx: int, phi_ptr: int, m_ptr: int, t: float, demag_only: bool, B_ptr: int) -> None:
+    lib = load()
+    _check(lib, ctx, lib.llg_field(c_void_p(ctx), c_void_p(phi_ptr), c_void_p(m_ptr), t,
+                                   int(bool(demag_only)), c_void_p(B_ptr)))
+
+
+def llg_query(ctx: int):
+    lib = load()
+    b = ctypes.c_size_t()
+    ms = c_double()
+    _check(lib, ctx, lib.llg_query(c_void_p(ctx), ctypes.byref(b), ctypes.byref(ms)))
+    return b.value, ms.value
+
+
+def llg_launch_count(ctx: int) -> int:
+    return load().llg_launch_count(c_void_p(ctx))
+
+
+def llg_last_error(ctx: int) -> str:
+    return load().llg_last_error(c_void_p(ctx)).decode()
+
+
+def llg_destroy(ctx: int) -> None:
+    load().llg_destroy(c_void_p(ctx))
+
+
+def llg_schedule(nsteps: int, ckpt: int = LLG_CKPT_PERIODIC, seg_len: int = 0):
+    """(forward_actions, reverse_actions) as lists of (op, a, b)."""
+    lib = load()
+    nf = c_ll()
+    tot = lib.llg_schedule(nsteps, ckpt, seg_len, None, 0, ctypes.byref(nf))
+    if tot < 0:
+        raise LLGError(LLG_EINVAL, "bad schedule arguments")
+    buf = (c_ll * (3 * max(tot, 1)))()
+    lib.llg_schedule(nsteps, ckpt, seg_len, buf, tot, ctypes.byref(nf))
+    acts = [tuple(buf[3 * k:3 * k + 3]) for k in range(tot)]
+    return acts[:nf.value], acts[nf.value:]
+
+
+def llg_padded_extents(nx: int, ny: int):
+    px, py = c_int(), c_int()
+    load().llg_padded_extents(nx, ny, ctypes.byref(px), ctypes.byref(py))
+    return px.value, py.value
+
+
+# ---- torch convenience layer ------------------------------------------------
+
+class Solver:
+    """A batch of instances on one GPU.  Inputs and outputs are torch CUDA
+    tensors packed back to back in instance order (phi: [sum n_i], m:
+    [sum 3 n_i] with each instance laid out [3][ny][nx])."""
+
+    def __init__(self, problems: Sequence, precision: str = "fp32", ckpt: str = "periodic",
+                 seg_len: int = 0, stream=None, rows_per_cta: int = 0, cols_per_cta: int = 0):
+        import torch
+        self.torch = torch
+        self.problems = list(problems)
+        self.dtype = torch.float32 if precision == "fp32" else torch.float64
+        prec = LLG_FP32 if precision == "fp32" else LLG_FP64
+        ck = LLG_CKPT_PERIODIC if ckpt == "periodic" else LLG_CKPT_STORE_ALL
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = llg_create(self.problems, prec, ck, seg_len, self.stream.cuda_stream,
+                              rows_per_cta, cols_per_cta)
+        self.nodes = [p.nx * p.ny * p.nz for p in self.problems]
+        self.total = sum(self.nodes)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            llg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # packing helpers ---------------------------------------------------
+    def pack_scalar(self, arrays) -> "torch.Tensor":
+        t = self.torch
+        return t.cat([t.as_tensor(np.asarray(a).reshape(-1), dtype=self.dtype) for a in arrays]).cuda()
+
+    def pack_vector(self, arrays) -> "torch.Tensor":
+        return self.pack_scalar(arrays)
+
+    def unpack_scalar(self, x):
+        out, o = [], 0
+        for p, k in zip(self.problems, self.nodes):
+            out.append(x[o:o + k].reshape(p.nz, p.ny, p.nx))
+            o += k
+        return out
+
+    def unpack_vector(self, x):
+        out, o = [], 0
+        for p, k in zip(self.problems, self.nodes):
+            out.append(x[o:o + 3 * k].reshape(3, p.nz, p.ny, p.nx))
+            o += 3 * k
+        return out
+
+    def _chk(self, x, n):
+        t = self.torch
+        if not (isinstance(x, t.Tensor) and x.is_cuda and x.dtype == self.dtype and x.is_contiguous()
+                and x.numel() == n):
+            raise ValueError(f"expected a contiguous CUDA {self.dtype} tensor with {n} elements")
+        return x.data_ptr()
+
+    # calls ---------------------------------------------------------------
+    def forward(self, phi, m0, want_mT: bool = False):
+        mT = self.torch.empty(3 * self.total, dtype=self.dtype, device="cuda") if want_mT else None
+        J = llg_forward(self.ctx, self._chk(phi, self.total), self._chk(m0, 3 * self.total),
+                        len(self.problems), mT.data_ptr() if mT is not None else 0)
+        return J, mT
+
+    def adjoint(self, want_dm0: bool = False):
+        g = self.torch.empty(self.total, dtype=self.dtype, device="cuda")
+        dm0 = self.torch.empty(3 * self.total, dtype=self.dtype, device="cuda") if want_dm0 else None
+        llg_adjoint(self.ctx, g.data_ptr(), dm0.data_ptr() if dm0 is not None else 0)
+        return g, dm0
+
+    def levelset_step(self, phi, grad, mask, lr: float):
+        if mask.dtype != self.torch.uint8 or not mask.is_cuda:
+            raise ValueError("mask must be a CUDA uint8 tensor")
+        levelset_step(self.ctx, self._chk(phi, self.total), self._chk(grad, self.total), mask.data_ptr(), lr)
+        return phi
+
+    def field(self, phi, m, t: float = 0.0, demag_only: bool = False):
+        B = self.torch.empty(3 * self.total, dtype=self.dtype, device="cuda")
+        llg_field(self.ctx, self._chk(phi, self.total), self._chk(m, 3 * self.total), t, demag_only,
+                  B.data_ptr())
+        return B
+
+    def query(self):
+        return llg_query(self.ctx)
+
+    def launch_count(self) -> int:
+        return llg_launch_count(self.ctx)
+
+
+def _make_function():
+    import torch
+
+    class LLGFunction(torch.autograd.Function):
+        """J = LLGFunction.apply(phi, m0, solver): forward pass of the solver;
+        backward runs the hand-written adjoint sweep (no autograd tape)."""
+
+        @staticmethod
+        def forward(ctx, phi, m0, solver):
+            J, _ = solver.forward(phi.contiguous(), m0.contiguous())
+            ctx.solver = solver
+            ctx.counts = solver.nodes
+            return torch.as_tensor(J, dtype=torch.float64, device=phi.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            solver = ctx.solver
+            g, dm0 = solver.adjoint(want_dm0=True)
+            w = gJ.to(g.dtype)
+            scale = torch.repeat_interleave(w, torch.as_tensor(ctx.counts, device=g.device))
+            scale3 = torch.repeat_interleave(w, torch.as_tensor([3 * c for c in ctx.counts], device=g.device))
+            return g * scale, dm0 * scale3, None
+
+    return LLGFunction
+
+
+_fn = None
+
+
+def llg_function():
+    global _fn
+    if _fn is None:
+        _fn = _make_function()
+    return _fn

@@ -1,0 +1,147 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Tolerances: FP64 path 1e-9 relative (rounding order only); FP32
+path 1e-5 relative L2 on m after 1000 steps and 1e-4 relative L2 on dJ/dPhi
+(the targets the method's FP32 build is held to)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_util import gpu_run, gpu_solver, oracle_run, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _needs_gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_2411_19109_gb300 import load
+    load()
+
+
+FIELD_CASES = [(4, 1), (8, 5), (12, 7), (16, 9), (32, 32), (36, 20), (64, 3)]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 2e-6)])
+@pytest.mark.parametrize("shape", FIELD_CASES)
+def test_field_parity(shape, precision, tol):
+    from oracle import llg
+    inst = W.random_small(*shape, 1, seed=shape[0] * 7 + shape[1])
+    s = gpu_solver([inst], precision)
+    try:
+        phi = s.pack_scalar([inst.phi])
+        m = s.pack_vector([inst.m0])
+        model = llg.Model(inst.problem, inst.phi)
+        Bd = s.unpack_vector(s.field(phi, m, 0.0, demag_only=True))[0].double().cpu().numpy()
+        assert rel_l2(Bd, model.demag(inst.m0)) < tol
+        t = 3.7e-11
+        B = s.unpack_vector(s.field(phi, m, t))[0].double().cpu().numpy()
+        assert rel_l2(B, model.field(inst.m0, t)) < tol
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("precision,tol_m,tol_g", [("fp64", 1e-10, 1e-9), ("fp32", 1e-5, 1e-4)])
+@pytest.mark.parametrize("shape,objective", [((12, 8), W.J_PORT), ((16, 12), W.J_ENERGY_AREA),
+                                             ((8, 5), W.J_PORT), ((20, 3), W.J_ENERGY_AREA)])
+def test_forward_adjoint_parity_small(shape, objective, precision, tol_m, tol_g):
+    inst = W.random_small(*shape, 1, seed=3, nsteps=40, objective=objective)
+    g = gpu_run([inst], precision, want_dm0=True)
+    o = oracle_run(inst)
+    assert rel_l2(g["mT"][0], o["mT"]) < tol_m
+    assert abs(g["J"][0] - o["J"]) <= tol_g * max(abs(o["J"]), 1e-30)
+    assert rel_l2(g["dphi"][0], o["dphi"]) < tol_g
+    assert rel_l2(g["dm0"][0], o["dm0"]) < tol_g
+
+
+@pytest.mark.parametrize("precision,tol_m,tol_g", [("fp64", 1e-10, 1e-9), ("fp32", 1e-5, 1e-4)])
+def test_film32_1000_steps(precision, tol_m, tol_g):
+    inst = W.film32()
+    g = gpu_run([inst], precision)
+    o = oracle_run(inst)
+    assert rel_l2(g["mT"][0], o["mT"]) < tol_m
+    assert abs(g["J"][0] - o["J"]) <= tol_g * abs(o["J"])
+    assert rel_l2(g["dphi"][0], o["dphi"]) < tol_g
+
+
+def test_batch_of_uneven_grids_matches_single_runs():
+    insts = [W.random_small(12, 8, 1, seed=1, nsteps=30),
+             W.random_small(32, 5, 1, seed=2, nsteps=30, objective=W.J_ENERGY_AREA),
+             W.random_small(8, 16, 1, seed=3, nsteps=30)]
+    b = gpu_run(insts, "fp64")
+    for k, inst in enumerate(insts):
+        o = oracle_run(inst)
+        assert rel_l2(b["mT"][k], o["mT"]) < 1e-10
+        assert rel_l2(b["dphi"][k], o["dphi"]) < 1e-9
+        single = gpu_run([inst], "fp64")
+        np.testing.assert_array_equal(single["dphi"][0], b["dphi"][k])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_schedules_give_identical_gradients(precision):
+    inst = W.random_small(12, 8, 1, seed=5, nsteps=23)
+    ref = gpu_run([inst], precision, ckpt="store_all")
+    for seg in (0, 1, 4, 23, 40):
+        g = gpu_run([inst], precision, ckpt="periodic", seg_len=seg)
+        np.testing.assert_array_equal(g["dphi"][0], ref["dphi"][0])
+        assert g["J"][0] == ref["J"][0]
+
+
+def test_levelset_step_matches_oracle():
+    from oracle import llg
+    insts = [W.random_small(12, 8, 1, seed=1), W.random_small(8, 4, 1, seed=2)]
+    rng = np.random.default_rng(0)
+    s = gpu_solver(insts, "fp64")
+    try:
+        phi = s.pack_scalar([i.phi for i in insts])
+        grads = [rng.standard_normal(i.phi.shape) for i in insts]
+        masks = []
+        for i in insts:
+            mk = (rng.uniform(size=i.phi.shape) < 0.6).astype(np.uint8)
+            masks.append(mk)
+        grad = s.pack_scalar(grads)
+        mask = torch.cat([torch.as_tensor(mk.reshape(-1)) for mk in masks]).cuda()
+        s.levelset_step(phi, grad, mask, 0.07)
+        out = s.unpack_scalar(phi)
+        for k, inst in enumerate(insts):
+            ref = llg.levelset_step(inst.phi, grads[k], masks[k], 0.07)
+            np.testing.assert_allclose(out[k].cpu().numpy(), ref, rtol=1e-15, atol=1e-15)
+    finally:
+        s.close()
+
+
+def test_zero_steps_and_late_window():
+    inst = W.random_small(8, 4, 1, seed=4, nsteps=0, objective=W.J_ENERGY_AREA)
+    g = gpu_run([inst], "fp64")
+    o = oracle_run(inst)
+    assert abs(g["J"][0] - o["J"]) < 1e-9 * abs(o["J"])
+    assert rel_l2(g["dphi"][0], o["dphi"]) < 1e-9
+    inst = W.random_small(8, 4, 1, seed=4, nsteps=5, n_from=9)
+    g = gpu_run([inst], "fp64")
+    assert g["J"][0] == 0.0
+    assert np.abs(g["dphi"][0]).max() == 0.0
+
+
+def test_autograd_function():
+    from paper_2411_19109_gb300 import llg_function
+    inst = W.random_small(12, 8, 1, seed=6, nsteps=20)
+    s = gpu_solver([inst], "fp64")
+    try:
+        phi = s.pack_scalar([inst.phi]).requires_grad_(True)
+        m0 = s.pack_vector([inst.m0]).requires_grad_(True)
+        J = llg_function().apply(phi, m0, s)
+        (3.0 * J.sum()).backward()
+        o = oracle_run(inst)
+        assert rel_l2(phi.grad.cpu().numpy(), 3.0 * o["dphi"]) < 1e-9
+        assert rel_l2(m0.grad.cpu().numpy(), 3.0 * o["dm0"]) < 1e-9
+    finally:
+        s.close()
+
+
+def test_invalid_sizes_are_rejected():
+    from paper_2411_19109_gb300 import LLGError
+    bad = W.random_small(6, 4, 1).problem        # nx % 4 != 0
+    with pytest.raises(LLGError):
+        gpu_solver([type("I", (), {"problem": bad})()])

@@ -56,5 +56,8 @@ def test_default_segment():
 
 
 def test_store_all():
-    assert S.store_all(10) == ([(S.RECORD, 0, 10)], [(S.REVERSE, 10, 0)])
+    fwd, rev = S.store_all(3)
+    assert fwd == [(S.SNAP, 0, 0), (S.ADVANCE, 0, 1), (S.SNAP, 1, 1), (S.ADVANCE, 1, 2), (S.RECORD, 2, 3)]
+    assert rev == [(S.REVERSE, 3, 2), (S.RESTORE, 1, 1), (S.RECORD, 1, 2), (S.REVERSE, 2, 1),
+                   (S.RESTORE, 0, 0), (S.RECORD, 0, 1), (S.REVERSE, 1, 0)]
     assert S.store_all(0) == ([], [])
