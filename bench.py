@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Benchmark of the LLG forward + adjoint hot path on one node.
+
+A step is one level-set iteration of the batched demultiplexer workload
+(`batch64`): 8 candidates x 4 grid shapes (128x64, 256x64, 256x128, 512x128)
+x 2 drive frequencies = 64 instances, 1,966,080 nodes, each integrated for
+10,000 RK4 steps (forward), swept back by the checkpointed discrete adjoint
+(dJ/dPhi) and updated by the level-set step.  Metric: node-steps per second
+of forward + adjoint, node-steps = sum over instances of nodes x RK4 steps.
+
+Multi-GPU: every rank runs its own copy of the workload (independent
+instances, no collective on the data path); value = all ranks' node-steps /
+the slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "LLG fwd+adjoint node-steps/s, FP32 batched vs FP64 plain on GB300; % HBM roofline"
+UNIT = "node-steps/s"
+
+# Algorithmic bytes per node per launch (FP32), the data each kernel must move
+# at least once: see DESIGN.md, "Kernels and their rooflines".
+BYTES_PER_NODE = {0: 112.0, 1: 48.0, 2: 185.0}
+FAMILY = {0: "rows_kernel<float,ROW_STAGE> (inverse row FFT + field + RK4 stage + forward row FFT)",
+          1: "cols_kernel<float> (column FFT, tensor product, inverse column FFT)",
+          2: "adj_kernel<float> (adjoint stage: demag/exchange transposes, dJ/dpsi, next Bbar + row FFT)"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--nsteps", type=int, default=10000, help="RK4 steps per instance")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 and CPU legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2411_19109_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(family):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("source_hash") != kernel_source_hash():
+            return None
+        e = d["families"].get(str(family))
+        return None if e is None else float(e["dram_bytes_per_full_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# --------------------------------------------------------------------------
+# oracle leg (host cores): the CPU baseline and the reference arm
+# --------------------------------------------------------------------------
+
+def oracle_sample(nsteps=120):
+    """Forward + adjoint of one 128x64 demultiplexer instance for `nsteps`
+    RK4 steps with the FP64 oracle.  Returns (node-steps/s, seconds, sample)."""
+    from oracle import llg as ollg
+    inst = W.batch64(nsteps=nsteps, candidates=1)[0]
+    t0 = time.perf_counter()
+    model = ollg.Model(inst.problem, inst.phi)
+    J, _, traj = model.forward(inst.m0, keep=True)
+    model.adjoint(inst.m0, traj)
+    dt = time.perf_counter() - t0
+    ns = inst.problem.nx * inst.problem.ny * nsteps
+    return ns / dt, dt, f"1 instance 128x64 of batch64, {nsteps} RK4 steps forward + store-all adjoint (FP64 numpy)"
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    nst = 120
+    for _ in range(max(0, args.warmup)):
+        oracle_sample(20)
+    vals, secs = [], []
+    for _ in range(max(1, args.steps)):
+        v, s, sample = oracle_sample(nst)
+        vals.append(v)
+        secs.append(s)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "batch64 (sampled: one 128x64 instance per step)", "nsteps": nst},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    from paper_2411_19109_gb300 import Solver
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    insts = W.batch64(nsteps=args.nsteps)
+    nodes = sum(i.problem.nx * i.problem.ny for i in insts)
+    node_steps = nodes * args.nsteps
+    stream = torch.cuda.current_stream()
+    s = Solver([i.problem for i in insts], precision="fp32", ckpt="periodic", time_kernels=True, stream=stream)
+    phi0 = s.pack_scalar([i.phi for i in insts])
+    m0 = s.pack_vector([i.m0 for i in insts])
+    mask = torch.cat([torch.as_tensor(i.mask.reshape(-1)) for i in insts]).cuda()
+    phi = phi0.clone()
+
+    def step(lr):
+        J, _ = s.forward(phi, m0)
+        g, _ = s.adjoint()
+        s.levelset_step(phi, g, mask, lr)
+        return J, g
+
+    # warm-up; the learning rate is fixed from the first gradient
+    lr = 0.0
+    for w in range(max(3, args.warmup)):
+        J, g = step(lr)
+        if w == 0:
+            gmax = float(g.abs().max().item())
+            lr = 0.02 / gmax if gmax > 0 else 0.0
+    torch.cuda.synchronize()
+
+    fam0 = {f: s.kernel_time(f) for f in (0, 1, 2)}
+    l0 = s.launch_count()
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        J, g = step(lr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = s.launch_count() - l0
+    fam1 = {f: s.kernel_time(f) for f in (0, 1, 2)}
+    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = node_steps * world / (ms_max / 1e3)
+
+    # roofline of the dominant kernel family over the timed region
+    hbm, peak_kind = measured_peaks()
+    kern = {}
+    for f in (0, 1, 2):
+        n = fam1[f][0] - fam0[f][0]
+        t = fam1[f][1] - fam0[f][1]
+        if n <= 0:
+            continue
+        avg_ms = t / n
+        bytes_launch = BYTES_PER_NODE[f] * nodes
+        kern[f] = {"kernel": FAMILY[f], "launches": n, "total_ms": t, "avg_us": 1e3 * avg_ms,
+                   "share": None, "bytes_per_launch": bytes_launch,
+                   "achieved_gbs": bytes_launch / (avg_ms / 1e3) / 1e9}
+    tot = sum(v["total_ms"] for v in kern.values()) or 1.0
+    for v in kern.values():
+        v["share"] = v["total_ms"] / tot
+    dom = max(kern, key=lambda f: kern[f]["total_ms"])
+    ach = kern[dom]["achieved_gbs"]
+    roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": ncu_traffic(dom), "kernel": kern[dom]["kernel"],
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                "bytes_per_node": BYTES_PER_NODE[dom], "nodes_per_launch": nodes}
+
+    mem_bytes, _ = s.query()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch64: 8 candidates x {128x64,256x64,256x128,512x128} x 2 frequencies "
+                                   "(3.0/3.4 GHz), YIG demultiplexer, 5 nm cells",
+                       "instances": len(insts), "nodes": nodes, "rk4_steps": args.nsteps,
+                       "checkpoint": "periodic, K = ceil(sqrt(N))", "precision": "fp32",
+                       "l2": "inputs larger than L2 (working set %.1f GB per GPU)" % (mem_bytes / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "kernels": {FAMILY[f].split(" ")[0]: {k: v for k, v in kern[f].items() if k != "kernel"}
+                        for f in kern},
+            "peak_mem_bytes": int(mem_bytes)}
+
+    if rank == 0 and not args.no_extras:
+        # e2e: the same step through the public API with host buffers
+        phi_h = phi0.cpu().pin_memory()
+        m0_h = m0.cpu().pin_memory()
+        g_h = torch.empty(s.total, dtype=torch.float32).pin_memory()
+        phi_d = torch.empty_like(phi0)
+        m0_d = torch.empty_like(m0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        phi_d.copy_(phi_h, non_blocking=True)
+        m0_d.copy_(m0_h, non_blocking=True)
+        Jh, _ = s.forward(phi_d, m0_d)
+        gd, _ = s.adjoint()
+        s.levelset_step(phi_d, gd, mask, lr)
+        g_h.copy_(gd, non_blocking=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        e2e_ms = max(a0.elapsed_time(a1), 1e3 * wall)
+        h2d = (phi0.numel() + m0.numel()) * 4
+        d2h = s.total * 4 + 8 * len(insts)
+        line["e2e"] = {"value": node_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "steps": 1}
+        # plain FP64 store-all path on the same instances, sampled steps
+        nst64 = 200
+        insts64 = W.batch64(nsteps=nst64)
+        s64 = Solver([i.problem for i in insts64], precision="fp64", ckpt="store_all")
+        p64 = s64.pack_scalar([i.phi for i in insts64])
+        q64 = s64.pack_vector([i.m0 for i in insts64])
+        s64.forward(p64, q64)
+        s64.adjoint()
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        s64.forward(p64, q64)
+        s64.adjoint()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = b0.elapsed_time(b1)
+        mem64, _ = s64.query()
+        per_step = mem64 / nst64
+        line["fp64_store_all"] = {"value": nodes * nst64 / (ms64 / 1e3), "unit": UNIT,
+                                  "sample": f"all 64 instances, {nst64} RK4 steps",
+                                  "device_bytes_sample": int(mem64),
+                                  "device_bytes_projected_full": int(per_step * args.nsteps)}
+        s64.close()
+        del p64, q64
+        # CPU baseline: the oracle on this host's cores
+        v, secs, sample = oracle_sample(120)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                                "seconds": secs}
+    elif rank == 0:
+        line["e2e"] = None
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -97,8 +97,9 @@ typedef struct {
   int ckpt;        /* LLG_CKPT_PERIODIC (O(sqrt N) memory) or LLG_CKPT_STORE_ALL */
   int seg_len;     /* periodic segment length K; 0 = ceil(sqrt(max nsteps))     */
   int use_graph;   /* 1 = replay captured CUDA graphs of whole segments         */
-  int rows_per_cta;/* tile rows of the row kernels; 0 = autotune                */
-  int cols_per_cta;/* tile columns of the column kernel; 0 = autotune           */
+  int rows_per_cta;/* reserved (tile rows follow from the row FFT length)      */
+  int cols_per_cta;/* reserved (tile columns follow from the column FFT length) */
+  int time_kernels;/* 1 = bracket every stage-kernel launch with CUDA events    */
 } llg_options;
 
 typedef struct llg_ctx llg_ctx;
@@ -139,8 +140,15 @@ llg_status llg_field(llg_ctx* ctx, const void* phi_dev, const void* m_dev, doubl
  * llg_forward / llg_adjoint call. */
 llg_status llg_query(llg_ctx* ctx, size_t* device_bytes, double* last_ms);
 
-/* Number of kernels the last llg_forward + llg_adjoint pair launched. */
+/* Number of kernels the context has launched since llg_create. */
 long long llg_launch_count(llg_ctx* ctx);
+
+/* Device time of one kernel family since llg_create, summed over CUDA-event
+ * pairs recorded around each launch on the context's stream (needs
+ * llg_options.time_kernels = 1; otherwise both outputs are 0).
+ * family: 0 = forward row/stage kernel, 1 = column (demag) kernel,
+ *         2 = adjoint stage kernel. */
+llg_status llg_kernel_time(llg_ctx* ctx, int family, long long* launches, double* total_ms);
 
 const char* llg_last_error(llg_ctx* ctx);
 void llg_destroy(llg_ctx* ctx);

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libllg_gb300.so")
-SOURCES = ("tensor.cu", "kernels.cu", "runtime.cu")
+SOURCES = ("k_stage_f32.cu", "k_adj_f32.cu", "k_stage_f64.cu", "k_adj_f64.cu", "k_rowmisc_f32.cu",
+           "k_rowmisc_f64.cu", "k_cols_f32.cu", "k_cols_f64.cu", "tensor.cu", "k_misc.cu", "runtime.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
@@ -56,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             print(r.stdout + r.stderr, file=sys.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]

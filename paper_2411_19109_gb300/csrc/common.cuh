@@ -10,7 +10,7 @@ namespace llg {
 constexpr double kMu0 = 1.2566370614359173e-06;     // 4 pi 1e-7
 constexpr double kGamma = 1.76085963023e11;         // rad s^-1 T^-1
 constexpr int kTwiddleN = 4096;                      // W_4096^k table length
-constexpr int kMaxLx = 2048;                         // complex row FFT length
+constexpr int kMaxLx = 1024;                         // complex row FFT length (nx <= 1024)
 constexpr int kMaxPy = 1024;                         // column FFT length
 
 template <typename T> struct Cplx;
@@ -32,6 +32,19 @@ template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s)
 template <typename C> __device__ __forceinline__ C mul_mi(C a) { return mk<C>(a.y, -a.x); }
 template <typename C> __device__ __forceinline__ C mul_pi(C a) { return mk<C>(-a.y, a.x); }
 
+// Block-wide sum of a double; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+
 // Per-instance descriptor (device copy).  Offsets are in elements of the
 // pooled arrays; every node offset is a multiple of 4.
 struct DevInst {
@@ -44,6 +57,7 @@ struct DevInst {
   long long spec_off;    // offset into the spectrum pool, complex elements
   long long tens_off;    // offset into the tensor pool, real elements
   long long slot_off;    // offset into the per-step objective slots (nsteps+1)
+  long long rf_off;      // offset into the RF drive table (3 nsteps + 3 values)
   double Ms;
   double cex_x, cex_y, cex_z;   // 2A/(Ms h^2)
   double kan;                   // 2Ku/Ms
@@ -64,6 +78,18 @@ struct DevInst {
   double A;                     // exchange constant
   double area_target, penalty_w;
 };
+
+// Cooperative copy of a descriptor into shared memory (all threads call it).
+__device__ __forceinline__ void load_inst(DevInst& dst, const DevInst* src) {
+  static_assert(sizeof(DevInst) % 4 == 0, "descriptor must be word sized");
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(DevInst) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+// Rows per row tile for a row FFT of length L: L/8 threads per row in a
+// 128-thread block (every thread then owns a row slot).
+__host__ __device__ constexpr int rows_per_tile(int L) { return 1024 / L; }
 
 // Row tile: rows y0 .. y0+nrows-1 of instance `inst`.
 struct RowTile { int inst, y0, nrows, pad; };

@@ -1,0 +1,69 @@
+// Kernel-family dispatch and the small untemplated kernels.
+#include "kernels.cuh"
+
+namespace llg {
+
+int rows_threads() { return 128; }
+int cols_threads() { return 128; }
+int adj_threads() { return 128; }
+
+__global__ void set_step_kernel(long long* p, long long v) { *p = v; }
+
+// J_i = Kahan sum of the per-step slots + terminal term + area penalty
+__global__ void reduce_slots_kernel(const DevInst* inst, const double* slots, long long nslots,
+                                    const double* jterm, const double* psisum, double* J) {
+  __shared__ double red[32];
+  const DevInst& I = inst[blockIdx.x];
+  double sum = 0.0, comp = 0.0;
+  for (long long k = threadIdx.x; k < nslots; k += blockDim.x) {
+    const double y = slots[I.slot_off + k] - comp;
+    const double t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+  }
+  const double tot = block_sum(sum - comp, red);
+  if (threadIdx.x == 0) {
+    double j = tot + jterm[blockIdx.x];
+    if (I.objective == 1) {
+      const double f = psisum[blockIdx.x] / (double)I.nodes - I.area_target;
+      j += I.penalty_w * f * f;
+    }
+    J[blockIdx.x] = j;
+  }
+}
+
+void launch_set_step(long long* step_base, long long v, cudaStream_t st) {
+  set_step_kernel<<<1, 1, 0, st>>>(step_base, v);
+}
+
+void launch_reduce_slots(const DevInst* inst, int n_inst, const double* slots, long long nslots,
+                         const double* jterm, const double* psisum, double* J, cudaStream_t st) {
+  reduce_slots_kernel<<<n_inst, 256, 0, st>>>(inst, slots, nslots, jterm, psisum, J);
+}
+
+template <typename T>
+void launch_rows(const RowArgs<T>& a, int mode, int ntiles, size_t smem, cudaStream_t st) {
+  switch (mode) {
+    case ROW_FFT_ONLY: launch_rows_mode<T, ROW_FFT_ONLY>(a, ntiles, smem, st); break;
+    case ROW_STAGE: launch_rows_mode<T, ROW_STAGE>(a, ntiles, smem, st); break;
+    case ROW_FIELD: launch_rows_mode<T, ROW_FIELD>(a, ntiles, smem, st); break;
+    default: launch_rows_mode<T, ROW_TERMINAL>(a, ntiles, smem, st); break;
+  }
+}
+
+template <typename T>
+void set_smem_limits(size_t rows, size_t cols, size_t adj) {
+  smem_rows_mode<T, ROW_FFT_ONLY>(cols);
+  smem_rows_mode<T, ROW_STAGE>(rows);
+  smem_rows_mode<T, ROW_FIELD>(cols);
+  smem_rows_mode<T, ROW_TERMINAL>(cols);
+  smem_cols<T>(cols);
+  smem_adj<T>(adj);
+}
+
+template void launch_rows<float>(const RowArgs<float>&, int, int, size_t, cudaStream_t);
+template void launch_rows<double>(const RowArgs<double>&, int, int, size_t, cudaStream_t);
+template void set_smem_limits<float>(size_t, size_t, size_t);
+template void set_smem_limits<double>(size_t, size_t, size_t);
+
+}  // namespace llg

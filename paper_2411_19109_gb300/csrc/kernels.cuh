@@ -30,6 +30,8 @@ struct RowArgs {
   T* ckpt;            // copy of m_{n+1} (stage 4, nullable)
   double* slots;      // objective slots (nullable: do not accumulate)
   const long long* step_base;
+  int* err;           // error word (bounded waits that ran out)
+  const double* rf;   // per instance, per step: b_rf sin(2 pi f t) at t = n dt + c dt, c = 0, 1/2, 1
   int local_step;
   int stage;          // 1..4
   int rows_max;       // smem sizing: rows per tile
@@ -74,6 +76,7 @@ struct AdjArgs {
   const T* Bprev;
   T* BbarOut;
   const long long* step_base;
+  int* err;
   int local_step;
   int stage;          // 4..1
   int seed_only;      // 1: only form u_4, Bbar_4 of step n from lambda
@@ -89,8 +92,16 @@ template <typename T>
 void launch_cols(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
 template <typename T>
 void launch_adj(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+template <typename T, int MODE>
+void launch_rows_mode(const RowArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+template <typename T, int MODE>
+void smem_rows_mode(size_t smem);
 template <typename T>
-void set_smem_limits(size_t smem);
+void smem_cols(size_t smem);
+template <typename T>
+void smem_adj(size_t smem);
+template <typename T>
+void set_smem_limits(size_t rows, size_t cols, size_t adj);
 template <typename T>
 void launch_material_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* phi, T* psi,
                            T* dpsi, double* psisum, cudaStream_t st);

@@ -1,0 +1,163 @@
+// Register-resident FFTs for the demag convolution.
+//
+// A length-L transform (L = 2^m, 8 <= L <= 2048) is computed by TT = L/8
+// threads.  Thread t holds the eight elements x[t + TT*s], s = 0..7, on entry
+// and X[t + TT*s] on exit (the same "stride-TT" layout, so global loads and
+// stores of consecutive t are coalesced and no bit reversal is needed).
+// The schedule is Stockham's auto-sort: one radix-2 or radix-4 pass first
+// when m is not a multiple of 3, then radix-8 passes.  Between passes the
+// data goes through shared memory, where index i lives at i + i/8 (one pad
+// slot per eight) to spread the scattered writes over the banks; the last
+// pass leaves its output in registers.
+//
+// Twiddles W_L^k come from the FP64-computed table of W_4096^k.  DIR = -1 is
+// the forward transform, +1 the unnormalised inverse.
+#pragma once
+
+#include "common.cuh"
+
+namespace llg {
+
+__host__ __device__ constexpr int rf_pad(int i) { return i + (i >> 3); }
+__host__ __device__ constexpr int rf_padded_len(int L) { return L + (L >> 3); }
+
+template <typename C, int DIR>
+__device__ __forceinline__ C rf_tw(const C* __restrict__ tw, int m, int stride) {
+  C w = tw[m * stride];
+  if (DIR > 0) w.y = -w.y;
+  return w;
+}
+
+template <typename C, int DIR>
+__device__ __forceinline__ void rf_dft2(C& a, C& b) {
+  const C s = cadd(a, b), d = csub(a, b);
+  a = s;
+  b = d;
+}
+
+template <typename C, int DIR>
+__device__ __forceinline__ void rf_dft4(C& x0, C& x1, C& x2, C& x3) {
+  C a = cadd(x0, x2), b = csub(x0, x2);
+  C c = cadd(x1, x3), d = csub(x1, x3);
+  d = (DIR < 0) ? mul_mi(d) : mul_pi(d);
+  x0 = cadd(a, c);
+  x2 = csub(a, c);
+  x1 = cadd(b, d);
+  x3 = csub(b, d);
+}
+
+// 8-point DFT in place: x[k] <- sum_j x[j] W_8^{jk}
+template <typename C, int DIR>
+__device__ __forceinline__ void rf_dft8(C x[8]) {
+  using R = decltype(C::x);
+  const R h = (R)0.70710678118654752440;
+  C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+  C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+  rf_dft4<C, DIR>(e0, e1, e2, e3);
+  rf_dft4<C, DIR>(o0, o1, o2, o3);
+  // o_k *= W_8^k
+  if (DIR < 0) {
+    o1 = mk<C>(h * (o1.x + o1.y), h * (o1.y - o1.x));      // (1 - i)/sqrt2
+    o2 = mul_mi(o2);
+    o3 = mk<C>(h * (o3.y - o3.x), -h * (o3.x + o3.y));     // (-1 - i)/sqrt2
+  } else {
+    o1 = mk<C>(h * (o1.x - o1.y), h * (o1.x + o1.y));      // (1 + i)/sqrt2
+    o2 = mul_pi(o2);
+    o3 = mk<C>(-h * (o3.x + o3.y), h * (o3.x - o3.y));     // (-1 + i)/sqrt2
+  }
+  x[0] = cadd(e0, o0);
+  x[4] = csub(e0, o0);
+  x[1] = cadd(e1, o1);
+  x[5] = csub(e1, o1);
+  x[2] = cadd(e2, o2);
+  x[6] = csub(e2, o2);
+  x[3] = cadd(e3, o3);
+  x[7] = csub(e3, o3);
+}
+
+// One Stockham pass of radix RP on the eight registers of thread t.
+// Butterfly b of the thread is j = t + TT*b (b < 8/RP); its inputs are
+// v[b + r*(8/RP)], r < RP.  Returns the outputs in the same slots; `dst`
+// receives the shared-memory index of each slot's output.
+template <typename C, int L, int RP, int DIR>
+__device__ __forceinline__ void rf_pass(C v[8], int t, int Ns, const C* __restrict__ tw, int dst[8]) {
+  constexpr int TT = L / 8;
+  constexpr int NB = 8 / RP;
+  constexpr int tstride = kTwiddleN / L;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = t + TT * b;
+    const int k = j & (Ns - 1);
+    const int step = (L / (Ns * RP)) * k;         // twiddle W_L^{r*step}
+    C x[RP];
+#pragma unroll
+    for (int r = 0; r < RP; ++r) x[r] = v[b + r * NB];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < RP; ++r) x[r] = cmul(x[r], rf_tw<C, DIR>(tw, r * step, tstride));
+    }
+    if (RP == 2) {
+      rf_dft2<C, DIR>(x[0], x[1]);
+    } else if (RP == 4) {
+      rf_dft4<C, DIR>(x[0], x[1], x[2], x[3]);
+    } else {
+      rf_dft8<C, DIR>(x);
+    }
+    const int base = (j / Ns) * Ns * RP + k;
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+      v[b + r * NB] = x[r];
+      dst[b + r * NB] = base + r * Ns;
+    }
+  }
+}
+
+// Full transform of NCOMP sequences held by the same threads (v[c][8] for
+// c < NCOMP).  Element i of sequence c is exchanged through
+// sm[(c*sstride + pad(i)) * estride]: estride = 1 keeps each sequence
+// contiguous, estride = G interleaves G groups element by element (lanes of
+// consecutive groups then touch consecutive banks).  Every thread of the
+// block must call it (it synchronises the block between passes).
+template <typename C, int L, int DIR, int NCOMP>
+__device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int estride, int t,
+                                       const C* __restrict__ tw) {
+  constexpr int M = (L == 8) ? 3 : (L == 16) ? 4 : (L == 32) ? 5 : (L == 64) ? 6 : (L == 128) ? 7
+                  : (L == 256) ? 8 : (L == 512) ? 9 : (L == 1024) ? 10 : 11;
+  static_assert((1 << M) == L, "L must be a power of two in [8, 2048]");
+  constexpr int TT = L / 8;
+  constexpr int R0 = (M % 3 == 1) ? 2 : (M % 3 == 2) ? 4 : 8;
+  constexpr int NPASS = (M % 3 == 0) ? M / 3 : M / 3 + 1;
+  int dst[8];
+  int Ns = 1;
+#pragma unroll
+  for (int p = 0; p < NPASS; ++p) {
+    if (p > 0) {
+      // exchange: scattered write of the previous pass, then the strided read
+#pragma unroll
+      for (int c = 0; c < NCOMP; ++c)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) sm[(c * sstride + rf_pad(dst[s])) * estride] = v[c][s];
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < NCOMP; ++c)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) v[c][s] = sm[(c * sstride + rf_pad(t + TT * s)) * estride];
+      __syncthreads();
+    }
+    if (p == 0 && R0 == 2) {
+#pragma unroll
+      for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, 2, DIR>(v[c], t, Ns, tw, dst);
+      Ns *= 2;
+    } else if (p == 0 && R0 == 4) {
+#pragma unroll
+      for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, 4, DIR>(v[c], t, Ns, tw, dst);
+      Ns *= 4;
+    } else {
+#pragma unroll
+      for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, 8, DIR>(v[c], t, Ns, tw, dst);
+      Ns *= 8;
+    }
+  }
+}
+
+}  // namespace llg

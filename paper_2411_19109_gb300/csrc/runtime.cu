@@ -21,6 +21,7 @@
 
 #include "kernels.cuh"
 #include "llg.h"
+#include "regfft.cuh"
 
 using namespace llg;
 
@@ -88,6 +89,7 @@ struct llg_ctx {
   virtual size_t device_bytes() const = 0;
   virtual double last_ms() const = 0;
   virtual long long launches() const = 0;
+  virtual void kernel_time(int family, long long* count, double* ms) = 0;
 };
 
 template <typename T>
@@ -107,7 +109,8 @@ struct Engine final : llg_ctx {
   RowTile* dRT = nullptr;
   ColTile* dCT = nullptr;
   int R = 2, TX = 8;
-  size_t smem = 0;
+  size_t smem = 0, smem_rows = 0, smem_cols = 0, smem_adj = 0;
+  int* errw = nullptr;
   long long total_nodes = 0, total_spec = 0, total_tens = 0;
   long long K = 1, nckpt = 0, rec_steps = 0;
   std::vector<Action> fwd, rev;
@@ -118,7 +121,7 @@ struct Engine final : llg_ctx {
   T *psib = nullptr, *psic = nullptr;
   C *spec = nullptr, *tw = nullptr;
   double2* tw64 = nullptr;
-  double *slots = nullptr, *jterm = nullptr, *psisum = nullptr, *Jd = nullptr;
+  double *slots = nullptr, *jterm = nullptr, *psisum = nullptr, *Jd = nullptr, *rf = nullptr;
   long long* step_base = nullptr;
   unsigned int* maxbits = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -134,11 +137,62 @@ struct Engine final : llg_ctx {
     for (void* p : allocs) cudaFree(p);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    for (Timer& tm : timers)
+      for (cudaEvent_t e : tm.ev) cudaEventDestroy(e);
   }
 
   size_t device_bytes() const override { return bytes; }
   double last_ms() const override { return ms; }
   long long launches() const override { return nlaunch; }
+
+  // per-family event timing: pairs recorded around launches, drained after
+  // every synchronising API call
+  struct Timer {
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
+    long long count = 0;
+    double ms = 0.0;
+  };
+  Timer timers[3];
+  void time_begin(int fam) {
+    if (!opt.time_kernels) return;
+    Timer& tm = timers[fam];
+    if (tm.used + 2 > tm.ev.size()) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      tm.ev.push_back(a);
+      tm.ev.push_back(b);
+    }
+    cudaEventRecord(tm.ev[tm.used], st);
+  }
+  void time_end(int fam) {
+    if (!opt.time_kernels) return;
+    Timer& tm = timers[fam];
+    cudaEventRecord(tm.ev[tm.used + 1], st);
+    tm.used += 2;
+  }
+  void time_drain() {
+    for (Timer& tm : timers) {
+      for (size_t i = 0; i + 1 < tm.used; i += 2) {
+        float f = 0.f;
+        if (cudaEventElapsedTime(&f, tm.ev[i], tm.ev[i + 1]) == cudaSuccess) {
+          tm.ms += f;
+          tm.count += 1;
+        }
+      }
+      tm.used = 0;
+    }
+  }
+  void kernel_time(int family, long long* count, double* ms) override {
+    if (family < 0 || family > 2) {
+      if (count) *count = 0;
+      if (ms) *ms = 0.0;
+      return;
+    }
+    if (count) *count = timers[family].count;
+    if (ms) *ms = timers[family].ms;
+  }
 
   llg_status fail(llg_status s, const std::string& msg) {
     err = msg;
@@ -198,8 +252,8 @@ struct Engine final : llg_ctx {
       if (p.objective == LLG_J_PORT && (p.comp < 0 || p.comp > 2 || (p.power != 1 && p.power != 2)))
         return fail(LLG_EINVAL, "port objective needs comp in 0..2 and power 1 or 2");
       if (p.absorb_nodes < 0) return fail(LLG_EINVAL, "absorb_nodes must be >= 0");
-      const int Px = std::max(8, next_pow2(2 * p.nx));
-      const int Py = std::max(2, next_pow2(2 * p.ny));
+      const int Px = std::max(16, next_pow2(2 * p.nx));
+      const int Py = std::max(8, next_pow2(2 * p.ny));
       Lx_max = std::max(Lx_max, Px / 2);
       Py_max = std::max(Py_max, Py);
     }
@@ -208,18 +262,24 @@ struct Engine final : llg_ctx {
     if (opt.ckpt != LLG_CKPT_PERIODIC && opt.ckpt != LLG_CKPT_STORE_ALL)
       return fail(LLG_EINVAL, "ckpt must be LLG_CKPT_PERIODIC or LLG_CKPT_STORE_ALL");
 
-    // tile shapes: rows per row tile and complex columns per column tile,
-    // bounded by the shared memory of two ping-pong FFT buffers
-    const size_t cap = 200 * 1024;
-    R = opt.rows_per_cta > 0 ? opt.rows_per_cta : 2;
-    while (R > 1 && (size_t)2 * 3 * R * Lx_max * sizeof(C) > cap) --R;
-    if ((size_t)2 * 3 * R * Lx_max * sizeof(C) > cap) return fail(LLG_EINVAL, "row tile does not fit");
-    TX = opt.cols_per_cta > 0 ? opt.cols_per_cta : 8;
-    TX = next_pow2(TX);
-    while (TX > 1 && (size_t)2 * 3 * TX * (Py_max + 1) * sizeof(C) > cap) TX >>= 1;
-    if ((size_t)2 * 3 * TX * (Py_max + 1) * sizeof(C) > cap) return fail(LLG_EINVAL, "column tile does not fit");
-    smem = std::max((size_t)2 * 3 * R * Lx_max * sizeof(C), (size_t)2 * 3 * TX * (Py_max + 1) * sizeof(C));
-
+    // Tile shapes follow from the register FFTs: a row FFT of length Lx
+    // takes Lx/8 threads, so a 128-thread block covers 1024/Lx rows (at most
+    // 64); a column FFT of length Py takes Py/8 threads, so a block covers
+    // 1024/Py columns.  FFT exchange scratch is 3456 complex values.
+    R = 64;
+    TX = 0;
+    smem_cols = smem_adj = (size_t)3456 * sizeof(C);
+    smem_rows = smem_cols;
+    for (int i = 0; i < n; ++i) {
+      const int Lx = std::max(16, next_pow2(2 * P[i].nx)) / 2;
+      const size_t sb = (size_t)rows_per_tile(Lx) * 3 * rf_padded_len(Lx) * sizeof(C) +
+                        (size_t)(10 * rows_per_tile(Lx) + 8) * P[i].nx * sizeof(T);
+      smem_rows = std::max(smem_rows, sb);
+    }
+    smem = std::max(smem_rows, smem_cols);
+    if (smem_rows > 220 * 1024) return fail(LLG_EINVAL, "row tile does not fit in shared memory");
+    (void)Lx_max;
+    (void)Py_max;
     // descriptors, shapes, tiles
     struct Shape { int nx, ny; double dx, dy, dz; long long off; int Px, Py; };
     std::vector<Shape> shapes;
@@ -230,9 +290,9 @@ struct Engine final : llg_ctx {
       DevInst d;
       std::memset(&d, 0, sizeof d);
       d.nx = p.nx; d.ny = p.ny; d.nz = 1;
-      const int Px = std::max(8, next_pow2(2 * p.nx));
+      const int Px = std::max(16, next_pow2(2 * p.nx));
       d.Lx = Px / 2;
-      d.Py = std::max(2, next_pow2(2 * p.ny));
+      d.Py = std::max(8, next_pow2(2 * p.ny));
       d.log2Lx = ilog2(d.Lx);
       d.log2Py = ilog2(d.Py);
       int sid = -1;
@@ -253,6 +313,7 @@ struct Engine final : llg_ctx {
       d.spec_off = spec_off;
       spec_off += (long long)p.ny * 3 * d.Lx;
       d.slot_off = (long long)i * (N + 1);
+      d.rf_off = (long long)i * 3 * (N + 1);
       d.Ms = p.Ms;
       d.cex_x = 2.0 * p.A / (p.Ms * p.dx * p.dx);
       d.cex_y = 2.0 * p.A / (p.Ms * p.dy * p.dy);
@@ -293,9 +354,11 @@ struct Engine final : llg_ctx {
       d.area_target = p.area_target;
       d.penalty_w = p.penalty_w;
       H[i] = d;
-      for (int y0 = 0; y0 < p.ny; y0 += R) rt.push_back({i, y0, std::min(R, p.ny - y0), 0});
-      const int tx = std::min(TX, d.Lx);
+      const int rows = rows_per_tile(d.Lx);
+      for (int y0 = 0; y0 < p.ny; y0 += rows) rt.push_back({i, y0, std::min(rows, p.ny - y0), 0});
+      const int tx = std::max(1, std::min(1024 / d.Py, d.Lx));
       for (int k0 = 0; k0 < d.Lx; k0 += tx) ct.push_back({i, k0, tx, 0});
+      TX = std::max(TX, tx);
     }
     total_nodes = node_off;
     total_spec = spec_off;
@@ -322,7 +385,7 @@ struct Engine final : llg_ctx {
               alloc(&lam, S) && alloc(&G, S) && alloc(&gpart, S) && alloc(&bb[0], S) && alloc(&bb[1], S) &&
               alloc(&psib, total_nodes) && alloc(&psic, total_nodes) && alloc(&slots, (size_t)n * (N + 1)) &&
               alloc(&jterm, n) && alloc(&psisum, n) && alloc(&Jd, n) && alloc(&step_base, 1) &&
-              alloc(&maxbits, 2 * n);
+              alloc(&maxbits, 2 * n) && alloc(&rf, (size_t)n * 3 * (N + 1)) && alloc(&errw, 1);
     if (!ok) return fail(LLG_ENOMEM, "device allocation failed (" + std::to_string(bytes >> 20) + " MiB so far)");
 
     cudaError_t e;
@@ -350,6 +413,20 @@ struct Engine final : llg_ctx {
         return cuda_fail(e, "upload twiddles");
       if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "create");
     }
+    {
+      // RF drive per step and stage time t = n dt + c dt (c = 0, 1/2, 1), in FP64
+      std::vector<double> h((size_t)n * 3 * (N + 1));
+      for (int i = 0; i < n; ++i)
+        for (long long s = 0; s <= N; ++s)
+          for (int c = 0; c < 3; ++c) {
+            const double t = (double)s * dt + 0.5 * c * dt;
+            h[(size_t)i * 3 * (N + 1) + 3 * s + c] = P[i].b_rf * std::sin(2.0 * M_PI * P[i].f_rf * t);
+          }
+      if ((e = cudaMemcpyAsync(rf, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, st)) !=
+          cudaSuccess)
+        return cuda_fail(e, "upload RF table");
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "create");
+    }
     // demag spectra, FP64 scratch of the largest shape
     size_t gmax = 0;
     for (const Shape& s : shapes) gmax = std::max(gmax, (size_t)4 * s.Px * s.Py);
@@ -369,7 +446,8 @@ struct Engine final : llg_ctx {
     e = cudaStreamSynchronize(st);
     cudaFree(Gs);
     if (e != cudaSuccess) return cuda_fail(e, "demag tensor");
-    set_smem_limits<T>(smem);
+    set_smem_limits<T>(smem_rows, smem_cols, smem_adj);
+    cudaMemsetAsync(errw, 0, sizeof(int), st);
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "create");
@@ -386,6 +464,8 @@ struct Engine final : llg_ctx {
     a.tw = tw;
     a.psi = psi;
     a.step_base = step_base;
+    a.err = errw;
+    a.rf = rf;
     a.rows_max = R;
     a.dt = dt;
     a.n_from = n_from;
@@ -393,7 +473,9 @@ struct Engine final : llg_ctx {
     return a;
   }
   void rows(const RowArgs<T>& a, int mode) {
-    launch_rows<T>(a, mode, (int)rt.size(), smem, st);
+    if (mode == ROW_STAGE) time_begin(0);
+    launch_rows<T>(a, mode, (int)rt.size(), mode == ROW_STAGE ? smem_rows : smem_cols, st);
+    if (mode == ROW_STAGE) time_end(0);
     ++nlaunch;
   }
   void cols() {
@@ -404,7 +486,9 @@ struct Engine final : llg_ctx {
     c.tw = tw;
     c.tens = tens;
     c.cols_max = TX;
-    launch_cols<T>(c, (int)ct.size(), smem, st);
+    time_begin(1);
+    launch_cols<T>(c, (int)ct.size(), smem_cols, st);
+    time_end(1);
     ++nlaunch;
   }
   void set_step(long long v) {
@@ -492,9 +576,13 @@ struct Engine final : llg_ctx {
     if (mT) cudaMemcpyAsync(mT, cur, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
     cudaEventRecord(ev1, st);
     cudaMemcpyAsync(J, Jd, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    int herr = 0;
+    cudaMemcpyAsync(&herr, errw, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "llg_forward");
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "llg_forward");
+    time_drain();
+    if (herr) return fail(LLG_ETIMEOUT, "a bounded device wait ran out in llg_forward");
     float f = 0.f;
     cudaEventElapsedTime(&f, ev0, ev1);
     ms = f;
@@ -519,13 +607,16 @@ struct Engine final : llg_ctx {
     a.psib = psib;
     a.psic = psic;
     a.step_base = step_base;
+    a.err = errw;
     a.rows_max = R;
     a.dt = dt;
     a.n_from = n_from;
     return a;
   }
   void adj(const AdjArgs<T>& a) {
-    launch_adj<T>(a, (int)rt.size(), smem, st);
+    time_begin(2);
+    launch_adj<T>(a, (int)rt.size(), smem_adj, st);
+    time_end(2);
     ++nlaunch;
   }
 
@@ -582,9 +673,13 @@ struct Engine final : llg_ctx {
     ++nlaunch;
     if (dm0) cudaMemcpyAsync(dm0, lam, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
     cudaEventRecord(ev1, st);
+    int herr = 0;
+    cudaMemcpyAsync(&herr, errw, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "llg_adjoint");
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "llg_adjoint");
+    time_drain();
+    if (herr) return fail(LLG_ETIMEOUT, "a bounded device wait ran out in llg_adjoint");
     float f = 0.f;
     cudaEventElapsedTime(&f, ev0, ev1);
     ms = f;
@@ -605,6 +700,7 @@ struct Engine final : llg_ctx {
 
   llg_status field(const void* phi, const void* mv, double t, int demag_only, void* B) override {
     if (!phi || !mv || !B) return fail(LLG_EINVAL, "phi, m and B must not be NULL");
+    if (((uintptr_t)mv | (uintptr_t)B) % 16 != 0) return fail(LLG_EINVAL, "m and B must be 16-byte aligned");
     have_fwd = false;
     material(static_cast<const T*>(phi));
     fft_only(static_cast<const T*>(mv));
@@ -685,6 +781,12 @@ llg_status llg_query(llg_ctx* ctx, size_t* device_bytes, double* last_ms) {
 
 long long llg_launch_count(llg_ctx* ctx) { return ctx ? ctx->launches() : 0; }
 
+llg_status llg_kernel_time(llg_ctx* ctx, int family, long long* launches, double* total_ms) {
+  if (!ctx || family < 0 || family > 2) return LLG_EINVAL;
+  ctx->kernel_time(family, launches, total_ms);
+  return LLG_OK;
+}
+
 const char* llg_last_error(llg_ctx* ctx) {
   if (!ctx) return "null context";
   return ctx->err.c_str();
@@ -717,8 +819,8 @@ long long llg_schedule(long long nsteps, int ckpt, int seg_len, long long* actio
 
 int llg_padded_extents(int nx, int ny, int* Px, int* Py) {
   if (nx < 1 || ny < 1) return -1;
-  if (Px) *Px = std::max(8, next_pow2(2 * nx));
-  if (Py) *Py = std::max(2, next_pow2(2 * ny));
+  if (Px) *Px = std::max(16, next_pow2(2 * nx));
+  if (Py) *Py = std::max(8, next_pow2(2 * ny));
   return 0;
 }
 

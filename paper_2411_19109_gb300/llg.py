@@ -26,7 +26,7 @@ LLG_FP32, LLG_FP64 = 0, 1
 LLG_CKPT_STORE_ALL, LLG_CKPT_PERIODIC = 0, 1
 
 EXPORTED = ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query",
-            "llg_launch_count", "llg_last_error", "llg_destroy", "llg_schedule",
+            "llg_launch_count", "llg_kernel_time", "llg_last_error", "llg_destroy", "llg_schedule",
             "llg_padded_extents", "llg_abi_version")
 
 
@@ -46,7 +46,7 @@ class llg_problem(ctypes.Structure):
 
 class llg_options(ctypes.Structure):
     _fields_ = [("precision", c_int), ("ckpt", c_int), ("seg_len", c_int), ("use_graph", c_int),
-                ("rows_per_cta", c_int), ("cols_per_cta", c_int)]
+                ("rows_per_cta", c_int), ("cols_per_cta", c_int), ("time_kernels", c_int)]
 
 
 class LLGError(RuntimeError):
@@ -81,6 +81,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.llg_query.argtypes = [c_void_p, P(ctypes.c_size_t), P(c_double)]
     lib.llg_launch_count.argtypes = [c_void_p]
     lib.llg_launch_count.restype = c_ll
+    lib.llg_kernel_time.argtypes = [c_void_p, c_int, P(c_ll), P(c_double)]
+    lib.llg_kernel_time.restype = c_int
     lib.llg_last_error.argtypes = [c_void_p]
     lib.llg_last_error.restype = ctypes.c_char_p
     lib.llg_destroy.argtypes = [c_void_p]
@@ -127,10 +129,10 @@ def _check(lib, ctx, st):
 # ---- thin wrappers with the C names -------------------------------------
 
 def llg_create(problems: Sequence, precision=LLG_FP32, ckpt=LLG_CKPT_PERIODIC, seg_len=0,
-               stream=0, rows_per_cta=0, cols_per_cta=0, use_graph=0) -> int:
+               stream=0, rows_per_cta=0, cols_per_cta=0, use_graph=0, time_kernels=0) -> int:
     lib = load()
     arr = (llg_problem * len(problems))(*[to_struct(p) for p in problems])
-    opt = llg_options(precision, ckpt, seg_len, use_graph, rows_per_cta, cols_per_cta)
+    opt = llg_options(precision, ckpt, seg_len, use_graph, rows_per_cta, cols_per_cta, time_kernels)
     ctx = c_void_p()
     st = lib.llg_create(arr, len(problems), ctypes.byref(opt), c_void_p(stream), ctypes.byref(ctx))
     if st != LLG_OK:
@@ -178,6 +180,15 @@ def llg_launch_count(ctx: int) -> int:
     return load().llg_launch_count(c_void_p(ctx))
 
 
+def llg_kernel_time(ctx: int, family: int):
+    """(launches, total_ms) of a kernel family: 0 row stage, 1 column, 2 adjoint."""
+    lib = load()
+    n = c_ll()
+    ms = c_double()
+    _check(lib, ctx, lib.llg_kernel_time(c_void_p(ctx), family, ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
 def llg_last_error(ctx: int) -> str:
     return load().llg_last_error(c_void_p(ctx)).decode()
 
@@ -213,7 +224,8 @@ class Solver:
     [sum 3 n_i] with each instance laid out [3][ny][nx])."""
 
     def __init__(self, problems: Sequence, precision: str = "fp32", ckpt: str = "periodic",
-                 seg_len: int = 0, stream=None, rows_per_cta: int = 0, cols_per_cta: int = 0):
+                 seg_len: int = 0, stream=None, rows_per_cta: int = 0, cols_per_cta: int = 0,
+                 time_kernels: bool = False):
         import torch
         self.torch = torch
         self.problems = list(problems)
@@ -222,7 +234,7 @@ class Solver:
         ck = LLG_CKPT_PERIODIC if ckpt == "periodic" else LLG_CKPT_STORE_ALL
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ctx = llg_create(self.problems, prec, ck, seg_len, self.stream.cuda_stream,
-                              rows_per_cta, cols_per_cta)
+                              rows_per_cta, cols_per_cta, 0, int(time_kernels))
         self.nodes = [p.nx * p.ny * p.nz for p in self.problems]
         self.total = sum(self.nodes)
 
@@ -296,6 +308,9 @@ class Solver:
 
     def launch_count(self) -> int:
         return llg_launch_count(self.ctx)
+
+    def kernel_time(self, family: int):
+        return llg_kernel_time(self.ctx, family)
 
 
 def _make_function():
