@@ -1,0 +1,73 @@
+"""Host-only checks of the C ABI library (no GPU needed): it builds, loads,
+exports every function include/*.h declares, and its host-side integer
+artefacts (checkpoint action lists, padded extents) agree bit for bit with
+the oracle's independent generators."""
+import glob
+import os
+import re
+
+import pytest
+
+from oracle import schedule as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:llg_status|long long|int|void|const char\s*\*)\s*\**\s*(\w+)\s*\(",
+                             text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2411_19109_gb300 import load
+    return load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_function(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_binding_names_match_the_c_names():
+    import paper_2411_19109_gb300 as pkg
+    from paper_2411_19109_gb300 import llg
+    for name in declared_functions() - {"llg_abi_version"}:
+        assert hasattr(llg, name), f"binding lacks {name}"
+    assert set(llg.EXPORTED) <= declared_functions()
+    assert callable(pkg.llg_forward)
+
+
+@pytest.mark.parametrize("N,seg", [(1, 0), (2, 0), (17, 0), (100, 0), (101, 3), (20000, 0), (10000, 0),
+                                   (50, 50), (50, 80), (9, 1)])
+def test_schedule_matches_oracle(lib, N, seg):
+    from paper_2411_19109_gb300 import LLG_CKPT_PERIODIC, LLG_CKPT_STORE_ALL, llg_schedule
+    assert llg_schedule(N, LLG_CKPT_PERIODIC, seg) == S.periodic(N, seg)
+    assert llg_schedule(N, LLG_CKPT_STORE_ALL, 0) == S.store_all(N)
+
+
+def test_padded_extents(lib):
+    from paper_2411_19109_gb300 import llg_padded_extents
+    for nx, ny in [(4, 1), (32, 32), (36, 20), (128, 64), (512, 128), (1024, 512)]:
+        px, py = llg_padded_extents(nx, ny)
+        # linear (non-circular) convolution needs P >= 2N - 1; powers of two
+        assert px >= 2 * nx - 1 and py >= 2 * ny - 1
+        assert px & (px - 1) == 0 and py & (py - 1) == 0
+
+
+def test_schedule_rejects_bad_arguments(lib):
+    from paper_2411_19109_gb300 import LLGError, llg_schedule
+    with pytest.raises(LLGError):
+        llg_schedule(-1)
