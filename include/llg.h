@@ -153,6 +153,30 @@ llg_status llg_kernel_time(llg_ctx* ctx, int family, long long* launches, double
 const char* llg_last_error(llg_ctx* ctx);
 void llg_destroy(llg_ctx* ctx);
 
+/* Effective field of one FP32 instance without any device allocation.
+ * There is no counterpart in the paper: this entry point exists for callers
+ * that must not allocate device memory where they need a field evaluation,
+ * e.g. during CUDA stream capture (cudaMalloc is not allowed there), inside a
+ * host framework that owns all device memory, or in a latency-critical loop
+ * where cudaMalloc/cudaFree would synchronise other streams.
+ * Same result as llg_field (same kernels) for a single instance, FP32 only.
+ * prob: the instance (nsteps, objective fields are ignored); phi_dev [ny*nx],
+ * m_dev [3][ny][nx] and B_dev [3][ny][nx] are caller-owned float device
+ * buffers (m_dev and B_dev 16-byte aligned); cuda_stream is a cudaStream_t
+ * (NULL = default stream); the work is queued asynchronously on it.
+ * Scratch: one fixed device array of about 5.3 MB inside this library, held
+ * by every GPU that loads the library until the process exits.  It limits the
+ * grid to nz == 1, nx a multiple of 4 with 4 <= nx <= 128 and 1 <= ny <= 128;
+ * larger grids return LLG_EINVAL.  No cudaMalloc, cudaFree or allocating
+ * library call is made.  The first call on a device (with that device
+ * current) looks up the array's device address and uploads constant tables,
+ * synchronously: make that first call before any stream capture.  All calls
+ * on a device share the array and leave their contents in it; calls that
+ * overlap on the GPU (different streams, no ordering) race with each other.
+ * On error *err_msg (if non-NULL) points to a static description. */
+llg_status llg_field_noalloc(const llg_problem* prob, const void* phi_dev, const void* m_dev, double t,
+                             int demag_only, void* B_dev, void* cuda_stream, const char** err_msg);
+
 /* Host-only: the checkpoint action list the library executes.  Writes up to
  * max_actions triples (op, a, b) to `actions` (forward actions first, then
  * reverse), sets *n_forward to the number of forward actions and returns the

@@ -1,0 +1,244 @@
+// llg_field_noalloc: the effective-field evaluation of llg_field for one
+// FP32 instance, with every scratch buffer in a fixed device array of this
+// file instead of memory obtained from the CUDA allocator.
+//
+// Who needs it: code that must not allocate device memory at the point
+// where it wants a field evaluation -- for example while a stream is being
+// captured into a CUDA graph (cudaMalloc may not be called during capture),
+// inside a host application or framework that owns all device memory through
+// its own allocator, or in a latency-critical loop where the implicit
+// synchronisation of cudaMalloc/cudaFree would stall other streams.  The
+// caller still provides phi, m and the output B.
+//
+// The scratch below (about 5.3 MB) is a static __device__ object: every GPU
+// that loads this library holds it until the process exits.  It bounds the
+// grid to NA_MAX_N x NA_MAX_N nodes.  In host code the array's name is only a
+// host-side stand-in; its device address is looked up with
+// cudaGetSymbolAddress once per device (on the first call made with that
+// device current) and carved into the buffers the kernels use.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "kernels.cuh"
+#include "llg.h"
+
+using namespace llg;
+
+namespace {
+
+constexpr int NA_MAX_N = 128;                  // max nx and ny
+constexpr int NA_PX = 2 * NA_MAX_N;            // padded extents at the maximum
+constexpr int NA_PY = 2 * NA_MAX_N;
+constexpr int NA_LX = NA_PX / 2;
+constexpr int NA_MAX_ROW_TILES = NA_MAX_N;     // at most one row tile per row
+constexpr int NA_MAX_COL_TILES = NA_LX;        // at most one column tile per column
+
+constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// region sizes in bytes
+constexpr size_t SZ_G = align256(sizeof(double2) * 4 * NA_PX * NA_PY);                     // FP64 tensor grid
+constexpr size_t SZ_TENS = align256(sizeof(float) * 4 * (NA_PX / 2 + 1) * (NA_PY / 2 + 1));  // tensor spectrum
+constexpr size_t SZ_SPEC = align256(sizeof(float2) * 3 * NA_MAX_N * NA_LX);                  // row spectra
+constexpr size_t SZ_PSI = align256(sizeof(float) * NA_MAX_N * NA_MAX_N);                     // psi, dpsi
+constexpr size_t SZ_TW = align256(sizeof(float2) * kTwiddleN);
+constexpr size_t SZ_TW64 = align256(sizeof(double2) * kTwiddleN);
+constexpr size_t SZ_INST = align256(sizeof(DevInst));
+constexpr size_t SZ_RT = align256(sizeof(RowTile) * NA_MAX_ROW_TILES);
+constexpr size_t SZ_CT = align256(sizeof(ColTile) * NA_MAX_COL_TILES);
+constexpr size_t SZ_SUM = 256;                                                                // psi sum (double)
+
+constexpr size_t OFF_G = 0;
+constexpr size_t OFF_TENS = OFF_G + SZ_G;
+constexpr size_t OFF_SPEC = OFF_TENS + SZ_TENS;
+constexpr size_t OFF_PSI = OFF_SPEC + SZ_SPEC;
+constexpr size_t OFF_DPSI = OFF_PSI + SZ_PSI;
+constexpr size_t OFF_TW = OFF_DPSI + SZ_PSI;
+constexpr size_t OFF_TW64 = OFF_TW + SZ_TW;
+constexpr size_t OFF_INST = OFF_TW64 + SZ_TW64;
+constexpr size_t OFF_RT = OFF_INST + SZ_INST;
+constexpr size_t OFF_CT = OFF_RT + SZ_RT;
+constexpr size_t OFF_SUM = OFF_CT + SZ_CT;
+constexpr size_t NA_BYTES = OFF_SUM + SZ_SUM;
+
+// The scratch array itself.  Shared by every call on a device; it keeps the
+// contents of the last call.
+static __device__ __align__(256) unsigned char g_field_scratch[NA_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+unsigned char* g_scratch_dev[kMaxDevices] = {};   // device address of g_field_scratch per device
+
+int pow2_at_least(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+int log2_of(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+// Once per device, with that device current: resolve the array's device
+// address and fill the twiddle tables (which never change afterwards).
+llg_status setup_device(int dev, unsigned char** base, const char** msg) {
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (g_scratch_dev[dev]) {
+    *base = g_scratch_dev[dev];
+    return LLG_OK;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_field_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    if (msg) *msg = "llg_field_noalloc: cudaGetSymbolAddress of the scratch array failed";
+    return LLG_ECUDA;
+  }
+  unsigned char* b = static_cast<unsigned char*>(p);
+  static float2 htw[kTwiddleN];
+  static double2 htw64[kTwiddleN];
+  for (int k = 0; k < kTwiddleN; ++k) {
+    const double ang = -2.0 * M_PI * (double)k / (double)kTwiddleN;
+    htw64[k] = make_double2(std::cos(ang), std::sin(ang));
+    htw[k] = make_float2((float)htw64[k].x, (float)htw64[k].y);
+  }
+  if (cudaMemcpy(b + OFF_TW, htw, sizeof(htw), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b + OFF_TW64, htw64, sizeof(htw64), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (msg) *msg = "llg_field_noalloc: uploading the twiddle tables failed";
+    return LLG_ECUDA;
+  }
+  g_scratch_dev[dev] = b;
+  *base = b;
+  return LLG_OK;
+}
+
+}  // namespace
+
+extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi_dev, const void* m_dev,
+                                        double t, int demag_only, void* B_dev, void* cuda_stream,
+                                        const char** err_msg) {
+  if (err_msg) *err_msg = "";
+  if (!prob || !phi_dev || !m_dev || !B_dev) {
+    if (err_msg) *err_msg = "llg_field_noalloc: prob, phi, m and B must not be NULL";
+    return LLG_EINVAL;
+  }
+  const llg_problem& p = *prob;
+  if (p.nz != 1 || p.nx < 4 || p.nx % 4 != 0 || p.nx > NA_MAX_N || p.ny < 1 || p.ny > NA_MAX_N) {
+    if (err_msg)
+      *err_msg = "llg_field_noalloc: grid exceeds the fixed scratch (needs nz == 1, nx a multiple of 4 "
+                 "with 4 <= nx <= 128, 1 <= ny <= 128)";
+    return LLG_EINVAL;
+  }
+  if (!(p.dx > 0 && p.dy > 0 && p.dz > 0 && p.Ms > 0 && p.A >= 0)) {
+    if (err_msg) *err_msg = "llg_field_noalloc: dx, dy, dz, Ms must be > 0 and A >= 0";
+    return LLG_EINVAL;
+  }
+  if ((((uintptr_t)m_dev) | ((uintptr_t)B_dev)) % 16 != 0) {
+    if (err_msg) *err_msg = "llg_field_noalloc: m and B must be 16-byte aligned";
+    return LLG_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (err_msg) *err_msg = "llg_field_noalloc: no usable current device";
+    return LLG_ECUDA;
+  }
+  unsigned char* base = nullptr;
+  llg_status s = setup_device(dev, &base, err_msg);
+  if (s != LLG_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+  // descriptor and work tiles of this call (same layout rules as llg_create)
+  const int Px = std::max(16, pow2_at_least(2 * p.nx));
+  const int Py = std::max(8, pow2_at_least(2 * p.ny));
+  DevInst d;
+  std::memset(&d, 0, sizeof d);
+  d.nx = p.nx; d.ny = p.ny; d.nz = 1;
+  d.Lx = Px / 2; d.Py = Py;
+  d.log2Lx = log2_of(d.Lx); d.log2Py = log2_of(Py);
+  d.nodes = (long long)p.nx * p.ny;
+  d.Ms = p.Ms;
+  d.cex_x = 2.0 * p.A / (p.Ms * p.dx * p.dx);
+  d.cex_y = 2.0 * p.A / (p.Ms * p.dy * p.dy);
+  d.cex_z = 2.0 * p.A / (p.Ms * p.dz * p.dz);
+  d.kan = 2.0 * p.Ku / p.Ms;
+  const double kn = std::sqrt(p.ku[0] * p.ku[0] + p.ku[1] * p.ku[1] + p.ku[2] * p.ku[2]);
+  for (int c = 0; c < 3; ++c) {
+    d.ku[c] = kn > 0 ? p.ku[c] / kn : 0.0;
+    d.B_bias[c] = p.B_bias[c];
+    d.rf_dir[c] = p.rf_dir[c];
+  }
+  for (int c = 0; c < 4; ++c) d.src[c] = p.src[c];
+  d.b_rf = p.b_rf;
+  d.f_rf = p.f_rf;
+  d.sigmoid_a = p.sigmoid_a;
+  d.alpha = p.alpha;
+  d.alpha_edge = p.alpha_edge;
+  d.absorb_nodes = p.absorb_nodes;
+  d.absorb_x = p.absorb_x;
+  d.absorb_y = p.absorb_y;
+  d.V = p.dx * p.dy * p.dz;
+  RowTile rt[NA_MAX_ROW_TILES];
+  ColTile ct[NA_MAX_COL_TILES];
+  int nrt = 0, nct = 0;
+  const int rows = rows_per_tile(d.Lx);
+  for (int y0 = 0; y0 < p.ny; y0 += rows) rt[nrt++] = {0, y0, std::min(rows, p.ny - y0), 0};
+  const int tx = std::max(1, std::min(1024 / Py, d.Lx));
+  for (int k0 = 0; k0 < d.Lx; k0 += tx) ct[nct++] = {0, k0, tx, 0};
+
+  DevInst* dI = reinterpret_cast<DevInst*>(base + OFF_INST);
+  RowTile* dRT = reinterpret_cast<RowTile*>(base + OFF_RT);
+  ColTile* dCT = reinterpret_cast<ColTile*>(base + OFF_CT);
+  float* tens = reinterpret_cast<float*>(base + OFF_TENS);
+  float2* spec = reinterpret_cast<float2*>(base + OFF_SPEC);
+  float* psi = reinterpret_cast<float*>(base + OFF_PSI);
+  float* dpsi = reinterpret_cast<float*>(base + OFF_DPSI);
+  double* psisum = reinterpret_cast<double*>(base + OFF_SUM);
+  double2* G = reinterpret_cast<double2*>(base + OFF_G);
+  const float2* tw = reinterpret_cast<const float2*>(base + OFF_TW);
+  const double2* tw64 = reinterpret_cast<const double2*>(base + OFF_TW64);
+
+  cudaError_t e = cudaMemcpyAsync(dI, &d, sizeof d, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dRT, rt, sizeof(RowTile) * nrt, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dCT, ct, sizeof(ColTile) * nct, cudaMemcpyHostToDevice, st);
+  // the demag spectrum of this grid, FP64 on the device (G is cleared inside)
+  if (e == cudaSuccess)
+    e = build_tensor_spectrum<float>(tens, G, p.nx, p.ny, Px, Py, p.dx, p.dy, p.dz, tw64, st);
+  // psi from phi; the psi sum starts at zero
+  if (e == cudaSuccess) e = cudaMemsetAsync(psisum, 0, sizeof(double), st);
+  if (e != cudaSuccess) {
+    if (err_msg) *err_msg = "llg_field_noalloc: set-up copies or tensor build failed";
+    return LLG_ECUDA;
+  }
+  launch_material_tiles<float>(dI, dRT, nrt, static_cast<const float*>(phi_dev), psi, dpsi, psisum, st);
+
+  RowArgs<float> a;
+  std::memset(&a, 0, sizeof a);
+  a.inst = dI;
+  a.tiles = dRT;
+  a.spec = spec;
+  a.tw = tw;
+  a.psi = psi;
+  a.Yin = static_cast<const float*>(m_dev);
+  const size_t smem = (size_t)3456 * sizeof(float2);
+  launch_rows<float>(a, ROW_FFT_ONLY, nrt, smem, st);
+  ColArgs<float> c;
+  c.inst = dI;
+  c.tiles = dCT;
+  c.spec = spec;
+  c.tw = tw;
+  c.tens = tens;
+  c.cols_max = tx;
+  launch_cols<float>(c, nct, smem, st);
+  a.Bout = static_cast<float*>(B_dev);
+  a.t_field = t;
+  a.demag_only = demag_only;
+  launch_rows<float>(a, ROW_FIELD, nrt, smem, st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    if (err_msg) *err_msg = "llg_field_noalloc: kernel launch failed";
+    return LLG_ECUDA;
+  }
+  return LLG_OK;
+}

@@ -27,7 +27,7 @@ LLG_CKPT_STORE_ALL, LLG_CKPT_PERIODIC = 0, 1
 
 EXPORTED = ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query",
             "llg_launch_count", "llg_kernel_time", "llg_last_error", "llg_destroy", "llg_schedule",
-            "llg_padded_extents", "llg_abi_version")
+            "llg_padded_extents", "llg_abi_version", "llg_field_noalloc")
 
 
 class llg_problem(ctypes.Structure):
@@ -91,6 +91,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.llg_schedule.restype = c_ll
     lib.llg_padded_extents.argtypes = [c_int, c_int, P(c_int), P(c_int)]
     lib.llg_abi_version.restype = c_int
+    lib.llg_field_noalloc.argtypes = [P(llg_problem), c_void_p, c_void_p, c_double, c_int, c_void_p, c_void_p,
+                                      P(ctypes.c_char_p)]
+    lib.llg_field_noalloc.restype = c_int
     for f in ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query"):
         getattr(lib, f).restype = c_int
     _lib = lib
@@ -166,6 +169,19 @@ def llg_field(ctx: int, phi_ptr: int, m_ptr: int, t: float, demag_only: bool, B_
     lib = load()
     _check(lib, ctx, lib.llg_field(c_void_p(ctx), c_void_p(phi_ptr), c_void_p(m_ptr), t,
                                    int(bool(demag_only)), c_void_p(B_ptr)))
+
+
+def llg_field_noalloc(problem, phi_ptr: int, m_ptr: int, t: float, demag_only: bool, B_ptr: int,
+                      stream: int = 0) -> None:
+    """Field of one FP32 instance with the library's fixed scratch (no device
+    allocation; grids up to 128 x 128).  Queued on `stream`."""
+    lib = load()
+    s = to_struct(problem)
+    msg = ctypes.c_char_p()
+    st = lib.llg_field_noalloc(ctypes.byref(s), c_void_p(phi_ptr), c_void_p(m_ptr), t, int(bool(demag_only)),
+                               c_void_p(B_ptr), c_void_p(stream), ctypes.byref(msg))
+    if st != LLG_OK:
+        raise LLGError(st, msg.value.decode() if msg.value else "")
 
 
 def llg_query(ctx: int):
