@@ -52,11 +52,12 @@ struct DevInst {
   int Lx, Py;            // complex row FFT length (Px/2) and column FFT length
   int log2Lx, log2Py;
   int shape;             // index of the demag spectrum table
+  int ntile, tile_off;   // row tiles of this instance, index of its first row tile
   long long nodes;       // nx*ny*nz
   long long node_off;    // offset into node arrays (per component block: 3*nodes)
   long long spec_off;    // offset into the spectrum pool, complex elements
   long long tens_off;    // offset into the tensor pool, real elements
-  long long slot_off;    // offset into the per-step objective slots (nsteps+1)
+  long long slot_off;    // offset into the objective partials: (nsteps+1) x ntile
   long long rf_off;      // offset into the RF drive table (3 nsteps + 3 values)
   double Ms;
   double cex_x, cex_y, cex_z;   // 2A/(Ms h^2)
@@ -87,12 +88,35 @@ __device__ __forceinline__ void load_inst(DevInst& dst, const DevInst* src) {
   for (int i = threadIdx.x; i < (int)(sizeof(DevInst) / 4); i += blockDim.x) d[i] = s[i];
 }
 
-// Rows per row tile for a row FFT of length L: L/8 threads per row in a
-// 128-thread block (every thread then owns a row slot).
+// Rows per row tile for a row FFT of length L: 3 x L/8 threads per row in a
+// 384-thread block (every thread then owns a row slot).
 __host__ __device__ constexpr int rows_per_tile(int L) { return 1024 / L; }
 
-// Row tile: rows y0 .. y0+nrows-1 of instance `inst`.
-struct RowTile { int inst, y0, nrows, pad; };
+// FFT exchange scratch of every stage kernel, complex values: the row kernels
+// use R = 1024/L row slots x 3 components x (padded length rounded to even),
+// the column kernel 3 x 1024/L groups of (padded length + 1); both <= 3840.
+constexpr int kExch = 3840;
+
+// Dynamic shared memory of the stage and adjoint kernels for a row FFT of
+// length L on rows of nx nodes: exchange scratch, the staged halo rows (4
+// resp. 7 node arrays over R+2 rows), the staged pointwise rows (6 resp. 17
+// node arrays over R rows) and the W_{2L} table.
+template <typename T>
+__host__ __device__ constexpr size_t stage_smem_bytes(int L, int nx, bool pointwise) {
+  return (size_t)kExch * sizeof(cplx<T>) + (size_t)4 * (rows_per_tile(L) + 2) * nx * sizeof(T) +
+         (pointwise ? (size_t)6 * rows_per_tile(L) * nx * sizeof(T) : 0) + (size_t)2 * L * sizeof(cplx<T>);
+}
+template <typename T>
+__host__ __device__ constexpr size_t adj_smem_bytes(int L, int nx, bool pointwise) {
+  return (size_t)kExch * sizeof(cplx<T>) + (size_t)7 * (rows_per_tile(L) + 2) * nx * sizeof(T) +
+         (pointwise ? (size_t)17 * rows_per_tile(L) * nx * sizeof(T) : 0) + (size_t)2 * L * sizeof(cplx<T>);
+}
+
+
+// Row tile: rows y0 .. y0+nrows-1 of instance `inst`; k is the tile's index
+// within its instance (the slot of its partial sums, which are added in tile
+// order afterwards so that J does not depend on the order tiles finish).
+struct RowTile { int inst, y0, nrows, k; };
 // Column tile: complex columns kx0 .. kx0+ncols-1 of instance `inst`.
 struct ColTile { int inst, kx0, ncols, pad; };
 

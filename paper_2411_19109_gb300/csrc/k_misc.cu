@@ -3,17 +3,20 @@
 
 namespace llg {
 
-int rows_threads() { return 128; }
-int cols_threads() { return 128; }
-int adj_threads() { return 128; }
+int rows_threads() { return 384; }
+int cols_threads() { return 384; }
+int adj_threads() { return 384; }
 
 __global__ void set_step_kernel(long long* p, long long v) { *p = v; }
 
-// J_i = Kahan sum of the per-step slots + terminal term + area penalty
-__global__ void reduce_slots_kernel(const DevInst* inst, const double* slots, long long nslots,
-                                    const double* jterm, const double* psisum, double* J) {
+// J_i = Kahan sum of the per-(step, row tile) partials + terminal term + area
+// penalty on the mean of psi.  Every sum runs in a fixed order, so J is
+// reproducible bit for bit.
+__global__ void reduce_slots_kernel(const DevInst* inst, const double* slots, long long nsteps1,
+                                    const double* jterm, const double* psitile, double* J) {
   __shared__ double red[32];
   const DevInst& I = inst[blockIdx.x];
+  const long long nslots = nsteps1 * I.ntile;
   double sum = 0.0, comp = 0.0;
   for (long long k = threadIdx.x; k < nslots; k += blockDim.x) {
     const double y = slots[I.slot_off + k] - comp;
@@ -23,9 +26,13 @@ __global__ void reduce_slots_kernel(const DevInst* inst, const double* slots, lo
   }
   const double tot = block_sum(sum - comp, red);
   if (threadIdx.x == 0) {
-    double j = tot + jterm[blockIdx.x];
+    double j = tot, ps = 0.0;
+    for (int t = 0; t < I.ntile; ++t) {
+      j += jterm[I.tile_off + t];
+      ps += psitile[I.tile_off + t];
+    }
     if (I.objective == 1) {
-      const double f = psisum[blockIdx.x] / (double)I.nodes - I.area_target;
+      const double f = ps / (double)I.nodes - I.area_target;
       j += I.penalty_w * f * f;
     }
     J[blockIdx.x] = j;
@@ -36,9 +43,9 @@ void launch_set_step(long long* step_base, long long v, cudaStream_t st) {
   set_step_kernel<<<1, 1, 0, st>>>(step_base, v);
 }
 
-void launch_reduce_slots(const DevInst* inst, int n_inst, const double* slots, long long nslots,
-                         const double* jterm, const double* psisum, double* J, cudaStream_t st) {
-  reduce_slots_kernel<<<n_inst, 256, 0, st>>>(inst, slots, nslots, jterm, psisum, J);
+void launch_reduce_slots(const DevInst* inst, int n_inst, const double* slots, long long nsteps1,
+                         const double* jterm, const double* psitile, double* J, cudaStream_t st) {
+  reduce_slots_kernel<<<n_inst, 256, 0, st>>>(inst, slots, nsteps1, jterm, psitile, J);
 }
 
 template <typename T>
@@ -52,18 +59,18 @@ void launch_rows(const RowArgs<T>& a, int mode, int ntiles, size_t smem, cudaStr
 }
 
 template <typename T>
-void set_smem_limits(size_t rows, size_t cols, size_t adj) {
-  smem_rows_mode<T, ROW_FFT_ONLY>(cols);
-  smem_rows_mode<T, ROW_STAGE>(rows);
-  smem_rows_mode<T, ROW_FIELD>(cols);
-  smem_rows_mode<T, ROW_TERMINAL>(cols);
+void set_smem_limits(size_t stage, size_t misc, size_t cols, size_t adj) {
+  smem_rows_mode<T, ROW_FFT_ONLY>(misc);
+  smem_rows_mode<T, ROW_STAGE>(stage);
+  smem_rows_mode<T, ROW_FIELD>(misc);
+  smem_rows_mode<T, ROW_TERMINAL>(misc);
   smem_cols<T>(cols);
   smem_adj<T>(adj);
 }
 
 template void launch_rows<float>(const RowArgs<float>&, int, int, size_t, cudaStream_t);
 template void launch_rows<double>(const RowArgs<double>&, int, int, size_t, cudaStream_t);
-template void set_smem_limits<float>(size_t, size_t, size_t);
-template void set_smem_limits<double>(size_t, size_t, size_t);
+template void set_smem_limits<float>(size_t, size_t, size_t, size_t);
+template void set_smem_limits<double>(size_t, size_t, size_t, size_t);
 
 }  // namespace llg

@@ -34,6 +34,7 @@ struct RowArgs {
   const double* rf;   // per instance, per step: b_rf sin(2 pi f t) at t = n dt + c dt, c = 0, 1/2, 1
   int local_step;
   int stage;          // 1..4
+  int stage_pw;       // ROW_STAGE: also stage m_n and the accumulator in shared memory
   int rows_max;       // smem sizing: rows per tile
   int demag_only;     // ROW_FIELD
   double t_field;     // ROW_FIELD time
@@ -43,8 +44,8 @@ struct RowArgs {
   T* lam;             // lambda_N
   T* psib;            // dJ/dpsi accumulator (sum)
   T* psic;            //                     (compensation)
-  double* jterm;      // per-instance terminal J
-  const double* psisum; // per-instance sum of psi
+  double* jterm;      // per-row-tile partial of the terminal J
+  const double* psitile; // per-row-tile partial sums of psi
   long long nsteps;
 };
 
@@ -81,6 +82,7 @@ struct AdjArgs {
   int stage;          // 4..1
   int seed_only;      // 1: only form u_4, Bbar_4 of step n from lambda
   int seed_next;      // stage 1: also seed step n-1 (Yprev/Bprev of its stage 4)
+  int stage_pw;       // also stage the pointwise rows in shared memory
   int rows_max;
   double dt;
   long long n_from;
@@ -101,10 +103,10 @@ void smem_cols(size_t smem);
 template <typename T>
 void smem_adj(size_t smem);
 template <typename T>
-void set_smem_limits(size_t rows, size_t cols, size_t adj);
+void set_smem_limits(size_t stage, size_t misc, size_t cols, size_t adj);
 template <typename T>
 void launch_material_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* phi, T* psi,
-                           T* dpsi, double* psisum, cudaStream_t st);
+                           T* dpsi, double* psitile, cudaStream_t st);
 template <typename T>
 void launch_grad_finish_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* dpsi,
                               const T* psib, const T* psic, T* out, cudaStream_t st);
@@ -113,7 +115,7 @@ void launch_levelset_tiles(const DevInst* inst, const RowTile* tiles, int ntiles
                            const unsigned char* mask, double lr, unsigned int* maxbits, cudaStream_t st);
 void launch_set_step(long long* step_base, long long v, cudaStream_t st);
 void launch_reduce_slots(const DevInst* inst, int n_inst, const double* slots, long long nslots,
-                         const double* jterm, const double* psisum, double* J, cudaStream_t st);
+                         const double* jterm, const double* psitile, double* J, cudaStream_t st);
 int rows_threads();
 int cols_threads();
 int adj_threads();

@@ -23,9 +23,9 @@
 
 namespace llg {
 
-constexpr int kRowThreads = 128;
-constexpr int kColThreads = 128;
-constexpr int kAdjThreads = 128;
+constexpr int kRowThreads = 384;   // 3 components x L/8 lanes x 1024/L rows
+constexpr int kColThreads = 384;   // 1024/L columns x 3 components x L/8 lanes
+constexpr int kAdjThreads = 384;
 
 
 
@@ -183,66 +183,104 @@ __device__ __forceinline__ void exchange_node(const PairNbr<T>& q, int i, T cx, 
 }
 
 template <typename C>
-__device__ __forceinline__ C unpack_one(const C* __restrict__ X, int kk, int L, const C* __restrict__ tw) {
-  // Z[k] = (X_k + conj X_{L-k}) + i W_P^{-k} (X_k - conj X_{L-k}),  P = 2L
+__device__ __forceinline__ C unpack_one(const C* __restrict__ X, int kk, int L, const C* __restrict__ tw2) {
+  // Z[k] = (X_k + conj X_{L-k}) + i W_P^{-k} (X_k - conj X_{L-k}),  P = 2L;  tw2[k] = W_P^k
   const C xk = X[kk];
   if (kk == 0) return mk<C>(xk.x + xk.y, xk.x - xk.y);
   const C xm = cconj(X[L - kk]);
-  C w = tw[kk * (kTwiddleN / (2 * L))];
+  C w = tw2[kk];
   w.y = -w.y;
   return cadd(cadd(xk, xm), mul_pi(cmul(w, csub(xk, xm))));
 }
 
 template <typename C>
-__device__ __forceinline__ C pack_one(C zk, C zm_conj, int kk, int L, const C* __restrict__ tw) {
-  // X[k] = (Z_k + conj Z_{L-k})/2 - i W_P^k (Z_k - conj Z_{L-k})/2
+__device__ __forceinline__ C pack_one(C zk, C zm_conj, int kk, const C* __restrict__ tw2) {
+  // X[k] = (Z_k + conj Z_{L-k})/2 - i W_P^k (Z_k - conj Z_{L-k})/2, X[0] = (Re+Im, Re-Im)
   using R = decltype(C::x);
   if (kk == 0) return mk<C>(zk.x + zk.y, zk.x - zk.y);
-  const C w = tw[kk * (kTwiddleN / (2 * L))];
+  const C w = tw2[kk];
   return cscale(cadd(cadd(zk, zm_conj), mul_mi(cmul(w, csub(zk, zm_conj)))), (R)0.5);
 }
 
-// Inverse row FFT of the three packed field spectra of one row into
-// v[c][s] = (F_c[2j], F_c[2j+1]), j = t + TT s.
-template <typename T, int L>
-__device__ __forceinline__ void row_inverse(cplx<T> (&v)[3][8], const cplx<T>* __restrict__ row, bool active,
-                                            cplx<T>* sm, int t, const cplx<T>* __restrict__ tw) {
-  using C = cplx<T>;
-  constexpr int TT = L / 8;
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int s = 0; s < 8; ++s)
-      v[c][s] = active ? unpack_one(row + c * L, t + TT * s, L, tw) : mk<C>((T)0, (T)0);
-  regfft<C, L, 1, 3>(v, sm, rf_padded_len(L), 1, t, tw);
+// One component's FFT: v[s] holds element t + (L/8)s of the sequence whose
+// element i is exchanged through grp[pad(i) * estride].
+template <typename C, int L, int DIR>
+__device__ __forceinline__ void fft1(C (&v)[8], C* grp, int estride, int t, const C* __restrict__ tw, int tws,
+                                     GroupSync sync) {
+  regfft<C, L, DIR, 1>(*reinterpret_cast<C(*)[1][8]>(&v), grp, 0, estride, t, tw, tws, sync);
 }
 
-// Forward row FFT of v[c][s] = (M_c[2j], M_c[2j+1]) and packed store.
-template <typename T, int L>
-__device__ __forceinline__ void row_forward(cplx<T> (&v)[3][8], cplx<T>* __restrict__ row, bool active,
-                                            cplx<T>* sm, int t, const cplx<T>* __restrict__ tw) {
-  using C = cplx<T>;
-  constexpr int TT = L / 8;
-  constexpr int SP = rf_padded_len(L);
-  regfft<C, L, -1, 3>(v, sm, SP, 1, t, tw);
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int s = 0; s < 8; ++s) sm[c * SP + rf_pad(t + TT * s)] = v[c][s];
-  __syncthreads();
-  if (!active) return;
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const int kk = t + TT * s;
-      const C zm = cconj(sm[c * SP + rf_pad((L - kk) & (L - 1))]);
-      row[c * L + kk] = pack_one(v[c][s], zm, kk, L, tw);
-    }
-}
+// Row-kernel group stride: the padded length rounded up to even, so that
+// every (row slot, component) sequence starts on a 16-byte boundary.
+__host__ __device__ constexpr int group_stride(int L) { return (rf_padded_len(L) + 1) & ~1; }
 
 // ---------------------------------------------------------------------------
-// column pass: FFT_y, product with the tensor spectrum, inverse FFT_y
+// Thread layout of the row-family kernels (stage, spectrum/field/terminal,
+// adjoint): a block of 384 threads covers R = 1024/L rows; thread tid works on
+// row slot rl = tid / (3 L/8), field component c = (tid / (L/8)) % 3 and FFT
+// lane t = tid % (L/8).  Each (row slot, component) group of L/8 consecutive
+// threads owns one padded sequence of the exchange scratch,
+// sE + (3 rl + c) * GS, and synchronises only within itself (warp or named
+// barrier).  After the inverse FFT the first half of every sequence (complex
+// slot j = nodes 2j, 2j+1) is left in natural order; the node phase (all
+// threads of the row slot, one node each in turn) reads the field there and
+// writes the next FFT's input into the same slots.
+// ---------------------------------------------------------------------------
+
+template <typename T, int L>
+__device__ __forceinline__ void row_inverse_comp(cplx<T> (&v)[8], const cplx<T>* __restrict__ X, bool active,
+                                                 cplx<T>* grp, int t, const cplx<T>* __restrict__ tw2) {
+  using C = cplx<T>;
+  constexpr int TT = L / 8;
+  const GroupSync gs = group_sync(TT);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) v[s] = active ? unpack_one(X, t + TT * s, L, tw2) : mk<C>((T)0, (T)0);
+  gs();
+  fft1<C, L, 1>(v, grp, 1, t, tw2, 2, gs);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) grp[rf_pad(t + TT * s)] = v[s];
+}
+
+// Forward FFT of the node-phase output left in grp (slots j < npairs), packed
+// store of the row spectrum component to `out`.
+template <typename T, int L>
+__device__ __forceinline__ void row_forward_comp(cplx<T>* grp, int npairs, cplx<T>* __restrict__ out, bool active,
+                                                 int t, const cplx<T>* __restrict__ tw2) {
+  using C = cplx<T>;
+  constexpr int TT = L / 8;
+  const GroupSync gs = group_sync(TT);
+  C v[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int j = t + TT * s;
+    v[s] = (s < 4 && j < npairs) ? grp[rf_pad(j)] : mk<C>((T)0, (T)0);
+  }
+  gs();
+  fft1<C, L, -1>(v, grp, 1, t, tw2, 2, gs);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) grp[rf_pad(t + TT * s)] = v[s];
+  gs();
+  if (!active) return;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int kk = t + TT * s;
+    const C zm = cconj(grp[rf_pad((L - kk) & (L - 1))]);
+    out[kk] = pack_one(v[s], zm, kk, tw2);
+  }
+}
+
+// Node x of a row slot's three sequences: complex slot x/2, real (x even) or
+// imaginary (x odd) part.
+template <typename T>
+__device__ __forceinline__ int node_slot(int x) { return 2 * rf_pad(x >> 1) + (x & 1); }
+
+// ---------------------------------------------------------------------------
+// column pass: FFT_y, product with the tensor spectrum, inverse FFT_y.
+// Block of 384 threads: 3 components x NC = 1024/L columns groups of L/8
+// lanes; group (c, col) owns smem + (c NC + col)(SP + 1) and synchronises
+// within itself.  The tile is loaded and stored through shared memory with
+// the column index fastest (coalesced); the twiddle table W_L^k, k < L,
+// follows the scratch.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ void load_tensor(const float* tab, long long idx, float n[4]) {
@@ -260,33 +298,39 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
                                           cplx<T>* smem) {
   using C = cplx<T>;
   constexpr int TT = L / 8;
-  constexpr int NC = (kColThreads / TT) > 0 ? kColThreads / TT : 1;   // columns per block
-  constexpr int SP = rf_padded_len(L);
+  constexpr int NC = 1024 / L;                     // columns per block
+  constexpr int GSC = rf_padded_len(L) + 1;        // group stride (odd: spreads banks)
   const int tid = threadIdx.x;
-  const int t = tid / NC, col = tid - t * NC;
-  const bool active = col < tile.ncols;
+  const int t = tid % TT, grp_id = tid / TT;       // group = (component, column)
+  const int c = grp_id / NC, col = grp_id % NC;
+  const int ncols = tile.ncols;
+  const bool active = col < ncols;
   const int kx = tile.kx0 + (active ? col : 0);
   const int Lx = I.Lx, ny = I.ny;
-  C* sm = smem + col;                    // element (c, i) of this column at sm[(c*SP + pad(i))*NC]
-  C* spec = a.spec + I.spec_off;
-  C v[3][8];
+  C* grp = smem + grp_id * GSC;
+  C* tw1 = smem + kExch;
+  C* spec = a.spec + I.spec_off + tile.kx0;
+  const GroupSync gs = group_sync(TT);
+  load_twiddles(tw1, a.tw, L);
+  // coalesced load of the tile (ny rows x 3 components x ncols) into the groups
+  for (int e = tid; e < ny * 3 * ncols; e += kColThreads) {
+    const int y = e / (3 * ncols), r = e - y * 3 * ncols;
+    const int cc = r / ncols, cl = r - cc * ncols;
+    smem[(cc * NC + cl) * GSC + rf_pad(y)] = spec[((long long)y * 3 + cc) * Lx + cl];
+  }
+  __syncthreads();
+  C v[8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int y = t + TT * s;
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      v[c][s] = (active && y < ny) ? spec[((long long)y * 3 + c) * Lx + kx] : mk<C>((T)0, (T)0);
+    v[s] = (active && y < ny) ? grp[rf_pad(y)] : mk<C>((T)0, (T)0);
   }
-  regfft<C, L, -1, 3>(v, sm, SP, NC, t, a.tw);
-  const bool dc_tile = tile.kx0 == 0;               // uniform over the block
-  if (dc_tile) {
-    if (col == 0)
+  gs();
+  fft1<C, L, -1>(v, grp, 1, t, tw1, 1, gs);
+  // publish every component at every ky for the 3x3 product
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int s = 0; s < 8; ++s) sm[(c * SP + rf_pad(t + TT * s)) * NC] = v[c][s];
-    __syncthreads();
-  }
+  for (int s = 0; s < 8; ++s) grp[rf_pad(t + TT * s)] = v[s];
+  __syncthreads();
   const T* tab = a.tens + I.tens_off;
   constexpr int nky = L / 2 + 1;
 #pragma unroll
@@ -298,10 +342,13 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
       T n[4];
       load_tensor(tab, (long long)kx * nky + kyf, n);
       const T nxy = lo ? n[3] : -n[3];
-      const C mx = v[0][s], my = v[1][s], mz = v[2][s];
-      v[0][s] = mk<C>(n[0] * mx.x + nxy * my.x, n[0] * mx.y + nxy * my.y);
-      v[1][s] = mk<C>(nxy * mx.x + n[1] * my.x, nxy * mx.y + n[1] * my.y);
-      v[2][s] = mk<C>(n[2] * mz.x, n[2] * mz.y);
+      if (c == 2) {
+        v[s] = cscale(v[s], n[2]);
+      } else {
+        const C other = smem[((1 - c) * NC + col) * GSC + rf_pad(ky)];   // the other in-plane component
+        const T diag = (c == 0) ? n[0] : n[1];
+        v[s] = mk<C>(diag * v[s].x + nxy * other.x, diag * v[s].y + nxy * other.y);
+      }
     } else {
       // packed DC (kx = 0) and Nyquist (kx = Px/2) columns: separate them by
       // Hermitian symmetry in ky, apply each its own (diagonal) tensor
@@ -309,23 +356,23 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
       load_tensor(tab, (long long)kyf, nd);
       load_tensor(tab, (long long)Lx * nky + kyf, nq);
       const int km = (L - ky) & (L - 1);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const T p = (T)0.5 * (nd[c] + nq[c]), q = (T)0.5 * (nd[c] - nq[c]);
-        const C vb = cconj(sm[(c * SP + rf_pad(km)) * NC]);
-        v[c][s] = cadd(cscale(v[c][s], p), cscale(vb, q));
-      }
+      const T p = (T)0.5 * (nd[c] + nq[c]), q = (T)0.5 * (nd[c] - nq[c]);
+      const C vb = cconj(grp[rf_pad(km)]);
+      v[s] = cadd(cscale(v[s], p), cscale(vb, q));
     }
   }
-  if (dc_tile) __syncthreads();
-  regfft<C, L, 1, 3>(v, sm, SP, NC, t, a.tw);
-  if (!active) return;
+  __syncthreads();
+  fft1<C, L, 1>(v, grp, 1, t, tw1, 1, gs);
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int y = t + TT * s;
-    if (y < ny)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) spec[((long long)y * 3 + c) * Lx + kx] = v[c][s];
+    if (y < ny) grp[rf_pad(y)] = v[s];
+  }
+  __syncthreads();
+  for (int e = tid; e < ny * 3 * ncols; e += kColThreads) {
+    const int y = e / (3 * ncols), r = e - y * 3 * ncols;
+    const int cc = r / ncols, cl = r - cc * ncols;
+    spec[((long long)y * 3 + cc) * Lx + cl] = smem[(cc * NC + cl) * GSC + rf_pad(y)];
   }
 }
 
@@ -352,230 +399,8 @@ __global__ void __launch_bounds__(kColThreads) cols_kernel(ColArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
-// row pass of the forward stage (and its variants)
+// staged halo rows
 // ---------------------------------------------------------------------------
-
-template <typename T, int L, int MODE>
-__device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I, const RowTile& tile,
-                                          cplx<T>* smem, double* red, T rf) {
-  using C = cplx<T>;
-  constexpr int TT = L / 8;
-  constexpr int SP = rf_padded_len(L);
-  const int tid = threadIdx.x;
-  const int rl = tid / TT, t = tid - rl * TT;
-  const bool active = rl < tile.nrows;
-  const int nx = I.nx, ny = I.ny;
-  const int y = tile.y0 + (active ? rl : 0);
-  const long long nodes = I.nodes;
-  C* sm = smem + rl * 3 * SP;
-  C* row = a.spec + I.spec_off + (long long)y * 3 * L;
-  const long long n = (a.step_base ? *a.step_base : 0) + a.local_step;
-  const int s = a.stage;
-  const long long off3 = 3 * I.node_off;
-  const T* __restrict__ Y = a.Yin + off3;
-  const T* __restrict__ ps = a.psi + I.node_off;
-  const T Ms = (T)I.Ms, cx = (T)I.cex_x, cy = (T)I.cex_y, kan = (T)I.kan;
-  const T ku[3] = {(T)I.ku[0], (T)I.ku[1], (T)I.ku[2]};
-  const T dt = (T)a.dt;
-
-  C v[3][8];
-  if (MODE != ROW_FFT_ONLY) row_inverse<T, L>(v, row, active, sm, t, a.tw);
-
-  double vsum = 0.0;
-  const bool objective_step = (MODE == ROW_STAGE) && s == 4 && a.slots != nullptr && I.objective == 0 &&
-                              (n + 1) >= a.n_from;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int x0 = 2 * (t + TT * q);
-    if (!active || x0 >= nx) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) v[c][q] = mk<C>((T)0, (T)0);
-      continue;
-    }
-    const long long n0 = (long long)y * nx + x0;
-    if (MODE == ROW_FFT_ONLY) {
-      T p0, p1;
-      ld2(ps + n0, p0, p1);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        T a0, a1;
-        ld2(Y + c * nodes + n0, a0, a1);
-        v[c][q] = mk<C>(Ms * p0 * a0, Ms * p1 * a1);
-      }
-      continue;
-    }
-    T Bd[2][3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      Bd[0][c] = v[c][q].x;
-      Bd[1][c] = v[c][q].y;
-    }
-    if (MODE == ROW_FIELD && a.demag_only) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) st2(a.Bout + off3 + c * nodes + n0, Bd[0][c], Bd[1][c]);
-      continue;
-    }
-    PairNbr<T> P;
-    gather_pair(Y, ps, nodes, nx, ny, x0, y, P);
-    if (MODE == ROW_TERMINAL) {
-      T lam[2][3] = {{0, 0, 0}, {0, 0, 0}};
-      T qpsi[2] = {0, 0};
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int xi = x0 + i;
-        T Bex[3] = {0, 0, 0};
-        exchange_node(P, i, cx, cy, Bex);
-        if (I.objective == 1) {
-          const T V = (T)I.V, sc = (T)I.escale;
-          const T pi = P.p[i];
-          const T mdb = dot3(P.y[i], Bd[i]);
-          vsum += -0.5 * (double)V * (double)Ms * (double)pi * (double)mdb;
-          const T hh[4] = {(T)I.ihx2, (T)I.ihx2, (T)I.ihy2, (T)I.ihy2};
-#pragma unroll
-          for (int d = 0; d < 4; ++d) {
-            if (!P.ok[i][d]) continue;
-            const T pj = P.pn[i][d];
-            T dm2 = 0;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const T dd = P.yn[i][d][c] - P.y[i][c];
-              dm2 += dd * dd;
-            }
-            const T sp = pi + pj;
-            const T Aij = sp > (T)0 ? (T)2 * (T)I.A * pi * pj / sp : (T)0;
-            vsum += 0.5 * (double)Aij * (double)V * (double)dm2 * (double)hh[d];
-            if (sp > (T)0) qpsi[i] += (T)2 * (T)I.A * pj * pj / (sp * sp) * V * dm2 * hh[d] * sc;
-          }
-          qpsi[i] += -V * Ms * mdb * sc;
-          const double meanpsi = a.psisum[tile.inst] / (double)nodes;
-          qpsi[i] += (T)(2.0 * I.penalty_w * (meanpsi - I.area_target) / (double)nodes);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) lam[i][c] = -V * Ms * pi * (Bd[i][c] + Bex[c]) * sc;
-        } else if (a.nsteps >= a.n_from) {
-#pragma unroll
-          for (int b = 0; b < 2; ++b) {
-            if (!in_box(I.boxes[b], xi, y)) continue;
-            const T vv = P.y[i][I.comp];
-            lam[i][I.comp] += (T)I.wbox[b] * (I.power == 2 ? (T)2 * vv : (T)1);
-          }
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) st2(a.lam + off3 + c * nodes + n0, lam[0][c], lam[1][c]);
-      st2(a.psib + I.node_off + n0, qpsi[0], qpsi[1]);
-      st2(a.psic + I.node_off + n0, (T)0, (T)0);
-      continue;
-    }
-    T B[2][3];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int xi = x0 + i;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) B[i][c] = Bd[i][c];
-      exchange_node(P, i, cx, cy, B[i]);
-      if (kan != (T)0) {
-        const T d = dot3(P.y[i], ku);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) B[i][c] += kan * d * ku[c];
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) B[i][c] += (T)I.B_bias[c];
-      if (in_box(I.src, xi, y)) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) B[i][c] += rf * (T)I.rf_dir[c];
-      }
-    }
-    if (MODE == ROW_FIELD) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) st2(a.Bout + off3 + c * nodes + n0, B[0][c], B[1][c]);
-      continue;
-    }
-    // ROW_STAGE: LL right-hand side and RK4 stage combine
-    T k[2][3];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) llg_rhs(P.y[i], B[i], alpha_at<T>(I, x0 + i, y), k[i]);
-    if (a.Bout)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) st2(a.Bout + off3 + c * nodes + n0, B[0][c], B[1][c]);
-    T yn[2][3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const long long id = off3 + c * nodes + n0;
-      T m0, m1;
-      ld2(a.m + id, m0, m1);
-      if (s == 1) {
-        st2(a.acc + id, k[0][c], k[1][c]);
-        yn[0][c] = m0 + (T)0.5 * dt * k[0][c];
-        yn[1][c] = m1 + (T)0.5 * dt * k[1][c];
-      } else if (s == 2 || s == 3) {
-        const T h = (s == 2) ? (T)0.5 * dt : dt;
-        T a0, a1;
-        ld2(a.acc + id, a0, a1);
-        st2(a.acc + id, a0 + (T)2 * k[0][c], a1 + (T)2 * k[1][c]);
-        yn[0][c] = m0 + h * k[0][c];
-        yn[1][c] = m1 + h * k[1][c];
-      } else {
-        T a0, a1;
-        ld2(a.acc + id, a0, a1);
-        yn[0][c] = m0 + dt / (T)6 * (a0 + k[0][c]);
-        yn[1][c] = m1 + dt / (T)6 * (a1 + k[1][c]);
-        st2(a.mout + id, yn[0][c], yn[1][c]);
-        if (a.ckpt) st2(a.ckpt + id, yn[0][c], yn[1][c]);
-      }
-      if (s < 4) st2(a.Yout + id, yn[0][c], yn[1][c]);
-      v[c][q] = mk<C>(Ms * P.p[0] * yn[0][c], Ms * P.p[1] * yn[1][c]);
-    }
-    if (objective_step) {
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          if (!in_box(I.boxes[b], x0 + i, y)) continue;
-          const T vv = yn[i][I.comp];
-          vsum += I.wbox[b] * (double)(I.power == 2 ? vv * vv : vv);
-        }
-    }
-  }
-  if (MODE == ROW_TERMINAL) {
-    if (I.objective == 1) {
-      const double tot = block_sum(vsum, red);
-      if (threadIdx.x == 0) atomicAdd(a.jterm + tile.inst, tot * I.escale);
-    }
-    return;
-  }
-  if (objective_step) {
-    bool touches = false;
-    for (int b = 0; b < 2; ++b)
-      touches |= (I.wbox[b] != 0.0) && I.boxes[b][2] < tile.y0 + tile.nrows && I.boxes[b][3] > tile.y0;
-    if (touches) {
-      const double tot = block_sum(vsum, red);
-      if (threadIdx.x == 0) atomicAdd(a.slots + I.slot_off + n + 1, tot);
-    }
-  }
-  if (MODE == ROW_FIELD) return;
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int q = 4; q < 8; ++q) v[c][q] = mk<C>((T)0, (T)0);
-  row_forward<T, L>(v, row, active, sm, t, a.tw);
-}
-
-// ---------------------------------------------------------------------------
-// forward RK4 stage with its inputs staged by bulk asynchronous copies.
-//
-// At entry one thread issues cp.async.bulk copies of the tile's packed field
-// spectrum (barrier 0) and of the rows the stencil and the stage combine
-// read: Y_s with one halo row on each side, psi with the same halo, m_n and
-// the RK accumulator (barrier 1).  The inverse row FFTs run while the node
-// data is in flight.  Shared memory: [exchange / spectrum staging]
-// [Y halo 3 x (R+2) rows][psi halo (R+2) rows][m 3 x R rows][acc 3 x R rows].
-// ---------------------------------------------------------------------------
-
-template <typename T>
-__host__ __device__ constexpr size_t stage_smem_bytes(int L, int nx) {
-  return (size_t)rows_per_tile(L) * 3 * rf_padded_len(L) * sizeof(cplx<T>) +
-         (size_t)(10 * rows_per_tile(L) + 8) * nx * sizeof(T);
-}
 
 // Neighbour data of the pair at (x0, row rr of the staged halo arrays).
 template <typename T>
@@ -607,144 +432,317 @@ __device__ __forceinline__ void gather_pair_smem(const T* sF, int cstride, const
   }
 }
 
+// Issue the halo copies (rows ylo..yhi-1 of `ncomp` components of F) into a
+// staged array with rows y0-1 .. y0+R; returns the bytes issued.
+template <typename T>
+__device__ __forceinline__ unsigned stage_halo(T* sF, int RM, const T* F, long long nodes, int ncomp, int nx,
+                                               int y0, int ylo, int yhi, uint64_t* bar) {
+  const unsigned hb = (unsigned)((yhi - ylo) * nx * sizeof(T));
+  const int r0 = ylo - y0 + 1;
+  for (int c = 0; c < ncomp; ++c)
+    bulk_load(sF + (c * (RM + 2) + r0) * nx, F + c * nodes + (long long)ylo * nx, hb, bar);
+  return hb * ncomp;
+}
+
+// Common per-block geometry of the row-family kernels.
+template <int L>
+struct RowGeom {
+  static constexpr int TT = L / 8;
+  static constexpr int SP = rf_padded_len(L);
+  static constexpr int RM = rows_per_tile(L);
+  int rl, c, t, tr;
+  __device__ __forceinline__ RowGeom(int tid) {
+    t = tid % TT;
+    c = (tid / TT) % 3;
+    rl = tid / (3 * TT);
+    tr = c * TT + t;        // lane within the row (0 .. 3 TT - 1)
+  }
+};
+
+// ---------------------------------------------------------------------------
+// row pass variants run once per segment or call: spectrum of M = Ms psi Y,
+// effective field, terminal energies / lambda_N.  Shared memory: scratch
+// (kExch complex) then W_{2L}^k, k < 2L.
+// ---------------------------------------------------------------------------
+
+template <typename T, int L, int MODE>
+__device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I, const RowTile& tile,
+                                          cplx<T>* smem, double* red, T rf) {
+  using C = cplx<T>;
+  using G = RowGeom<L>;
+  constexpr int GS = group_stride(L);
+  const G g(threadIdx.x);
+  const bool active = g.rl < tile.nrows;
+  const int nx = I.nx, ny = I.ny;
+  const int y = tile.y0 + (active ? g.rl : 0);
+  const long long nodes = I.nodes;
+  C* sE = smem + g.rl * 3 * GS;        // the three sequences of this row slot
+  C* grp = sE + g.c * GS;
+  T* sEr = reinterpret_cast<T*>(sE);
+  C* tw2 = smem + kExch;
+  C* row = a.spec + I.spec_off + (long long)y * 3 * L;
+  const long long off3 = 3 * I.node_off;
+  const T* __restrict__ Y = a.Yin + off3;
+  const T* __restrict__ ps = a.psi + I.node_off;
+  const T Ms = (T)I.Ms, cx = (T)I.cex_x, cy = (T)I.cex_y, kan = (T)I.kan;
+  const T ku[3] = {(T)I.ku[0], (T)I.ku[1], (T)I.ku[2]};
+  load_twiddles(tw2, a.tw, 2 * L);
+  __syncthreads();
+  if (MODE != ROW_FFT_ONLY) {
+    C v[8];
+    row_inverse_comp<T, L>(v, row + g.c * L, active, grp, g.t, tw2);
+    __syncthreads();
+  }
+  double vsum = 0.0;
+#pragma unroll 1
+  for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
+    const long long n0 = (long long)y * nx + x;
+    const int sl = node_slot<T>(x);
+    if (MODE == ROW_FFT_ONLY) {
+      const T p = ps[n0];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sEr[2 * c * GS + sl] = Ms * p * Y[c * nodes + n0];
+      continue;
+    }
+    T Bd[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Bd[c] = sEr[2 * c * GS + sl];
+    if (MODE == ROW_FIELD && a.demag_only) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a.Bout[off3 + c * nodes + n0] = Bd[c];
+      continue;
+    }
+    // own value and the four neighbours (+x, -x, +y, -y) from global memory
+    T yi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) yi[c] = Y[c * nodes + n0];
+    const T pi = ps[n0];
+    T Bex[3] = {0, 0, 0};
+    T qpsi = 0, eex = 0;
+    const T hh[4] = {(T)I.ihx2, (T)I.ihx2, (T)I.ihy2, (T)I.ihy2};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const bool ok = d == 0 ? x + 1 < nx : d == 1 ? x > 0 : d == 2 ? y + 1 < ny : y > 0;
+      if (!ok) continue;
+      const long long j = n0 + (d == 0 ? 1 : d == 1 ? -1 : d == 2 ? nx : -nx);
+      const T pj = ps[j];
+      const T w = (d < 2 ? cx : cy) * edge_weight(pi, pj);
+      T dm2 = 0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T dd = Y[c * nodes + j] - yi[c];
+        Bex[c] += w * dd;
+        dm2 += dd * dd;
+      }
+      if (MODE == ROW_TERMINAL && I.objective == 1) {
+        const T sp = pi + pj;
+        const T Aij = sp > (T)0 ? (T)2 * (T)I.A * pi * pj / sp : (T)0;
+        eex += (T)0.5 * Aij * dm2 * hh[d];
+        if (sp > (T)0) qpsi += (T)2 * (T)I.A * pj * pj / (sp * sp) * dm2 * hh[d];
+      }
+    }
+    if (MODE == ROW_TERMINAL) {
+      T lam[3] = {0, 0, 0};
+      T qp = 0;
+      if (I.objective == 1) {
+        const T V = (T)I.V, sc = (T)I.escale;
+        const T mdb = dot3(yi, Bd);
+        vsum += -0.5 * (double)V * (double)Ms * (double)pi * (double)mdb + (double)V * (double)eex;
+        qp = qpsi * V * sc - V * Ms * mdb * sc;
+        double psum = 0.0;   // the per-tile psi partials, added in tile order
+        for (int t = 0; t < I.ntile; ++t) psum += a.psitile[I.tile_off + t];
+        const double meanpsi = psum / (double)nodes;
+        qp += (T)(2.0 * I.penalty_w * (meanpsi - I.area_target) / (double)nodes);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) lam[c] = -V * Ms * pi * (Bd[c] + Bex[c]) * sc;
+      } else if (a.nsteps >= a.n_from) {
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          if (!in_box(I.boxes[b], x, y)) continue;
+          const T vv = yi[I.comp];
+          lam[I.comp] += (T)I.wbox[b] * (I.power == 2 ? (T)2 * vv : (T)1);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a.lam[off3 + c * nodes + n0] = lam[c];
+      a.psib[I.node_off + n0] = qp;
+      a.psic[I.node_off + n0] = (T)0;
+      continue;
+    }
+    // ROW_FIELD: full effective field
+    T B[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) B[c] = Bd[c] + Bex[c] + (T)I.B_bias[c];
+    if (kan != (T)0) {
+      const T dd = dot3(yi, ku);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) B[c] += kan * dd * ku[c];
+    }
+    if (in_box(I.src, x, y)) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) B[c] += rf * (T)I.rf_dir[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.Bout[off3 + c * nodes + n0] = B[c];
+  }
+  if (MODE == ROW_TERMINAL) {
+    if (I.objective == 1) {
+      const double tot = block_sum(vsum, red);
+      if (threadIdx.x == 0) a.jterm[I.tile_off + tile.k] = tot * I.escale;
+    }
+    return;
+  }
+  if (MODE == ROW_FIELD) return;
+  __syncthreads();
+  row_forward_comp<T, L>(grp, nx / 2, row + g.c * L, active, g.t, tw2);
+}
+
+// ---------------------------------------------------------------------------
+// forward RK4 stage.  At entry one thread issues cp.async.bulk copies of the
+// tile's packed field spectrum (barrier 0) and of the halo rows the stencil
+// reads, Y_s and psi with one row on each side (barrier 1); the inverse row
+// FFTs run while the halo rows, m_n and the RK accumulator (also barrier 1)
+// are in flight.  Shared memory: [scratch kExch complex][Y halo 3 x (R+2)
+// rows][psi halo (R+2) rows][m 3 x R rows][acc 3 x R rows][W_{2L}^k, k < 2L].
+// ---------------------------------------------------------------------------
+
 template <typename T, int L>
 __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I, const RowTile& tile,
                                            unsigned char* smem_raw, uint64_t* bars, double* red, T rf) {
   using C = cplx<T>;
-  constexpr int TT = L / 8;
-  constexpr int SP = rf_padded_len(L);
-  constexpr int RM = rows_per_tile(L);
+  using G = RowGeom<L>;
+  constexpr int RM = G::RM;
+  constexpr int GS = group_stride(L);
+  const G g(threadIdx.x);
   const int tid = threadIdx.x;
-  const int rl = tid / TT, t = tid - rl * TT;
   const int nr = tile.nrows;
-  const bool active = rl < nr;
+  const bool active = g.rl < nr;
   const int nx = I.nx, ny = I.ny, y0 = tile.y0;
-  const int y = y0 + (active ? rl : 0);
+  const int y = y0 + (active ? g.rl : 0);
   const long long nodes = I.nodes;
   C* sx = reinterpret_cast<C*>(smem_raw);
-  T* sY = reinterpret_cast<T*>(sx + RM * 3 * SP);
+  T* sY = reinterpret_cast<T*>(sx + kExch);
   T* sP = sY + 3 * (RM + 2) * nx;
-  T* sM = sP + (RM + 2) * nx;
-  T* sA = sM + 3 * RM * nx;
+  const bool spw = a.stage_pw != 0;           // m_n and the accumulator staged too
+  T* sM = sP + (RM + 2) * nx;                 // m_n rows            [c][r][x]
+  T* sA = sM + 3 * RM * nx;                   // RK accumulator rows [c][r][x]
+  C* tw2 = reinterpret_cast<C*>(spw ? sA + 3 * RM * nx : sM);
+  C* sE = sx + g.rl * 3 * GS;
+  C* grp = sE + g.c * GS;
+  T* sEr = reinterpret_cast<T*>(sE);
   const long long off3 = 3 * I.node_off;
   C* row0 = a.spec + I.spec_off + (long long)y0 * 3 * L;
   const int s = a.stage;
   const long long n = (a.step_base ? *a.step_base : 0) + a.local_step;
   const int ylo = max(0, y0 - 1), yhi = min(ny, y0 + nr + 1);
+  T* __restrict__ gacc = a.acc;
+  T* __restrict__ gYout = a.Yout;
+  T* __restrict__ gmout = a.mout;
+  T* __restrict__ gB = a.Bout;
+  T* __restrict__ gck = a.ckpt;
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     mbar_fence_init();
   }
+  load_twiddles(tw2, a.tw, 2 * L);
   __syncthreads();
   if (tid == 0) {
-    const unsigned sb = (unsigned)(nr * 3 * L * sizeof(C));
-    mbar_arrive_expect(&bars[0], sb);
-    bulk_load(sx, row0, sb, &bars[0]);
+    // each (row, component) spectrum lands at the start of its own group
+    const unsigned rowb = (unsigned)(L * sizeof(C));
+    mbar_arrive_expect(&bars[0], nr * 3 * rowb);
+    for (int r = 0; r < nr; ++r)
+      for (int c = 0; c < 3; ++c) bulk_load(sx + (r * 3 + c) * GS, row0 + (r * 3 + c) * L, rowb, &bars[0]);
     const unsigned hb = (unsigned)((yhi - ylo) * nx * sizeof(T));
     const unsigned rb = (unsigned)(nr * nx * sizeof(T));
-    const bool need_acc = s > 1;
-    mbar_arrive_expect(&bars[1], 4 * hb + 3 * rb + (need_acc ? 3 * rb : 0));
-    const int r0 = ylo - y0 + 1;
-    for (int c = 0; c < 3; ++c)
-      bulk_load(sY + (c * (RM + 2) + r0) * nx, a.Yin + off3 + c * nodes + (long long)ylo * nx, hb, &bars[1]);
-    bulk_load(sP + r0 * nx, a.psi + I.node_off + (long long)ylo * nx, hb, &bars[1]);
-    for (int c = 0; c < 3; ++c)
-      bulk_load(sM + c * RM * nx, a.m + off3 + c * nodes + (long long)y0 * nx, rb, &bars[1]);
-    if (need_acc)
+    mbar_arrive_expect(&bars[1], 4 * hb + (spw ? (s > 1 ? 6 : 3) * rb : 0));
+    stage_halo(sY, RM, a.Yin + off3, nodes, 3, nx, y0, ylo, yhi, &bars[1]);
+    stage_halo(sP, RM, a.psi + I.node_off, nodes, 1, nx, y0, ylo, yhi, &bars[1]);
+    if (spw) {
       for (int c = 0; c < 3; ++c)
-        bulk_load(sA + c * RM * nx, a.acc + off3 + c * nodes + (long long)y0 * nx, rb, &bars[1]);
+        bulk_load(sM + c * RM * nx, a.m + off3 + c * nodes + (long long)y0 * nx, rb, &bars[1]);
+      if (s > 1)
+        for (int c = 0; c < 3; ++c)
+          bulk_load(sA + c * RM * nx, a.acc + off3 + c * nodes + (long long)y0 * nx, rb, &bars[1]);
+    }
   }
-  // inverse row FFTs of the field spectra while the node data arrives
   mbar_wait(&bars[0], 0, a.err);
-  C v[3][8];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      v[c][q] = active ? unpack_one(sx + (rl * 3 + c) * L, t + TT * q, L, a.tw) : mk<C>((T)0, (T)0);
-  __syncthreads();
-  regfft<C, L, 1, 3>(v, sx + rl * 3 * SP, SP, 1, t, a.tw);
+  {
+    C v[8];
+    row_inverse_comp<T, L>(v, grp, active, grp, g.t, tw2);
+  }
   mbar_wait(&bars[1], 0, a.err);
+  __syncthreads();
 
   const T Ms = (T)I.Ms, cx = (T)I.cex_x, cy = (T)I.cex_y, kan = (T)I.kan;
   const T ku[3] = {(T)I.ku[0], (T)I.ku[1], (T)I.ku[2]};
   const T dt = (T)a.dt;
+  const T hs = (s == 1 || s == 2) ? (T)0.5 * dt : dt;     // Y_{s+1} = m + hs k_s
+  const int cs = (RM + 2) * nx;                            // component stride of the staged halo
   double vsum = 0.0;
   const bool objective_step = s == 4 && a.slots != nullptr && I.objective == 0 && (n + 1) >= a.n_from;
+#pragma unroll 1
+  for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
+    const long long n0 = (long long)y * nx + x;
+    const int sl = node_slot<T>(x);
+    const int oi = (g.rl + 1) * nx + x;
+    const T pi = sP[oi];
+    T yi[3], B[3];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int x0 = 2 * (t + TT * q);
-    if (!active || x0 >= nx) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) v[c][q] = mk<C>((T)0, (T)0);
-      continue;
+    for (int c = 0; c < 3; ++c) {
+      yi[c] = sY[c * cs + oi];
+      B[c] = sEr[2 * c * GS + sl] + (T)I.B_bias[c];
     }
-    PairNbr<T> P;
-    gather_pair_smem(sY, (RM + 2) * nx, sP, nx, ny, x0, y, rl + 1, P);
-    T B[2][3];
+    // exchange: sum over existing neighbours of c_d w_ij (Y_j - Y_i)
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int d = 0; d < 4; ++d) {
+      const bool ok = d == 0 ? x + 1 < nx : d == 1 ? x > 0 : d == 2 ? y + 1 < ny : y > 0;
+      if (!ok) continue;
+      const int oj = oi + (d == 0 ? 1 : d == 1 ? -1 : d == 2 ? nx : -nx);
+      const T w = (d < 2 ? cx : cy) * edge_weight(pi, sP[oj]);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) B[i][c] = (i == 0) ? v[c][q].x : v[c][q].y;
-      exchange_node(P, i, cx, cy, B[i]);
-      if (kan != (T)0) {
-        const T d = dot3(P.y[i], ku);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) B[i][c] += kan * d * ku[c];
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) B[i][c] += (T)I.B_bias[c];
-      if (in_box(I.src, x0 + i, y)) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) B[i][c] += rf * (T)I.rf_dir[c];
-      }
+      for (int c = 0; c < 3; ++c) B[c] += w * (sY[c * cs + oj] - yi[c]);
     }
-    T k[2][3];
+    if (kan != (T)0) {
+      const T dd = dot3(yi, ku);
 #pragma unroll
-    for (int i = 0; i < 2; ++i) llg_rhs(P.y[i], B[i], alpha_at<T>(I, x0 + i, y), k[i]);
-    const long long n0 = (long long)y * nx + x0;
-    if (a.Bout)
+      for (int c = 0; c < 3; ++c) B[c] += kan * dd * ku[c];
+    }
+    if (in_box(I.src, x, y)) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) st2(a.Bout + off3 + c * nodes + n0, B[0][c], B[1][c]);
-    T yn[2][3];
+      for (int c = 0; c < 3; ++c) B[c] += rf * (T)I.rf_dir[c];
+    }
+    T k[3];
+    llg_rhs(yi, B, alpha_at<T>(I, x, y), k);
+    T yn[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long id = off3 + c * nodes + n0;
-      const int so = (c * RM + rl) * nx + x0;
-      T m0, m1;
-      ld2(sM + so, m0, m1);
+      const int so = (c * RM + g.rl) * nx + x;
+      if (gB) gB[id] = B[c];
+      const T m0 = spw ? sM[so] : a.m[id];
       if (s == 1) {
-        st2(a.acc + id, k[0][c], k[1][c]);
-        yn[0][c] = m0 + (T)0.5 * dt * k[0][c];
-        yn[1][c] = m1 + (T)0.5 * dt * k[1][c];
-      } else if (s == 2 || s == 3) {
-        const T h = (s == 2) ? (T)0.5 * dt : dt;
-        T a0, a1;
-        ld2(sA + so, a0, a1);
-        st2(a.acc + id, a0 + (T)2 * k[0][c], a1 + (T)2 * k[1][c]);
-        yn[0][c] = m0 + h * k[0][c];
-        yn[1][c] = m1 + h * k[1][c];
+        gacc[id] = k[c];
+        yn[c] = m0 + hs * k[c];
+      } else if (s < 4) {
+        const T a0 = spw ? sA[so] : gacc[id];
+        gacc[id] = a0 + (T)2 * k[c];
+        yn[c] = m0 + hs * k[c];
       } else {
-        T a0, a1;
-        ld2(sA + so, a0, a1);
-        yn[0][c] = m0 + dt / (T)6 * (a0 + k[0][c]);
-        yn[1][c] = m1 + dt / (T)6 * (a1 + k[1][c]);
-        st2(a.mout + id, yn[0][c], yn[1][c]);
-        if (a.ckpt) st2(a.ckpt + id, yn[0][c], yn[1][c]);
+        yn[c] = m0 + dt / (T)6 * ((spw ? sA[so] : gacc[id]) + k[c]);
+        gmout[id] = yn[c];
+        if (gck) gck[id] = yn[c];
       }
-      if (s < 4) st2(a.Yout + id, yn[0][c], yn[1][c]);
-      v[c][q] = mk<C>(Ms * P.p[0] * yn[0][c], Ms * P.p[1] * yn[1][c]);
+      if (s < 4) gYout[id] = yn[c];
+      sEr[2 * c * GS + sl] = Ms * pi * yn[c];
     }
     if (objective_step) {
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          if (!in_box(I.boxes[b], x0 + i, y)) continue;
-          const T vv = yn[i][I.comp];
-          vsum += I.wbox[b] * (double)(I.power == 2 ? vv * vv : vv);
-        }
+      for (int b = 0; b < 2; ++b) {
+        if (!in_box(I.boxes[b], x, y)) continue;
+        const T vv = yn[I.comp];
+        vsum += I.wbox[b] * (double)(I.power == 2 ? vv * vv : vv);
+      }
     }
   }
   if (objective_step) {
@@ -753,14 +751,11 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
       touches |= (I.wbox[b] != 0.0) && I.boxes[b][2] < y0 + nr && I.boxes[b][3] > y0;
     if (touches) {
       const double tot = block_sum(vsum, red);
-      if (threadIdx.x == 0) atomicAdd(a.slots + I.slot_off + n + 1, tot);
+      if (threadIdx.x == 0) a.slots[I.slot_off + (long long)(n + 1) * I.ntile + tile.k] = tot;
     }
   }
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int q = 4; q < 8; ++q) v[c][q] = mk<C>((T)0, (T)0);
-  row_forward<T, L>(v, a.spec + I.spec_off + (long long)y * 3 * L, active, sx + rl * 3 * SP, t, a.tw);
+  __syncthreads();
+  row_forward_comp<T, L>(grp, nx / 2, a.spec + I.spec_off + (long long)y * 3 * L + g.c * L, active, g.t, tw2);
 }
 
 template <typename T, int MODE>
@@ -816,26 +811,49 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
-// adjoint stage
+// adjoint stage.  Staged by bulk copies: the packed spectrum of N * Bbar_s
+// (barrier 0) and, with one halo row on each side, Y_s, Bbar_s and psi, plus
+// the pointwise rows of lambda, gpart, G, the dJ/dpsi Kahan pair and Y, B of
+// the next stage (barrier 1).  Shared memory: [scratch kExch complex]
+// [Y_s halo][Bbar halo][psi halo][17 pointwise arrays x R rows]
+// [W_{2L}^k, k < 2L].
 // ---------------------------------------------------------------------------
 
 template <typename T, int L>
 __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, const RowTile& tile,
-                                         cplx<T>* smem) {
+                                         unsigned char* smem_raw, uint64_t* bars) {
   using C = cplx<T>;
-  constexpr int TT = L / 8;
+  using G = RowGeom<L>;
+  constexpr int RM = G::RM;
+  constexpr int GS = group_stride(L);
+  const G g(threadIdx.x);
   const int tid = threadIdx.x;
-  const int rl = tid / TT, t = tid - rl * TT;
-  const bool active = rl < tile.nrows;
-  const int nx = I.nx, ny = I.ny;
-  const int y = tile.y0 + (active ? rl : 0);
+  const int nr = tile.nrows;
+  const bool active = g.rl < nr;
+  const int nx = I.nx, ny = I.ny, y0 = tile.y0;
+  const int y = y0 + (active ? g.rl : 0);
   const long long nodes = I.nodes;
-  C* sm = smem + rl * 3 * rf_padded_len(L);
-  C* row = a.spec + I.spec_off + (long long)y * 3 * L;
+  C* sx = reinterpret_cast<C*>(smem_raw);
+  T* sYs = reinterpret_cast<T*>(sx + kExch);
+  T* sBb = sYs + 3 * (RM + 2) * nx;
+  T* sP = sBb + 3 * (RM + 2) * nx;
+  // pointwise rows [c][r][x]: lambda, gpart, G, dJ/dpsi sum and compensation, Y and B of the next stage
+  T* sL = sP + (RM + 2) * nx;
+  T* sGp = sL + 3 * RM * nx;
+  T* sG = sGp + 3 * RM * nx;
+  T* sQs = sG + 3 * RM * nx;
+  T* sQc = sQs + RM * nx;
+  T* sYp = sQc + RM * nx;
+  T* sBp = sYp + 3 * RM * nx;
+  const bool spw = a.stage_pw != 0;           // pointwise rows staged too
+  C* tw2 = reinterpret_cast<C*>(spw ? sBp + 3 * RM * nx : sL);
+  C* sE = sx + g.rl * 3 * GS;
+  C* grp = sE + g.c * GS;
+  T* sEr = reinterpret_cast<T*>(sE);
+  C* row0 = a.spec + I.spec_off + (long long)y0 * 3 * L;
   const long long n = (a.step_base ? *a.step_base : 0) + a.local_step;
   const int s = a.stage;
   const long long off3 = 3 * I.node_off;
-  const T* __restrict__ ps = a.psi + I.node_off;
   const T Ms = (T)I.Ms, cx = (T)I.cex_x, cy = (T)I.cex_y, kan = (T)I.kan;
   const T ku[3] = {(T)I.ku[0], (T)I.ku[1], (T)I.ku[2]};
   const T dt = (T)a.dt;
@@ -844,158 +862,192 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   else if (s == 3) { ca = dt / (T)3; cb = (T)0.5 * dt; }
   else if (s == 2) { ca = dt / (T)6; cb = (T)0.5 * dt; }
   const bool emit = a.seed_only || s > 1 || a.seed_next;
-
-  C v[3][8];
-  if (!a.seed_only) row_inverse<T, L>(v, row, active, sm, t, a.tw);
-
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int x0 = 2 * (t + TT * q);
-    if (!active || x0 >= nx) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) v[c][q] = mk<C>((T)0, (T)0);
-      continue;
+  const bool seed = a.seed_only != 0;
+  T* __restrict__ glam = a.lam;
+  T* __restrict__ gG = a.G;
+  T* __restrict__ ggp = a.gpart;
+  T* __restrict__ gpsib = a.psib;
+  T* __restrict__ gpsic = a.psic;
+  T* __restrict__ gbo = a.BbarOut;
+  const int ylo = max(0, y0 - 1), yhi = min(ny, y0 + nr + 1);
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_fence_init();
+  }
+  load_twiddles(tw2, a.tw, 2 * L);
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned rb = spw ? (unsigned)(nr * nx * sizeof(T)) : 0u;
+    const long long r0 = (long long)y0 * nx;
+    unsigned bytes = (3 + (emit ? 6 : 0)) * rb;
+    if (!seed) {
+      const unsigned rowb = (unsigned)(L * sizeof(C));
+      mbar_arrive_expect(&bars[0], nr * 3 * rowb);
+      for (int r = 0; r < nr; ++r)
+        for (int c = 0; c < 3; ++c) bulk_load(sx + (r * 3 + c) * GS, row0 + (r * 3 + c) * L, rowb, &bars[0]);
+      const unsigned hb = (unsigned)((yhi - ylo) * nx * sizeof(T));
+      bytes += 7 * hb + (3 + (s < 4 ? 3 : 0) + 2) * rb;
     }
-    const long long n0 = (long long)y * nx + x0;
-    T lam[2][3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) ld2(a.lam + off3 + c * nodes + n0, lam[0][c], lam[1][c]);
-    T u[2][3];
-    if (a.seed_only) {
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) u[i][c] = dt / (T)6 * lam[i][c];
-    } else {
-      PairNbr<T> Py, Pb;   // stage input Y_s and field cotangent Bbar_s around the pair
-      gather_pair(a.Ys + off3, ps, nodes, nx, ny, x0, y, Py);
-      gather_pair(a.Bbar + off3, ps, nodes, nx, ny, x0, y, Pb);
-      T g[2][3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) ld2(a.gpart + off3 + c * nodes + n0, g[0][c], g[1][c]);
-      T qpsi[2] = {0, 0};
-      const T cc[4] = {cx, cx, cy, cy};
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const T pi = Py.p[i];
-        // exchange transpose (gather form) and its psi derivative
-#pragma unroll
-        for (int d = 0; d < 4; ++d) {
-          if (!Py.ok[i][d]) continue;
-          const T pj = Py.pn[i][d];
-          const T wij = edge_weight(pi, pj), wji = edge_weight(pj, pi);
-          T eij = 0, eji = 0;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            g[i][c] += cc[d] * (wji * Pb.yn[i][d][c] - wij * Pb.y[i][c]);
-            eij += Pb.y[i][c] * (Py.yn[i][d][c] - Py.y[i][c]);
-            eji += Pb.yn[i][d][c] * (Py.y[i][c] - Py.yn[i][d][c]);
-          }
-          const T sp = pi + pj;
-          if (sp > (T)0) qpsi[i] += cc[d] * (T)2 * pj / (sp * sp) * (eji - eij);
+    mbar_arrive_expect(&bars[1], bytes);
+    if (!seed) {
+      stage_halo(sYs, RM, a.Ys + off3, nodes, 3, nx, y0, ylo, yhi, &bars[1]);
+      stage_halo(sBb, RM, a.Bbar + off3, nodes, 3, nx, y0, ylo, yhi, &bars[1]);
+      stage_halo(sP, RM, a.psi + I.node_off, nodes, 1, nx, y0, ylo, yhi, &bars[1]);
+      if (spw) {
+        for (int c = 0; c < 3; ++c) {
+          bulk_load(sGp + c * RM * nx, a.gpart + off3 + c * nodes + r0, rb, &bars[1]);
+          if (s < 4) bulk_load(sG + c * RM * nx, a.G + off3 + c * nodes + r0, rb, &bars[1]);
         }
-        // demag transpose Ms psi_i (N * Bbar)_i and its psi derivative
-        const T D[3] = {i == 0 ? v[0][q].x : v[0][q].y, i == 0 ? v[1][q].x : v[1][q].y,
-                        i == 0 ? v[2][q].x : v[2][q].y};
-#pragma unroll
-        for (int c = 0; c < 3; ++c) g[i][c] += Ms * pi * D[c];
-        qpsi[i] += Ms * dot3(Py.y[i], D);
+        bulk_load(sQs, a.psib + I.node_off + r0, rb, &bars[1]);
+        bulk_load(sQc, a.psic + I.node_off + r0, rb, &bars[1]);
       }
+    }
+    if (spw)
+      for (int c = 0; c < 3; ++c) {
+        bulk_load(sL + c * RM * nx, a.lam + off3 + c * nodes + r0, rb, &bars[1]);
+        if (emit) {
+          bulk_load(sYp + c * RM * nx, a.Yprev + off3 + c * nodes + r0, rb, &bars[1]);
+          bulk_load(sBp + c * RM * nx, a.Bprev + off3 + c * nodes + r0, rb, &bars[1]);
+        }
+      }
+  }
+  if (!seed) {
+    mbar_wait(&bars[0], 0, a.err);
+    C v[8];
+    row_inverse_comp<T, L>(v, grp, active, grp, g.t, tw2);
+  }
+  mbar_wait(&bars[1], 0, a.err);
+  __syncthreads();
+
+  const int cs = (RM + 2) * nx;
+  const T cc[4] = {cx, cx, cy, cy};
+#pragma unroll 1
+  for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
+    const long long n0 = (long long)y * nx + x;
+    const int sl = node_slot<T>(x);
+    const int po = g.rl * nx + x;             // pointwise staged index (component stride RM nx)
+    T lam[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lam[c] = spw ? sL[c * RM * nx + po] : glam[off3 + c * nodes + n0];
+    T u[3];
+    if (seed) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u[c] = dt / (T)6 * lam[c];
+    } else {
+      const int oi = (g.rl + 1) * nx + x;
+      const T pi = sP[oi];
+      T yi[3], bi[3], gg[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        yi[c] = sYs[c * cs + oi];
+        bi[c] = sBb[c * cs + oi];
+        gg[c] = spw ? sGp[c * RM * nx + po] : ggp[off3 + c * nodes + n0];
+      }
+      T qpsi = 0;
+      // exchange transpose (gather form) and its psi derivative
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        const bool ok = d == 0 ? x + 1 < nx : d == 1 ? x > 0 : d == 2 ? y + 1 < ny : y > 0;
+        if (!ok) continue;
+        const int oj = oi + (d == 0 ? 1 : d == 1 ? -1 : d == 2 ? nx : -nx);
+        const T pj = sP[oj];
+        const T wij = edge_weight(pi, pj), wji = edge_weight(pj, pi);
+        T eij = 0, eji = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const T yj = sYs[c * cs + oj], bj = sBb[c * cs + oj];
+          gg[c] += cc[d] * (wji * bj - wij * bi[c]);
+          eij += bi[c] * (yj - yi[c]);
+          eji += bj * (yi[c] - yj);
+        }
+        const T sp = pi + pj;
+        if (sp > (T)0) qpsi += cc[d] * (T)2 * pj / (sp * sp) * (eji - eij);
+      }
+      // demag transpose Ms psi_i (N * Bbar)_i and its psi derivative
+      T D[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        D[c] = sEr[2 * c * GS + sl];
+        gg[c] += Ms * pi * D[c];
+      }
+      qpsi += Ms * dot3(yi, D);
       {
-        T s0, s1, c0, c1;
-        ld2(a.psib + I.node_off + n0, s0, s1);
-        ld2(a.psic + I.node_off + n0, c0, c1);
-        kahan_add(s0, c0, qpsi[0]);
-        kahan_add(s1, c1, qpsi[1]);
-        st2(a.psib + I.node_off + n0, s0, s1);
-        st2(a.psic + I.node_off + n0, c0, c1);
+        T sum = spw ? sQs[po] : gpsib[I.node_off + n0], comp = spw ? sQc[po] : gpsic[I.node_off + n0];
+        kahan_add(sum, comp, qpsi);
+        gpsib[I.node_off + n0] = sum;
+        gpsic[I.node_off + n0] = comp;
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const long long id = off3 + c * nodes + n0;
         if (s == 4) {
-          st2(a.G + id, g[0][c], g[1][c]);
+          gG[id] = gg[c];
         } else if (s > 1) {
-          T g0, g1;
-          ld2(a.G + id, g0, g1);
-          st2(a.G + id, g0 + g[0][c], g1 + g[1][c]);
+          gG[id] = (spw ? sG[c * RM * nx + po] : gG[id]) + gg[c];
         } else {
-          T g0, g1;
-          ld2(a.G + id, g0, g1);
-          lam[0][c] += g0 + g[0][c];
-          lam[1][c] += g1 + g[1][c];
+          lam[c] += (spw ? sG[c * RM * nx + po] : gG[id]) + gg[c];
         }
       }
       if (s == 1) {
         if (I.objective == 0 && n >= a.n_from) {
 #pragma unroll
-          for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-              if (!in_box(I.boxes[b], x0 + i, y)) continue;
-              const T vv = Py.y[i][I.comp];
-              lam[i][I.comp] += (T)I.wbox[b] * (I.power == 2 ? (T)2 * vv : (T)1);
-            }
+          for (int b = 0; b < 2; ++b) {
+            if (!in_box(I.boxes[b], x, y)) continue;
+            const T vv = yi[I.comp];
+            lam[I.comp] += (T)I.wbox[b] * (I.power == 2 ? (T)2 * vv : (T)1);
+          }
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) st2(a.lam + off3 + c * nodes + n0, lam[0][c], lam[1][c]);
+        for (int c = 0; c < 3; ++c) glam[off3 + c * nodes + n0] = lam[c];
       }
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) u[i][c] = (s > 1) ? ca * lam[i][c] + cb * g[i][c] : dt / (T)6 * lam[i][c];
+      for (int c = 0; c < 3; ++c) u[c] = (s > 1) ? ca * lam[c] + cb * gg[c] : dt / (T)6 * lam[c];
     }
     if (!emit) continue;
-    T yp[2][3], bp[2][3];
+    T yp[3], bp[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      ld2(a.Yprev + off3 + c * nodes + n0, yp[0][c], yp[1][c]);
-      ld2(a.Bprev + off3 + c * nodes + n0, bp[0][c], bp[1][c]);
+      yp[c] = spw ? sYp[c * RM * nx + po] : a.Yprev[off3 + c * nodes + n0];
+      bp[c] = spw ? sBp[c * RM * nx + po] : a.Bprev[off3 + c * nodes + n0];
     }
-    T bbar[2][3], gl[2][3];
+    T bbar[3], gl[3];
+    rhs_vjp(u, yp, bp, alpha_at<T>(I, x, y), bbar, gl);
+    if (kan != (T)0) {
+      const T dd = dot3(bbar, ku);
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      rhs_vjp(u[i], yp[i], bp[i], alpha_at<T>(I, x0 + i, y), bbar[i], gl[i]);
-      if (kan != (T)0) {
-        const T d = dot3(bbar[i], ku);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) gl[i][c] += kan * d * ku[c];
-      }
+      for (int c = 0; c < 3; ++c) gl[c] += kan * dd * ku[c];
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long id = off3 + c * nodes + n0;
-      st2(a.BbarOut + id, bbar[0][c], bbar[1][c]);
-      st2(a.gpart + id, gl[0][c], gl[1][c]);
-      v[c][q] = mk<C>(bbar[0][c], bbar[1][c]);
+      gbo[id] = bbar[c];
+      ggp[id] = gl[c];
+      sEr[2 * c * GS + sl] = bbar[c];
     }
   }
   if (!emit) return;
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int q = 4; q < 8; ++q) v[c][q] = mk<C>((T)0, (T)0);
-  row_forward<T, L>(v, row, active, sm, t, a.tw);
+  __syncthreads();
+  row_forward_comp<T, L>(grp, nx / 2, a.spec + I.spec_off + (long long)y * 3 * L + g.c * L, active, g.t, tw2);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kAdjThreads) adj_kernel(AdjArgs<T> a) {
-  using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ DevInst sI;
+  __shared__ uint64_t bars[2];
   const RowTile tile = a.tiles[blockIdx.x];
   load_inst(sI, a.inst + tile.inst);
   __syncthreads();
-  C* sm = reinterpret_cast<C*>(smem_raw);
   switch (sI.log2Lx) {
-    case 3: adj_body<T, 8>(a, sI, tile, sm); break;
-    case 4: adj_body<T, 16>(a, sI, tile, sm); break;
-    case 5: adj_body<T, 32>(a, sI, tile, sm); break;
-    case 6: adj_body<T, 64>(a, sI, tile, sm); break;
-    case 7: adj_body<T, 128>(a, sI, tile, sm); break;
-    case 8: adj_body<T, 256>(a, sI, tile, sm); break;
-    case 9: adj_body<T, 512>(a, sI, tile, sm); break;
-    case 10: adj_body<T, 1024>(a, sI, tile, sm); break;
+    case 3: adj_body<T, 8>(a, sI, tile, smem_raw, bars); break;
+    case 4: adj_body<T, 16>(a, sI, tile, smem_raw, bars); break;
+    case 5: adj_body<T, 32>(a, sI, tile, smem_raw, bars); break;
+    case 6: adj_body<T, 64>(a, sI, tile, smem_raw, bars); break;
+    case 7: adj_body<T, 128>(a, sI, tile, smem_raw, bars); break;
+    case 8: adj_body<T, 256>(a, sI, tile, smem_raw, bars); break;
+    case 9: adj_body<T, 512>(a, sI, tile, smem_raw, bars); break;
+    case 10: adj_body<T, 1024>(a, sI, tile, smem_raw, bars); break;
     default: break;
   }
 }
@@ -1006,7 +1058,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_kernel(AdjArgs<T> a) {
 
 template <typename T>
 __global__ void material_kernel(const DevInst* inst, const RowTile* tiles, const T* phi, T* psi, T* dpsi,
-                                double* psisum) {
+                                double* psitile) {
   __shared__ double red[32];
   const RowTile tile = tiles[blockIdx.x];
   const DevInst& I = inst[tile.inst];
@@ -1021,7 +1073,7 @@ __global__ void material_kernel(const DevInst* inst, const RowTile* tiles, const
     acc += p;
   }
   const double tot = block_sum(acc, red);
-  if (threadIdx.x == 0) atomicAdd(psisum + tile.inst, tot);
+  if (threadIdx.x == 0) psitile[I.tile_off + tile.k] = tot;
 }
 
 template <typename T>
@@ -1086,9 +1138,19 @@ template <typename T, int MODE>
 void launch_rows_mode(const RowArgs<T>& a, int ntiles, size_t smem, cudaStream_t st) {
   rows_kernel<T, MODE><<<ntiles, kRowThreads, smem, st>>>(a);
 }
+// The dynamic shared-memory limit is a process-wide attribute of each kernel:
+// it is only ever raised, so that a context for small grids does not lower it
+// below what another context (or llg_field_noalloc) launches with.
+inline void raise_smem_limit(const void* fn, size_t* cur, size_t smem) {
+  if (smem > *cur) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    *cur = smem;
+  }
+}
 template <typename T, int MODE>
 void smem_rows_mode(size_t smem) {
-  cudaFuncSetAttribute(rows_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static size_t cur = 0;
+  raise_smem_limit(reinterpret_cast<const void*>(rows_kernel<T, MODE>), &cur, smem);
 }
 template <typename T>
 void launch_cols(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st) {
@@ -1096,7 +1158,8 @@ void launch_cols(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st) 
 }
 template <typename T>
 void smem_cols(size_t smem) {
-  cudaFuncSetAttribute(cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static size_t cur = 0;
+  raise_smem_limit(reinterpret_cast<const void*>(cols_kernel<T>), &cur, smem);
 }
 template <typename T>
 void launch_adj(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st) {
@@ -1104,12 +1167,13 @@ void launch_adj(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st) {
 }
 template <typename T>
 void smem_adj(size_t smem) {
-  cudaFuncSetAttribute(adj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static size_t cur = 0;
+  raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T>), &cur, smem);
 }
 template <typename T>
 void launch_material_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* phi, T* psi,
-                           T* dpsi, double* psisum, cudaStream_t st) {
-  material_kernel<T><<<ntiles, 256, 0, st>>>(inst, tiles, phi, psi, dpsi, psisum);
+                           T* dpsi, double* psitile, cudaStream_t st) {
+  material_kernel<T><<<ntiles, 256, 0, st>>>(inst, tiles, phi, psi, dpsi, psitile);
 }
 template <typename T>
 void launch_grad_finish_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* dpsi,

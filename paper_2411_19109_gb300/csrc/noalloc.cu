@@ -48,7 +48,7 @@ constexpr size_t SZ_TW64 = align256(sizeof(double2) * kTwiddleN);
 constexpr size_t SZ_INST = align256(sizeof(DevInst));
 constexpr size_t SZ_RT = align256(sizeof(RowTile) * NA_MAX_ROW_TILES);
 constexpr size_t SZ_CT = align256(sizeof(ColTile) * NA_MAX_COL_TILES);
-constexpr size_t SZ_SUM = 256;                                                                // psi sum (double)
+constexpr size_t SZ_SUM = align256(sizeof(double) * NA_MAX_ROW_TILES);                        // psi partials
 
 constexpr size_t OFF_G = 0;
 constexpr size_t OFF_TENS = OFF_G + SZ_G;
@@ -183,7 +183,9 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   ColTile ct[NA_MAX_COL_TILES];
   int nrt = 0, nct = 0;
   const int rows = rows_per_tile(d.Lx);
-  for (int y0 = 0; y0 < p.ny; y0 += rows) rt[nrt++] = {0, y0, std::min(rows, p.ny - y0), 0};
+  for (int y0 = 0; y0 < p.ny; y0 += rows, ++nrt) rt[nrt] = {0, y0, std::min(rows, p.ny - y0), nrt};
+  d.ntile = nrt;
+  d.tile_off = 0;
   const int tx = std::max(1, std::min(1024 / Py, d.Lx));
   for (int k0 = 0; k0 < d.Lx; k0 += tx) ct[nct++] = {0, k0, tx, 0};
 
@@ -194,7 +196,7 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   float2* spec = reinterpret_cast<float2*>(base + OFF_SPEC);
   float* psi = reinterpret_cast<float*>(base + OFF_PSI);
   float* dpsi = reinterpret_cast<float*>(base + OFF_DPSI);
-  double* psisum = reinterpret_cast<double*>(base + OFF_SUM);
+  double* psitile = reinterpret_cast<double*>(base + OFF_SUM);
   double2* G = reinterpret_cast<double2*>(base + OFF_G);
   const float2* tw = reinterpret_cast<const float2*>(base + OFF_TW);
   const double2* tw64 = reinterpret_cast<const double2*>(base + OFF_TW64);
@@ -205,13 +207,12 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   // the demag spectrum of this grid, FP64 on the device (G is cleared inside)
   if (e == cudaSuccess)
     e = build_tensor_spectrum<float>(tens, G, p.nx, p.ny, Px, Py, p.dx, p.dy, p.dz, tw64, st);
-  // psi from phi; the psi sum starts at zero
-  if (e == cudaSuccess) e = cudaMemsetAsync(psisum, 0, sizeof(double), st);
+  // psi from phi (the per-tile psi partials are not used by the field)
   if (e != cudaSuccess) {
     if (err_msg) *err_msg = "llg_field_noalloc: set-up copies or tensor build failed";
     return LLG_ECUDA;
   }
-  launch_material_tiles<float>(dI, dRT, nrt, static_cast<const float*>(phi_dev), psi, dpsi, psisum, st);
+  launch_material_tiles<float>(dI, dRT, nrt, static_cast<const float*>(phi_dev), psi, dpsi, psitile, st);
 
   RowArgs<float> a;
   std::memset(&a, 0, sizeof a);
@@ -221,8 +222,11 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   a.tw = tw;
   a.psi = psi;
   a.Yin = static_cast<const float*>(m_dev);
-  const size_t smem = (size_t)3456 * sizeof(float2);
-  launch_rows<float>(a, ROW_FFT_ONLY, nrt, smem, st);
+  // exchange scratch + twiddle table (W_{2Lx} for the row kernels, W_Py for
+  // the column kernel): below the 48 KB default, no opt-in attribute needed
+  const size_t smem_rows = (size_t)(kExch + 2 * d.Lx) * sizeof(float2);
+  const size_t smem_cols = (size_t)(kExch + Py) * sizeof(float2);
+  launch_rows<float>(a, ROW_FFT_ONLY, nrt, smem_rows, st);
   ColArgs<float> c;
   c.inst = dI;
   c.tiles = dCT;
@@ -230,11 +234,11 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   c.tw = tw;
   c.tens = tens;
   c.cols_max = tx;
-  launch_cols<float>(c, nct, smem, st);
+  launch_cols<float>(c, nct, smem_cols, st);
   a.Bout = static_cast<float*>(B_dev);
   a.t_field = t;
   a.demag_only = demag_only;
-  launch_rows<float>(a, ROW_FIELD, nrt, smem, st);
+  launch_rows<float>(a, ROW_FIELD, nrt, smem_rows, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     if (err_msg) *err_msg = "llg_field_noalloc: kernel launch failed";

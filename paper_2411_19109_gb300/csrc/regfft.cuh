@@ -10,8 +10,9 @@
 // slot per eight) to spread the scattered writes over the banks; the last
 // pass leaves its output in registers.
 //
-// Twiddles W_L^k come from the FP64-computed table of W_4096^k.  DIR = -1 is
-// the forward transform, +1 the unnormalised inverse.
+// Twiddles: W_L^m = tw[m * tws] for a table the caller provides (a copy of
+// the FP64-computed W_4096^k table in shared memory, or the global table
+// itself).  DIR = -1 is the forward transform, +1 the unnormalised inverse.
 #pragma once
 
 #include "common.cuh"
@@ -80,10 +81,9 @@ __device__ __forceinline__ void rf_dft8(C x[8]) {
 // v[b + r*(8/RP)], r < RP.  Returns the outputs in the same slots; `dst`
 // receives the shared-memory index of each slot's output.
 template <typename C, int L, int RP, int DIR>
-__device__ __forceinline__ void rf_pass(C v[8], int t, int Ns, const C* __restrict__ tw, int dst[8]) {
+__device__ __forceinline__ void rf_pass(C v[8], int t, int Ns, const C* __restrict__ tw, int tws, int dst[8]) {
   constexpr int TT = L / 8;
   constexpr int NB = 8 / RP;
-  constexpr int tstride = kTwiddleN / L;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int j = t + TT * b;
@@ -94,7 +94,7 @@ __device__ __forceinline__ void rf_pass(C v[8], int t, int Ns, const C* __restri
     for (int r = 0; r < RP; ++r) x[r] = v[b + r * NB];
     if (Ns > 1) {
 #pragma unroll
-      for (int r = 1; r < RP; ++r) x[r] = cmul(x[r], rf_tw<C, DIR>(tw, r * step, tstride));
+      for (int r = 1; r < RP; ++r) x[r] = cmul(x[r], rf_tw<C, DIR>(tw, r * step, tws));
     }
     if (RP == 2) {
       rf_dft2<C, DIR>(x[0], x[1]);
@@ -112,6 +112,36 @@ __device__ __forceinline__ void rf_pass(C v[8], int t, int Ns, const C* __restri
   }
 }
 
+// Synchronisation of the threads that exchange one sequence: the whole block,
+// one warp (the group lies inside it), or a named barrier over `n` threads.
+struct GroupSync {
+  int id;   // 0: whole block; < 0: warp; > 0: named barrier id
+  int n;    // threads in the named barrier
+  __device__ __forceinline__ void operator()() const {
+    if (id == 0) {
+      __syncthreads();
+    } else if (id < 0) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+    }
+  }
+};
+
+// Group sync for groups of TT consecutive threads (group index tid / TT):
+// warp-level when a group fits in a warp, a named barrier otherwise.
+__device__ __forceinline__ GroupSync group_sync(int TT) {
+  GroupSync g;
+  if (TT <= 32) {
+    g.id = -1;
+    g.n = 32;
+  } else {
+    g.id = 1 + (int)(threadIdx.x / TT);
+    g.n = TT;
+  }
+  return g;
+}
+
 // Full transform of NCOMP sequences held by the same threads (v[c][8] for
 // c < NCOMP).  Element i of sequence c is exchanged through
 // sm[(c*sstride + pad(i)) * estride]: estride = 1 keeps each sequence
@@ -120,7 +150,7 @@ __device__ __forceinline__ void rf_pass(C v[8], int t, int Ns, const C* __restri
 // block must call it (it synchronises the block between passes).
 template <typename C, int L, int DIR, int NCOMP>
 __device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int estride, int t,
-                                       const C* __restrict__ tw) {
+                                       const C* __restrict__ tw, int tws, GroupSync sync = GroupSync{0, 0}) {
   constexpr int M = (L == 8) ? 3 : (L == 16) ? 4 : (L == 32) ? 5 : (L == 64) ? 6 : (L == 128) ? 7
                   : (L == 256) ? 8 : (L == 512) ? 9 : (L == 1024) ? 10 : 11;
   static_assert((1 << M) == L, "L must be a power of two in [8, 2048]");
@@ -137,27 +167,35 @@ __device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int
       for (int c = 0; c < NCOMP; ++c)
 #pragma unroll
         for (int s = 0; s < 8; ++s) sm[(c * sstride + rf_pad(dst[s])) * estride] = v[c][s];
-      __syncthreads();
+      sync();
 #pragma unroll
       for (int c = 0; c < NCOMP; ++c)
 #pragma unroll
         for (int s = 0; s < 8; ++s) v[c][s] = sm[(c * sstride + rf_pad(t + TT * s)) * estride];
-      __syncthreads();
+      sync();
     }
     if (p == 0 && R0 == 2) {
 #pragma unroll
-      for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, 2, DIR>(v[c], t, Ns, tw, dst);
+      for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, 2, DIR>(v[c], t, Ns, tw, tws, dst);
       Ns *= 2;
     } else if (p == 0 && R0 == 4) {
 #pragma unroll
-      for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, 4, DIR>(v[c], t, Ns, tw, dst);
+      for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, 4, DIR>(v[c], t, Ns, tw, tws, dst);
       Ns *= 4;
     } else {
 #pragma unroll
-      for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, 8, DIR>(v[c], t, Ns, tw, dst);
+      for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, 8, DIR>(v[c], t, Ns, tw, tws, dst);
       Ns *= 8;
     }
   }
+}
+
+// Copy W_P^k, k < P, from the global W_4096 table into shared memory
+// (all threads; the caller synchronises before use).
+template <typename C>
+__device__ __forceinline__ void load_twiddles(C* dst, const C* __restrict__ tw4096, int P) {
+  const int stride = kTwiddleN / P;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) dst[i] = tw4096[i * stride];
 }
 
 }  // namespace llg

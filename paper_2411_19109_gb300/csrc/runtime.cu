@@ -14,6 +14,7 @@
 // recomputed once during the reverse sweep, O(sqrt N) states at the default K.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -109,7 +110,8 @@ struct Engine final : llg_ctx {
   RowTile* dRT = nullptr;
   ColTile* dCT = nullptr;
   int R = 2, TX = 8;
-  size_t smem = 0, smem_rows = 0, smem_cols = 0, smem_adj = 0;
+  size_t smem = 0, smem_rows = 0, smem_cols = 0, smem_adj = 0, smem_misc = 0;
+  bool stage_pw = false;
   int* errw = nullptr;
   long long total_nodes = 0, total_spec = 0, total_tens = 0;
   long long K = 1, nckpt = 0, rec_steps = 0;
@@ -121,7 +123,10 @@ struct Engine final : llg_ctx {
   T *psib = nullptr, *psic = nullptr;
   C *spec = nullptr, *tw = nullptr;
   double2* tw64 = nullptr;
-  double *slots = nullptr, *jterm = nullptr, *psisum = nullptr, *Jd = nullptr, *rf = nullptr;
+  // per-(step, row tile) objective partials, per-row-tile terminal and psi
+  // partials, per-instance J
+  double *slots = nullptr, *jterm = nullptr, *psitile = nullptr, *Jd = nullptr, *rf = nullptr;
+  long long total_slots = 0;
   long long* step_base = nullptr;
   unsigned int* maxbits = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -262,22 +267,26 @@ struct Engine final : llg_ctx {
     if (opt.ckpt != LLG_CKPT_PERIODIC && opt.ckpt != LLG_CKPT_STORE_ALL)
       return fail(LLG_EINVAL, "ckpt must be LLG_CKPT_PERIODIC or LLG_CKPT_STORE_ALL");
 
-    // Tile shapes follow from the register FFTs: a row FFT of length Lx
-    // takes Lx/8 threads, so a 128-thread block covers 1024/Lx rows (at most
-    // 64); a column FFT of length Py takes Py/8 threads, so a block covers
-    // 1024/Py columns.  FFT exchange scratch is 3456 complex values.
+    // Tile shapes follow from the register FFTs: one component of a row FFT
+    // of length Lx takes Lx/8 threads, so a 384-thread block covers 1024/Lx
+    // rows; a column FFT of length Py takes Py/8 threads per component, so a
+    // block covers 1024/Py columns.  FFT exchange scratch: kExch complex.
     R = 64;
     TX = 0;
-    smem_cols = smem_adj = (size_t)3456 * sizeof(C);
-    smem_rows = smem_cols;
+    // staging the pointwise node arrays too costs occupancy; measured slower
+    // for the FP32 batch, so it stays off unless LLG_STAGE_POINTWISE=1
+    stage_pw = getenv("LLG_STAGE_POINTWISE") && atoi(getenv("LLG_STAGE_POINTWISE")) != 0;
+    smem_cols = smem_misc = smem_rows = smem_adj = 0;
     for (int i = 0; i < n; ++i) {
       const int Lx = std::max(16, next_pow2(2 * P[i].nx)) / 2;
-      const size_t sb = (size_t)rows_per_tile(Lx) * 3 * rf_padded_len(Lx) * sizeof(C) +
-                        (size_t)(10 * rows_per_tile(Lx) + 8) * P[i].nx * sizeof(T);
-      smem_rows = std::max(smem_rows, sb);
+      const int Py = std::max(8, next_pow2(2 * P[i].ny));
+      smem_cols = std::max(smem_cols, (size_t)(kExch + Py) * sizeof(C));
+      smem_misc = std::max(smem_misc, (size_t)(kExch + 2 * Lx) * sizeof(C));
+      smem_rows = std::max(smem_rows, stage_smem_bytes<T>(Lx, P[i].nx, stage_pw));
+      smem_adj = std::max(smem_adj, adj_smem_bytes<T>(Lx, P[i].nx, stage_pw));
     }
-    smem = std::max(smem_rows, smem_cols);
-    if (smem_rows > 220 * 1024) return fail(LLG_EINVAL, "row tile does not fit in shared memory");
+    smem = std::max(std::max(smem_rows, smem_adj), std::max(smem_cols, smem_misc));
+    if (smem > 220 * 1024) return fail(LLG_EINVAL, "row tile does not fit in shared memory");
     (void)Lx_max;
     (void)Py_max;
     // descriptors, shapes, tiles
@@ -312,7 +321,10 @@ struct Engine final : llg_ctx {
       node_off += d.nodes;
       d.spec_off = spec_off;
       spec_off += (long long)p.ny * 3 * d.Lx;
-      d.slot_off = (long long)i * (N + 1);
+      d.ntile = (p.ny + rows_per_tile(d.Lx) - 1) / rows_per_tile(d.Lx);
+      d.tile_off = (int)rt.size();
+      d.slot_off = total_slots;
+      total_slots += (long long)d.ntile * (N + 1);
       d.rf_off = (long long)i * 3 * (N + 1);
       d.Ms = p.Ms;
       d.cex_x = 2.0 * p.A / (p.Ms * p.dx * p.dx);
@@ -355,7 +367,7 @@ struct Engine final : llg_ctx {
       d.penalty_w = p.penalty_w;
       H[i] = d;
       const int rows = rows_per_tile(d.Lx);
-      for (int y0 = 0; y0 < p.ny; y0 += rows) rt.push_back({i, y0, std::min(rows, p.ny - y0), 0});
+      for (int y0 = 0, k = 0; y0 < p.ny; y0 += rows, ++k) rt.push_back({i, y0, std::min(rows, p.ny - y0), k});
       const int tx = std::max(1, std::min(1024 / d.Py, d.Lx));
       for (int k0 = 0; k0 < d.Lx; k0 += tx) ct.push_back({i, k0, tx, 0});
       TX = std::max(TX, tx);
@@ -383,8 +395,8 @@ struct Engine final : llg_ctx {
               alloc(&tw64, kTwiddleN) && alloc(&recY, S * (4 * rec_steps + 1)) &&
               alloc(&recB, S * std::max(1LL, 4 * rec_steps)) && alloc(&ckpt, S * std::max(1LL, nckpt)) &&
               alloc(&lam, S) && alloc(&G, S) && alloc(&gpart, S) && alloc(&bb[0], S) && alloc(&bb[1], S) &&
-              alloc(&psib, total_nodes) && alloc(&psic, total_nodes) && alloc(&slots, (size_t)n * (N + 1)) &&
-              alloc(&jterm, n) && alloc(&psisum, n) && alloc(&Jd, n) && alloc(&step_base, 1) &&
+              alloc(&psib, total_nodes) && alloc(&psic, total_nodes) && alloc(&slots, (size_t)total_slots) &&
+              alloc(&jterm, rt.size()) && alloc(&psitile, rt.size()) && alloc(&Jd, n) && alloc(&step_base, 1) &&
               alloc(&maxbits, 2 * n) && alloc(&rf, (size_t)n * 3 * (N + 1)) && alloc(&errw, 1);
     if (!ok) return fail(LLG_ENOMEM, "device allocation failed (" + std::to_string(bytes >> 20) + " MiB so far)");
 
@@ -446,7 +458,7 @@ struct Engine final : llg_ctx {
     e = cudaStreamSynchronize(st);
     cudaFree(Gs);
     if (e != cudaSuccess) return cuda_fail(e, "demag tensor");
-    set_smem_limits<T>(smem_rows, smem_cols, smem_adj);
+    set_smem_limits<T>(smem_rows, smem_misc, smem_cols, smem_adj);
     cudaMemsetAsync(errw, 0, sizeof(int), st);
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
@@ -466,6 +478,7 @@ struct Engine final : llg_ctx {
     a.step_base = step_base;
     a.err = errw;
     a.rf = rf;
+    a.stage_pw = stage_pw;
     a.rows_max = R;
     a.dt = dt;
     a.n_from = n_from;
@@ -474,7 +487,7 @@ struct Engine final : llg_ctx {
   }
   void rows(const RowArgs<T>& a, int mode) {
     if (mode == ROW_STAGE) time_begin(0);
-    launch_rows<T>(a, mode, (int)rt.size(), mode == ROW_STAGE ? smem_rows : smem_cols, st);
+    launch_rows<T>(a, mode, (int)rt.size(), mode == ROW_STAGE ? smem_rows : smem_misc, st);
     if (mode == ROW_STAGE) time_end(0);
     ++nlaunch;
   }
@@ -501,8 +514,7 @@ struct Engine final : llg_ctx {
     rows(a, ROW_FFT_ONLY);
   }
   void material(const T* phi) {
-    cudaMemsetAsync(psisum, 0, sizeof(double) * n, st);
-    launch_material_tiles<T>(dI, dRT, (int)rt.size(), phi, psi, dpsi, psisum, st);
+    launch_material_tiles<T>(dI, dRT, (int)rt.size(), phi, psi, dpsi, psitile, st);
     ++nlaunch;
   }
 
@@ -540,8 +552,8 @@ struct Engine final : llg_ctx {
     cudaEventRecord(ev0, st);
     material(phi);
     cudaMemcpyAsync(m, m0_v, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
-    cudaMemsetAsync(slots, 0, sizeof(double) * n * (N + 1), st);
-    cudaMemsetAsync(jterm, 0, sizeof(double) * n, st);
+    cudaMemsetAsync(slots, 0, sizeof(double) * total_slots, st);
+    cudaMemsetAsync(jterm, 0, sizeof(double) * rt.size(), st);
     fft_only(m);
     const T* cur = m;
     for (const Action& ac : fwd) {
@@ -568,10 +580,10 @@ struct Engine final : llg_ctx {
       a.psib = psib;
       a.psic = psic;
       a.jterm = jterm;
-      a.psisum = psisum;
+      a.psitile = psitile;
       rows(a, ROW_TERMINAL);
     }
-    launch_reduce_slots(dI, n, slots, N + 1, jterm, psisum, Jd, st);
+    launch_reduce_slots(dI, n, slots, N + 1, jterm, psitile, Jd, st);
     ++nlaunch;
     if (mT) cudaMemcpyAsync(mT, cur, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
     cudaEventRecord(ev1, st);
@@ -608,6 +620,7 @@ struct Engine final : llg_ctx {
     a.psic = psic;
     a.step_base = step_base;
     a.err = errw;
+    a.stage_pw = stage_pw;
     a.rows_max = R;
     a.dt = dt;
     a.n_from = n_from;

@@ -157,3 +157,26 @@ def test_invalid_sizes_are_rejected():
     bad = W.random_small(6, 4, 1).problem        # nx % 4 != 0
     with pytest.raises(LLGError):
         gpu_solver([type("I", (), {"problem": bad})()])
+
+
+def test_contexts_of_different_sizes_coexist():
+    """A context for a small grid created after one for a large grid must not
+    restrict the large one's launches (kernel attributes are process-wide)."""
+    big = W.random_small(256, 24, 1, seed=31, nsteps=3)
+    small = W.random_small(8, 4, 1, seed=32, nsteps=3)
+    ref = gpu_run([big], "fp32")
+    s_big = gpu_solver([big], "fp32")
+    s_small = gpu_solver([small], "fp32")
+    try:
+        phi = s_small.pack_scalar([small.phi])
+        m0 = s_small.pack_vector([small.m0])
+        s_small.forward(phi, m0)
+        phi = s_big.pack_scalar([big.phi])
+        m0 = s_big.pack_vector([big.m0])
+        J, _ = s_big.forward(phi, m0)
+        g, _ = s_big.adjoint()
+        assert J[0] == ref["J"][0]
+        np.testing.assert_array_equal(s_big.unpack_scalar(g)[0].double().cpu().numpy(), ref["dphi"][0])
+    finally:
+        s_small.close()
+        s_big.close()
