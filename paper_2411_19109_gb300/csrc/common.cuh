@@ -1,6 +1,7 @@
 // Common device types of the LLG solver: complex arithmetic, the per-instance
 // descriptor and the work-tile tables shared by every kernel.
 #pragma once
+#include <cmath>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -45,6 +46,21 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Per-instance coefficients in the compute precision T, converted on the host
+// so that no kernel converts a double inside its node loop (the FP64 pipe of
+// this GPU is narrow; a conversion per node and term showed up as a third
+// of the issue slots of the FP32 stage kernel).
+template <typename T>
+struct Coef {
+  T Ms, cx, cy, kan;
+  T ku[3], B_bias[3], rf_dir[3];
+  T alpha, alpha_edge;   // Gilbert damping inside and at the absorbing edge
+  T absorb_w, inv_absorb_w;  // ramp width in nodes and its reciprocal
+  T gp0;                 // -gamma/(1+alpha^2) for the interior damping
+  T wbox[2];
+  T A, V, escale, ihx2, ihy2;
+};
+
 // Per-instance descriptor (device copy).  Offsets are in elements of the
 // pooled arrays; every node offset is a multiple of 4.
 struct DevInst {
@@ -78,7 +94,37 @@ struct DevInst {
   double escale;                // 1/(K_d V_domain)
   double A;                     // exchange constant
   double area_target, penalty_w;
+  Coef<double> cd;              // the coefficients above in FP64 ...
+  Coef<float> cf;               // ... and rounded to FP32
 };
+
+template <typename T> __device__ __forceinline__ const Coef<T>& coef(const DevInst& I);
+template <> __device__ __forceinline__ const Coef<double>& coef<double>(const DevInst& I) { return I.cd; }
+template <> __device__ __forceinline__ const Coef<float>& coef<float>(const DevInst& I) { return I.cf; }
+
+// Fill both coefficient sets from the FP64 fields of a descriptor.  gp0 is
+// formed with one fused multiply-add, as the device forms -gamma/(1+a^2).
+template <typename T>
+inline void fill_coef_t(Coef<T>& k, const DevInst& d) {
+  k.Ms = (T)d.Ms; k.cx = (T)d.cex_x; k.cy = (T)d.cex_y; k.kan = (T)d.kan;
+  for (int c = 0; c < 3; ++c) {
+    k.ku[c] = (T)d.ku[c];
+    k.B_bias[c] = (T)d.B_bias[c];
+    k.rf_dir[c] = (T)d.rf_dir[c];
+  }
+  k.alpha = (T)d.alpha;
+  k.alpha_edge = (T)d.alpha_edge;
+  k.absorb_w = (T)d.absorb_nodes;
+  k.inv_absorb_w = d.absorb_nodes > 0 ? (T)1 / k.absorb_w : (T)0;
+  k.gp0 = -(T)kGamma / std::fma(k.alpha, k.alpha, (T)1);
+  k.wbox[0] = (T)d.wbox[0];
+  k.wbox[1] = (T)d.wbox[1];
+  k.A = (T)d.A; k.V = (T)d.V; k.escale = (T)d.escale; k.ihx2 = (T)d.ihx2; k.ihy2 = (T)d.ihy2;
+}
+inline void fill_coef(DevInst& d) {
+  fill_coef_t(d.cd, d);
+  fill_coef_t(d.cf, d);
+}
 
 // Cooperative copy of a descriptor into shared memory (all threads call it).
 __device__ __forceinline__ void load_inst(DevInst& dst, const DevInst* src) {
@@ -99,17 +145,16 @@ constexpr int kExch = 3840;
 
 // Dynamic shared memory of the stage and adjoint kernels for a row FFT of
 // length L on rows of nx nodes: exchange scratch, the staged halo rows (4
-// resp. 7 node arrays over R+2 rows), the staged pointwise rows (6 resp. 17
-// node arrays over R rows) and the W_{2L} table.
+// resp. 7 node arrays over R+2 rows) and the W_{2L} table.
 template <typename T>
-__host__ __device__ constexpr size_t stage_smem_bytes(int L, int nx, bool pointwise) {
+__host__ __device__ constexpr size_t stage_smem_bytes(int L, int nx) {
   return (size_t)kExch * sizeof(cplx<T>) + (size_t)4 * (rows_per_tile(L) + 2) * nx * sizeof(T) +
-         (pointwise ? (size_t)6 * rows_per_tile(L) * nx * sizeof(T) : 0) + (size_t)2 * L * sizeof(cplx<T>);
+         (size_t)2 * L * sizeof(cplx<T>);
 }
 template <typename T>
-__host__ __device__ constexpr size_t adj_smem_bytes(int L, int nx, bool pointwise) {
+__host__ __device__ constexpr size_t adj_smem_bytes(int L, int nx) {
   return (size_t)kExch * sizeof(cplx<T>) + (size_t)7 * (rows_per_tile(L) + 2) * nx * sizeof(T) +
-         (pointwise ? (size_t)17 * rows_per_tile(L) * nx * sizeof(T) : 0) + (size_t)2 * L * sizeof(cplx<T>);
+         (size_t)2 * L * sizeof(cplx<T>);
 }
 
 

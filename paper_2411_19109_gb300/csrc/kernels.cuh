@@ -34,7 +34,6 @@ struct RowArgs {
   const double* rf;   // per instance, per step: b_rf sin(2 pi f t) at t = n dt + c dt, c = 0, 1/2, 1
   int local_step;
   int stage;          // 1..4
-  int stage_pw;       // ROW_STAGE: also stage m_n and the accumulator in shared memory
   int rows_max;       // smem sizing: rows per tile
   int demag_only;     // ROW_FIELD
   double t_field;     // ROW_FIELD time
@@ -82,7 +81,6 @@ struct AdjArgs {
   int stage;          // 4..1
   int seed_only;      // 1: only form u_4, Bbar_4 of step n from lambda
   int seed_next;      // stage 1: also seed step n-1 (Yprev/Bprev of its stage 4)
-  int stage_pw;       // also stage the pointwise rows in shared memory
   int rows_max;
   double dt;
   long long n_from;

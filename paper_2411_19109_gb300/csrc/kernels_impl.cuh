@@ -37,20 +37,24 @@ template <typename T>
 __device__ __forceinline__ T edge_weight(T pi, T pj) {
   // w_ij = 2 psi_j/(psi_i + psi_j): harmonic-mean exchange coupling seen by i
   const T s = pi + pj;
-  return s > (T)0 ? (T)2 * pj / s : (T)0;
+  return s > (T)0 ? (T)2 * pj * ((T)1 / s) : (T)0;
 }
 
+// Damping a and g = -gamma/(1+a^2) at node (x, y): the interior values, or a
+// linear ramp from alpha (W nodes from the edge) to alpha_edge (at the edge)
+// inside the absorbing layer.
 template <typename T>
-__device__ __forceinline__ T alpha_at(const DevInst& I, int x, int y) {
-  const T a0 = (T)I.alpha;
-  if (I.absorb_nodes <= 0) return a0;
+__device__ __forceinline__ void damping_at(const DevInst& I, const Coef<T>& K, int x, int y, T& a, T& g) {
+  a = K.alpha;
+  g = K.gp0;
+  if (I.absorb_nodes <= 0) return;
   int d = INT_MAX;
   if (I.absorb_x) d = min(d, min(x, I.nx - 1 - x));
   if (I.absorb_y) d = min(d, min(y, I.ny - 1 - y));
-  if (d == INT_MAX) return a0;
-  const T W = (T)I.absorb_nodes;
-  const T ramp = fmax((T)0, (W - (T)d) / W);
-  return a0 + ((T)I.alpha_edge - a0) * ramp;
+  if (d >= I.absorb_nodes) return;          // ramp (W - d)/W <= 0
+  const T ramp = (K.absorb_w - (T)d) * K.inv_absorb_w;
+  a = K.alpha + (K.alpha_edge - K.alpha) * ramp;
+  g = -(T)kGamma / ((T)1 + a * a);
 }
 
 template <typename T>
@@ -65,10 +69,9 @@ __device__ __forceinline__ T dot3(const T a[3], const T b[3]) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
-// LL form of Eq. 11: k = -gamma/(1+a^2) [Y x B + a Y x (Y x B)]
+// LL form of Eq. 11: k = g [Y x B + a Y x (Y x B)], g = -gamma/(1+a^2)
 template <typename T>
-__device__ __forceinline__ void llg_rhs(const T Y[3], const T B[3], T a, T k[3]) {
-  const T g = -(T)kGamma / ((T)1 + a * a);
+__device__ __forceinline__ void llg_rhs(const T Y[3], const T B[3], T a, T g, T k[3]) {
   T c1[3], c2[3];
   cross3(Y, B, c1);
   cross3(Y, c1, c2);
@@ -79,9 +82,8 @@ __device__ __forceinline__ void llg_rhs(const T Y[3], const T B[3], T a, T k[3])
 //   Bbar = -g [u x Y + a((u.Y) Y - (Y.Y) u)]
 //   mloc = -g [B x u + a((Y.B) u + (u.Y) B - 2 (u.B) Y)]
 template <typename T>
-__device__ __forceinline__ void rhs_vjp(const T u[3], const T Y[3], const T B[3], T a, T Bbar[3],
+__device__ __forceinline__ void rhs_vjp(const T u[3], const T Y[3], const T B[3], T a, T g, T Bbar[3],
                                         T mloc[3]) {
-  const T g = -(T)kGamma / ((T)1 + a * a);
   T uxY[3], Bxu[3];
   cross3(u, Y, uxY);
   cross3(B, u, Bxu);
@@ -484,8 +486,9 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
   const long long off3 = 3 * I.node_off;
   const T* __restrict__ Y = a.Yin + off3;
   const T* __restrict__ ps = a.psi + I.node_off;
-  const T Ms = (T)I.Ms, cx = (T)I.cex_x, cy = (T)I.cex_y, kan = (T)I.kan;
-  const T ku[3] = {(T)I.ku[0], (T)I.ku[1], (T)I.ku[2]};
+  const Coef<T>& K = coef<T>(I);
+  const T Ms = K.Ms, cx = K.cx, cy = K.cy, kan = K.kan;
+  const T ku[3] = {K.ku[0], K.ku[1], K.ku[2]};
   load_twiddles(tw2, a.tw, 2 * L);
   __syncthreads();
   if (MODE != ROW_FFT_ONLY) {
@@ -519,7 +522,7 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
     const T pi = ps[n0];
     T Bex[3] = {0, 0, 0};
     T qpsi = 0, eex = 0;
-    const T hh[4] = {(T)I.ihx2, (T)I.ihx2, (T)I.ihy2, (T)I.ihy2};
+    const T hh[4] = {K.ihx2, K.ihx2, K.ihy2, K.ihy2};
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
       const bool ok = d == 0 ? x + 1 < nx : d == 1 ? x > 0 : d == 2 ? y + 1 < ny : y > 0;
@@ -536,16 +539,16 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
       }
       if (MODE == ROW_TERMINAL && I.objective == 1) {
         const T sp = pi + pj;
-        const T Aij = sp > (T)0 ? (T)2 * (T)I.A * pi * pj / sp : (T)0;
+        const T Aij = sp > (T)0 ? (T)2 * K.A * pi * pj / sp : (T)0;
         eex += (T)0.5 * Aij * dm2 * hh[d];
-        if (sp > (T)0) qpsi += (T)2 * (T)I.A * pj * pj / (sp * sp) * dm2 * hh[d];
+        if (sp > (T)0) qpsi += (T)2 * K.A * pj * pj / (sp * sp) * dm2 * hh[d];
       }
     }
     if (MODE == ROW_TERMINAL) {
       T lam[3] = {0, 0, 0};
       T qp = 0;
       if (I.objective == 1) {
-        const T V = (T)I.V, sc = (T)I.escale;
+        const T V = K.V, sc = K.escale;
         const T mdb = dot3(yi, Bd);
         vsum += -0.5 * (double)V * (double)Ms * (double)pi * (double)mdb + (double)V * (double)eex;
         qp = qpsi * V * sc - V * Ms * mdb * sc;
@@ -560,7 +563,7 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
         for (int b = 0; b < 2; ++b) {
           if (!in_box(I.boxes[b], x, y)) continue;
           const T vv = yi[I.comp];
-          lam[I.comp] += (T)I.wbox[b] * (I.power == 2 ? (T)2 * vv : (T)1);
+          lam[I.comp] += K.wbox[b] * (I.power == 2 ? (T)2 * vv : (T)1);
         }
       }
 #pragma unroll
@@ -572,7 +575,7 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
     // ROW_FIELD: full effective field
     T B[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) B[c] = Bd[c] + Bex[c] + (T)I.B_bias[c];
+    for (int c = 0; c < 3; ++c) B[c] = Bd[c] + Bex[c] + K.B_bias[c];
     if (kan != (T)0) {
       const T dd = dot3(yi, ku);
 #pragma unroll
@@ -580,7 +583,7 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
     }
     if (in_box(I.src, x, y)) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) B[c] += rf * (T)I.rf_dir[c];
+      for (int c = 0; c < 3; ++c) B[c] += rf * K.rf_dir[c];
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) a.Bout[off3 + c * nodes + n0] = B[c];
@@ -623,10 +626,7 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
   C* sx = reinterpret_cast<C*>(smem_raw);
   T* sY = reinterpret_cast<T*>(sx + kExch);
   T* sP = sY + 3 * (RM + 2) * nx;
-  const bool spw = a.stage_pw != 0;           // m_n and the accumulator staged too
-  T* sM = sP + (RM + 2) * nx;                 // m_n rows            [c][r][x]
-  T* sA = sM + 3 * RM * nx;                   // RK accumulator rows [c][r][x]
-  C* tw2 = reinterpret_cast<C*>(spw ? sA + 3 * RM * nx : sM);
+  C* tw2 = reinterpret_cast<C*>(sP + (RM + 2) * nx);
   C* sE = sx + g.rl * 3 * GS;
   C* grp = sE + g.c * GS;
   T* sEr = reinterpret_cast<T*>(sE);
@@ -654,17 +654,9 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
     for (int r = 0; r < nr; ++r)
       for (int c = 0; c < 3; ++c) bulk_load(sx + (r * 3 + c) * GS, row0 + (r * 3 + c) * L, rowb, &bars[0]);
     const unsigned hb = (unsigned)((yhi - ylo) * nx * sizeof(T));
-    const unsigned rb = (unsigned)(nr * nx * sizeof(T));
-    mbar_arrive_expect(&bars[1], 4 * hb + (spw ? (s > 1 ? 6 : 3) * rb : 0));
+    mbar_arrive_expect(&bars[1], 4 * hb);
     stage_halo(sY, RM, a.Yin + off3, nodes, 3, nx, y0, ylo, yhi, &bars[1]);
     stage_halo(sP, RM, a.psi + I.node_off, nodes, 1, nx, y0, ylo, yhi, &bars[1]);
-    if (spw) {
-      for (int c = 0; c < 3; ++c)
-        bulk_load(sM + c * RM * nx, a.m + off3 + c * nodes + (long long)y0 * nx, rb, &bars[1]);
-      if (s > 1)
-        for (int c = 0; c < 3; ++c)
-          bulk_load(sA + c * RM * nx, a.acc + off3 + c * nodes + (long long)y0 * nx, rb, &bars[1]);
-    }
   }
   mbar_wait(&bars[0], 0, a.err);
   {
@@ -674,8 +666,9 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
   mbar_wait(&bars[1], 0, a.err);
   __syncthreads();
 
-  const T Ms = (T)I.Ms, cx = (T)I.cex_x, cy = (T)I.cex_y, kan = (T)I.kan;
-  const T ku[3] = {(T)I.ku[0], (T)I.ku[1], (T)I.ku[2]};
+  const Coef<T>& K = coef<T>(I);
+  const T Ms = K.Ms, cx = K.cx, cy = K.cy, kan = K.kan;
+  const T ku[3] = {K.ku[0], K.ku[1], K.ku[2]};
   const T dt = (T)a.dt;
   const T hs = (s == 1 || s == 2) ? (T)0.5 * dt : dt;     // Y_{s+1} = m + hs k_s
   const int cs = (RM + 2) * nx;                            // component stride of the staged halo
@@ -691,7 +684,7 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       yi[c] = sY[c * cs + oi];
-      B[c] = sEr[2 * c * GS + sl] + (T)I.B_bias[c];
+      B[c] = sEr[2 * c * GS + sl] + K.B_bias[c];
     }
     // exchange: sum over existing neighbours of c_d w_ij (Y_j - Y_i)
 #pragma unroll
@@ -710,26 +703,25 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
     }
     if (in_box(I.src, x, y)) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) B[c] += rf * (T)I.rf_dir[c];
+      for (int c = 0; c < 3; ++c) B[c] += rf * K.rf_dir[c];
     }
-    T k[3];
-    llg_rhs(yi, B, alpha_at<T>(I, x, y), k);
+    T k[3], al, ga;
+    damping_at(I, K, x, y, al, ga);
+    llg_rhs(yi, B, al, ga, k);
     T yn[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long id = off3 + c * nodes + n0;
-      const int so = (c * RM + g.rl) * nx + x;
       if (gB) gB[id] = B[c];
-      const T m0 = spw ? sM[so] : a.m[id];
+      const T m0 = a.m[id];
       if (s == 1) {
         gacc[id] = k[c];
         yn[c] = m0 + hs * k[c];
       } else if (s < 4) {
-        const T a0 = spw ? sA[so] : gacc[id];
-        gacc[id] = a0 + (T)2 * k[c];
+        gacc[id] = gacc[id] + (T)2 * k[c];
         yn[c] = m0 + hs * k[c];
       } else {
-        yn[c] = m0 + dt / (T)6 * ((spw ? sA[so] : gacc[id]) + k[c]);
+        yn[c] = m0 + dt / (T)6 * (gacc[id] + k[c]);
         gmout[id] = yn[c];
         if (gck) gck[id] = yn[c];
       }
@@ -837,16 +829,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   T* sYs = reinterpret_cast<T*>(sx + kExch);
   T* sBb = sYs + 3 * (RM + 2) * nx;
   T* sP = sBb + 3 * (RM + 2) * nx;
-  // pointwise rows [c][r][x]: lambda, gpart, G, dJ/dpsi sum and compensation, Y and B of the next stage
-  T* sL = sP + (RM + 2) * nx;
-  T* sGp = sL + 3 * RM * nx;
-  T* sG = sGp + 3 * RM * nx;
-  T* sQs = sG + 3 * RM * nx;
-  T* sQc = sQs + RM * nx;
-  T* sYp = sQc + RM * nx;
-  T* sBp = sYp + 3 * RM * nx;
-  const bool spw = a.stage_pw != 0;           // pointwise rows staged too
-  C* tw2 = reinterpret_cast<C*>(spw ? sBp + 3 * RM * nx : sL);
+  C* tw2 = reinterpret_cast<C*>(sP + (RM + 2) * nx);
   C* sE = sx + g.rl * 3 * GS;
   C* grp = sE + g.c * GS;
   T* sEr = reinterpret_cast<T*>(sE);
@@ -854,8 +837,9 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   const long long n = (a.step_base ? *a.step_base : 0) + a.local_step;
   const int s = a.stage;
   const long long off3 = 3 * I.node_off;
-  const T Ms = (T)I.Ms, cx = (T)I.cex_x, cy = (T)I.cex_y, kan = (T)I.kan;
-  const T ku[3] = {(T)I.ku[0], (T)I.ku[1], (T)I.ku[2]};
+  const Coef<T>& K = coef<T>(I);
+  const T Ms = K.Ms, cx = K.cx, cy = K.cy, kan = K.kan;
+  const T ku[3] = {K.ku[0], K.ku[1], K.ku[2]};
   const T dt = (T)a.dt;
   T ca = 0, cb = 0;   // u_{s-1} = ca lambda + cb g_s
   if (s == 4) { ca = dt / (T)3; cb = dt; }
@@ -878,39 +862,21 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   load_twiddles(tw2, a.tw, 2 * L);
   __syncthreads();
   if (tid == 0) {
-    const unsigned rb = spw ? (unsigned)(nr * nx * sizeof(T)) : 0u;
-    const long long r0 = (long long)y0 * nx;
-    unsigned bytes = (3 + (emit ? 6 : 0)) * rb;
+    unsigned bytes = 0;
     if (!seed) {
       const unsigned rowb = (unsigned)(L * sizeof(C));
       mbar_arrive_expect(&bars[0], nr * 3 * rowb);
       for (int r = 0; r < nr; ++r)
         for (int c = 0; c < 3; ++c) bulk_load(sx + (r * 3 + c) * GS, row0 + (r * 3 + c) * L, rowb, &bars[0]);
       const unsigned hb = (unsigned)((yhi - ylo) * nx * sizeof(T));
-      bytes += 7 * hb + (3 + (s < 4 ? 3 : 0) + 2) * rb;
+      bytes += 7 * hb;
     }
     mbar_arrive_expect(&bars[1], bytes);
     if (!seed) {
       stage_halo(sYs, RM, a.Ys + off3, nodes, 3, nx, y0, ylo, yhi, &bars[1]);
       stage_halo(sBb, RM, a.Bbar + off3, nodes, 3, nx, y0, ylo, yhi, &bars[1]);
       stage_halo(sP, RM, a.psi + I.node_off, nodes, 1, nx, y0, ylo, yhi, &bars[1]);
-      if (spw) {
-        for (int c = 0; c < 3; ++c) {
-          bulk_load(sGp + c * RM * nx, a.gpart + off3 + c * nodes + r0, rb, &bars[1]);
-          if (s < 4) bulk_load(sG + c * RM * nx, a.G + off3 + c * nodes + r0, rb, &bars[1]);
-        }
-        bulk_load(sQs, a.psib + I.node_off + r0, rb, &bars[1]);
-        bulk_load(sQc, a.psic + I.node_off + r0, rb, &bars[1]);
-      }
     }
-    if (spw)
-      for (int c = 0; c < 3; ++c) {
-        bulk_load(sL + c * RM * nx, a.lam + off3 + c * nodes + r0, rb, &bars[1]);
-        if (emit) {
-          bulk_load(sYp + c * RM * nx, a.Yprev + off3 + c * nodes + r0, rb, &bars[1]);
-          bulk_load(sBp + c * RM * nx, a.Bprev + off3 + c * nodes + r0, rb, &bars[1]);
-        }
-      }
   }
   if (!seed) {
     mbar_wait(&bars[0], 0, a.err);
@@ -926,10 +892,9 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
     const long long n0 = (long long)y * nx + x;
     const int sl = node_slot<T>(x);
-    const int po = g.rl * nx + x;             // pointwise staged index (component stride RM nx)
     T lam[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) lam[c] = spw ? sL[c * RM * nx + po] : glam[off3 + c * nodes + n0];
+    for (int c = 0; c < 3; ++c) lam[c] = glam[off3 + c * nodes + n0];
     T u[3];
     if (seed) {
 #pragma unroll
@@ -942,7 +907,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
       for (int c = 0; c < 3; ++c) {
         yi[c] = sYs[c * cs + oi];
         bi[c] = sBb[c * cs + oi];
-        gg[c] = spw ? sGp[c * RM * nx + po] : ggp[off3 + c * nodes + n0];
+        gg[c] = ggp[off3 + c * nodes + n0];
       }
       T qpsi = 0;
       // exchange transpose (gather form) and its psi derivative
@@ -952,7 +917,9 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
         if (!ok) continue;
         const int oj = oi + (d == 0 ? 1 : d == 1 ? -1 : d == 2 ? nx : -nx);
         const T pj = sP[oj];
-        const T wij = edge_weight(pi, pj), wji = edge_weight(pj, pi);
+        const T sp = pi + pj;
+        const T r = sp > (T)0 ? (T)1 / sp : (T)0;
+        const T wij = (T)2 * pj * r, wji = (T)2 * pi * r;   // edge weights seen by i and by j
         T eij = 0, eji = 0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -961,8 +928,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
           eij += bi[c] * (yj - yi[c]);
           eji += bj * (yi[c] - yj);
         }
-        const T sp = pi + pj;
-        if (sp > (T)0) qpsi += cc[d] * (T)2 * pj / (sp * sp) * (eji - eij);
+        qpsi += cc[d] * wij * r * (eji - eij);          // d w_ij/d psi_i = -2 psi_j/(psi_i+psi_j)^2
       }
       // demag transpose Ms psi_i (N * Bbar)_i and its psi derivative
       T D[3];
@@ -973,7 +939,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
       }
       qpsi += Ms * dot3(yi, D);
       {
-        T sum = spw ? sQs[po] : gpsib[I.node_off + n0], comp = spw ? sQc[po] : gpsic[I.node_off + n0];
+        T sum = gpsib[I.node_off + n0], comp = gpsic[I.node_off + n0];
         kahan_add(sum, comp, qpsi);
         gpsib[I.node_off + n0] = sum;
         gpsic[I.node_off + n0] = comp;
@@ -984,9 +950,9 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
         if (s == 4) {
           gG[id] = gg[c];
         } else if (s > 1) {
-          gG[id] = (spw ? sG[c * RM * nx + po] : gG[id]) + gg[c];
+          gG[id] = gG[id] + gg[c];
         } else {
-          lam[c] += (spw ? sG[c * RM * nx + po] : gG[id]) + gg[c];
+          lam[c] += gG[id] + gg[c];
         }
       }
       if (s == 1) {
@@ -995,7 +961,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
           for (int b = 0; b < 2; ++b) {
             if (!in_box(I.boxes[b], x, y)) continue;
             const T vv = yi[I.comp];
-            lam[I.comp] += (T)I.wbox[b] * (I.power == 2 ? (T)2 * vv : (T)1);
+            lam[I.comp] += K.wbox[b] * (I.power == 2 ? (T)2 * vv : (T)1);
           }
         }
 #pragma unroll
@@ -1008,11 +974,12 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
     T yp[3], bp[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      yp[c] = spw ? sYp[c * RM * nx + po] : a.Yprev[off3 + c * nodes + n0];
-      bp[c] = spw ? sBp[c * RM * nx + po] : a.Bprev[off3 + c * nodes + n0];
+      yp[c] = a.Yprev[off3 + c * nodes + n0];
+      bp[c] = a.Bprev[off3 + c * nodes + n0];
     }
-    T bbar[3], gl[3];
-    rhs_vjp(u, yp, bp, alpha_at<T>(I, x, y), bbar, gl);
+    T bbar[3], gl[3], al, ga;
+    damping_at(I, K, x, y, al, ga);
+    rhs_vjp(u, yp, bp, al, ga, bbar, gl);
     if (kan != (T)0) {
       const T dd = dot3(bbar, ku);
 #pragma unroll

@@ -201,6 +201,7 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   const float2* tw = reinterpret_cast<const float2*>(base + OFF_TW);
   const double2* tw64 = reinterpret_cast<const double2*>(base + OFF_TW64);
 
+  fill_coef(d);
   cudaError_t e = cudaMemcpyAsync(dI, &d, sizeof d, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dRT, rt, sizeof(RowTile) * nrt, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dCT, ct, sizeof(ColTile) * nct, cudaMemcpyHostToDevice, st);

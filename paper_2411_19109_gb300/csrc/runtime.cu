@@ -14,7 +14,6 @@
 // recomputed once during the reverse sweep, O(sqrt N) states at the default K.
 #include <algorithm>
 #include <cmath>
-#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -111,7 +110,6 @@ struct Engine final : llg_ctx {
   ColTile* dCT = nullptr;
   int R = 2, TX = 8;
   size_t smem = 0, smem_rows = 0, smem_cols = 0, smem_adj = 0, smem_misc = 0;
-  bool stage_pw = false;
   int* errw = nullptr;
   long long total_nodes = 0, total_spec = 0, total_tens = 0;
   long long K = 1, nckpt = 0, rec_steps = 0;
@@ -273,17 +271,14 @@ struct Engine final : llg_ctx {
     // block covers 1024/Py columns.  FFT exchange scratch: kExch complex.
     R = 64;
     TX = 0;
-    // staging the pointwise node arrays too costs occupancy; measured slower
-    // for the FP32 batch, so it stays off unless LLG_STAGE_POINTWISE=1
-    stage_pw = getenv("LLG_STAGE_POINTWISE") && atoi(getenv("LLG_STAGE_POINTWISE")) != 0;
     smem_cols = smem_misc = smem_rows = smem_adj = 0;
     for (int i = 0; i < n; ++i) {
       const int Lx = std::max(16, next_pow2(2 * P[i].nx)) / 2;
       const int Py = std::max(8, next_pow2(2 * P[i].ny));
       smem_cols = std::max(smem_cols, (size_t)(kExch + Py) * sizeof(C));
       smem_misc = std::max(smem_misc, (size_t)(kExch + 2 * Lx) * sizeof(C));
-      smem_rows = std::max(smem_rows, stage_smem_bytes<T>(Lx, P[i].nx, stage_pw));
-      smem_adj = std::max(smem_adj, adj_smem_bytes<T>(Lx, P[i].nx, stage_pw));
+      smem_rows = std::max(smem_rows, stage_smem_bytes<T>(Lx, P[i].nx));
+      smem_adj = std::max(smem_adj, adj_smem_bytes<T>(Lx, P[i].nx));
     }
     smem = std::max(std::max(smem_rows, smem_adj), std::max(smem_cols, smem_misc));
     if (smem > 220 * 1024) return fail(LLG_EINVAL, "row tile does not fit in shared memory");
@@ -365,6 +360,7 @@ struct Engine final : llg_ctx {
       d.A = p.A;
       d.area_target = p.area_target;
       d.penalty_w = p.penalty_w;
+      fill_coef(d);
       H[i] = d;
       const int rows = rows_per_tile(d.Lx);
       for (int y0 = 0, k = 0; y0 < p.ny; y0 += rows, ++k) rt.push_back({i, y0, std::min(rows, p.ny - y0), k});
@@ -478,7 +474,6 @@ struct Engine final : llg_ctx {
     a.step_base = step_base;
     a.err = errw;
     a.rf = rf;
-    a.stage_pw = stage_pw;
     a.rows_max = R;
     a.dt = dt;
     a.n_from = n_from;
@@ -620,7 +615,6 @@ struct Engine final : llg_ctx {
     a.psic = psic;
     a.step_base = step_base;
     a.err = errw;
-    a.stage_pw = stage_pw;
     a.rows_max = R;
     a.dt = dt;
     a.n_from = n_from;
