@@ -13,6 +13,7 @@
 // adjoint-state section): only every K-th state is kept and each segment is
 // recomputed once during the reverse sweep, O(sqrt N) states at the default K.
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -135,8 +136,18 @@ struct Engine final : llg_ctx {
   bool have_fwd = false;
   const T* mN_ptr = nullptr;
 
+  // CUDA graphs of whole segments, keyed by (segment kind, length).  A
+  // segment's launches depend only on its kind and length (the first step
+  // number is read from *step_base), so one capture serves every segment of
+  // that shape.  Value: the executable graph and the launches it holds.
+  enum SegKind { SEG_ADVANCE = 0, SEG_RECORD_FWD = 1, SEG_RECORD_ADJ = 2, SEG_REVERSE = 3 };
+  std::map<std::pair<int, long long>, std::pair<cudaGraphExec_t, long long>> graphs;
+  cudaStream_t cap_st = nullptr;   // private stream the captures are recorded on
+
   ~Engine() override {
     if (st) cudaStreamSynchronize(st);
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second.first);
+    if (cap_st) cudaStreamDestroy(cap_st);
     for (void* p : allocs) cudaFree(p);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -540,6 +551,90 @@ struct Engine final : llg_ctx {
     }
   }
 
+  // one backward sweep over a recorded segment of len steps: seed with the
+  // stage-4 inputs of its last step, then the 4 len adjoint stages
+  void reverse_segment(long long len) {
+    int cur = 0;
+    {
+      AdjArgs<T> a = adj_args();
+      a.local_step = (int)(len - 1);
+      a.stage = 4;
+      a.seed_only = 1;
+      a.Yprev = recY_slot(4 * (len - 1) + 3);
+      a.Bprev = recB_slot(4 * (len - 1) + 3);
+      a.BbarOut = bb[cur];
+      adj(a);
+    }
+    for (long long l = len - 1; l >= 0; --l) {
+      for (int s = 4; s >= 1; --s) {
+        cols();
+        AdjArgs<T> a = adj_args();
+        a.local_step = (int)l;
+        a.stage = s;
+        a.Ys = recY_slot(4 * l + s - 1);
+        a.Bbar = bb[cur];
+        a.BbarOut = bb[1 - cur];
+        if (s > 1) {
+          a.Yprev = recY_slot(4 * l + s - 2);
+          a.Bprev = recB_slot(4 * l + s - 2);
+        } else if (l > 0) {
+          a.Yprev = recY_slot(4 * (l - 1) + 3);
+          a.Bprev = recB_slot(4 * (l - 1) + 3);
+          a.seed_next = 1;
+        }
+        adj(a);
+        if (s > 1 || a.seed_next) cur ^= 1;
+      }
+    }
+  }
+
+  void segment_body(int kind, long long len) {
+    if (kind == SEG_REVERSE) {
+      reverse_segment(len);
+      return;
+    }
+    for (long long l = 0; l < len; ++l) step((int)l, kind != SEG_ADVANCE, kind != SEG_RECORD_ADJ);
+  }
+
+  // Runs one segment whose first step number is already in *step_base:
+  // directly, or by replaying (capturing on first use) its CUDA graph.
+  // Graphs are not used while per-launch CUDA-event timing is on.
+  llg_status run_segment(int kind, long long len) {
+    if (!opt.use_graph || opt.time_kernels) {
+      segment_body(kind, len);
+      return LLG_OK;
+    }
+    const auto key = std::make_pair(kind, len);
+    auto it = graphs.find(key);
+    if (it == graphs.end()) {
+      // capture on a private stream (the caller's may be the legacy default
+      // stream, which cannot be captured); nothing runs during capture
+      cudaError_t e = cudaSuccess;
+      if (!cap_st && (e = cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "create capture stream");
+      const long long before = nlaunch;
+      if ((e = cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "begin graph capture");
+      cudaStream_t user = st;
+      st = cap_st;
+      segment_body(kind, len);
+      st = user;
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(cap_st, &g);
+      if (e != cudaSuccess) return cuda_fail(e, "end graph capture");
+      cudaGraphExec_t ge = nullptr;
+      e = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "instantiate segment graph");
+      it = graphs.emplace(key, std::make_pair(ge, nlaunch - before)).first;
+      nlaunch = before;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second.first, st);
+    if (e != cudaSuccess) return cuda_fail(e, "launch segment graph");
+    nlaunch += it->second.second;
+    return LLG_OK;
+  }
+
   // ------------------------------------------------------------ forward
   llg_status forward(const void* phi_v, const void* m0_v, double* J, void* mT) override {
     if (!phi_v || !m0_v || !J) return fail(LLG_EINVAL, "phi, m0 and J must not be NULL");
@@ -556,12 +651,12 @@ struct Engine final : llg_ctx {
         cudaMemcpyAsync(ckpt + (size_t)ac.b * slot(), m, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
       } else if (ac.op == ADVANCE) {
         set_step(ac.a);
-        for (long long l = 0; l < ac.b - ac.a; ++l) step((int)l, false, true);
+        if (llg_status s = run_segment(SEG_ADVANCE, ac.b - ac.a)) return s;
         cur = m;
       } else if (ac.op == RECORD) {
         cudaMemcpyAsync(recY_slot(0), m, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
         set_step(ac.a);
-        for (long long l = 0; l < ac.b - ac.a; ++l) step((int)l, true, true);
+        if (llg_status s = run_segment(SEG_RECORD_FWD, ac.b - ac.a)) return s;
         cur = recY_slot(4 * (ac.b - ac.a));
       }
     }
@@ -631,7 +726,6 @@ struct Engine final : llg_ctx {
     if (!have_fwd) return fail(LLG_ESTATE, "llg_adjoint needs a preceding llg_forward");
     if (!dphi) return fail(LLG_EINVAL, "dJdphi must not be NULL");
     cudaEventRecord(ev0, st);
-    int cur = 0;
     for (const Action& ac : rev) {
       if (ac.op == RESTORE) {
         cudaMemcpyAsync(recY_slot(0), ckpt + (size_t)ac.a * slot(), sizeof(T) * slot(), cudaMemcpyDeviceToDevice,
@@ -639,41 +733,10 @@ struct Engine final : llg_ctx {
         fft_only(recY_slot(0));
       } else if (ac.op == RECORD) {
         set_step(ac.a);
-        for (long long l = 0; l < ac.b - ac.a; ++l) step((int)l, true, false);
+        if (llg_status s = run_segment(SEG_RECORD_ADJ, ac.b - ac.a)) return s;
       } else if (ac.op == REVERSE) {
-        const long long len = ac.a - ac.b;
         set_step(ac.b);
-        {
-          AdjArgs<T> a = adj_args();
-          a.local_step = (int)(len - 1);
-          a.stage = 4;
-          a.seed_only = 1;
-          a.Yprev = recY_slot(4 * (len - 1) + 3);
-          a.Bprev = recB_slot(4 * (len - 1) + 3);
-          a.BbarOut = bb[cur];
-          adj(a);
-        }
-        for (long long l = len - 1; l >= 0; --l) {
-          for (int s = 4; s >= 1; --s) {
-            cols();
-            AdjArgs<T> a = adj_args();
-            a.local_step = (int)l;
-            a.stage = s;
-            a.Ys = recY_slot(4 * l + s - 1);
-            a.Bbar = bb[cur];
-            a.BbarOut = bb[1 - cur];
-            if (s > 1) {
-              a.Yprev = recY_slot(4 * l + s - 2);
-              a.Bprev = recB_slot(4 * l + s - 2);
-            } else if (l > 0) {
-              a.Yprev = recY_slot(4 * (l - 1) + 3);
-              a.Bprev = recB_slot(4 * (l - 1) + 3);
-              a.seed_next = 1;
-            }
-            adj(a);
-            if (s > 1 || a.seed_next) cur ^= 1;
-          }
-        }
+        if (llg_status s = run_segment(SEG_REVERSE, ac.a - ac.b)) return s;
       }
     }
     launch_grad_finish_tiles<T>(dI, dRT, (int)rt.size(), dpsi, psib, psic, static_cast<T*>(dphi), st);

@@ -241,7 +241,7 @@ class Solver:
 
     def __init__(self, problems: Sequence, precision: str = "fp32", ckpt: str = "periodic",
                  seg_len: int = 0, stream=None, rows_per_cta: int = 0, cols_per_cta: int = 0,
-                 time_kernels: bool = False):
+                 time_kernels: bool = False, use_graph: bool = True):
         import torch
         self.torch = torch
         self.problems = list(problems)
@@ -250,7 +250,7 @@ class Solver:
         ck = LLG_CKPT_PERIODIC if ckpt == "periodic" else LLG_CKPT_STORE_ALL
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ctx = llg_create(self.problems, prec, ck, seg_len, self.stream.cuda_stream,
-                              rows_per_cta, cols_per_cta, 0, int(time_kernels))
+                              rows_per_cta, cols_per_cta, int(use_graph), int(time_kernels))
         self.nodes = [p.nx * p.ny * p.nz for p in self.problems]
         self.total = sum(self.nodes)
 
