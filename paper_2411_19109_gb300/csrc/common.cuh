@@ -13,6 +13,18 @@ constexpr double kGamma = 1.76085963023e11;         // rad s^-1 T^-1
 constexpr int kTwiddleN = 4096;                      // W_4096^k table length
 constexpr int kMaxLx = 1024;                         // complex row FFT length (nx <= 1024)
 constexpr int kMaxPy = 1024;                         // column FFT length
+constexpr int kMaxNz = 8;                            // layers of a 3D grid (padded z length <= 16)
+
+// Shared-memory index of element i of an FFT sequence: one pad slot per
+// eight elements spreads strided accesses over the banks.
+__host__ __device__ constexpr int rf_pad(int i) { return i + (i >> 3); }
+__host__ __device__ constexpr int rf_padded_len(int L) { return L + (L >> 3); }
+
+// Padded z length of the demag convolution: 1 for a film, else the power of
+// two >= 2 nz (any length >= 2 nz - 1 gives the same linear convolution).
+__host__ __device__ constexpr int pz_of(int nz) {
+  return nz <= 1 ? 1 : (nz <= 2 ? 4 : (nz <= 4 ? 8 : 16));
+}
 
 template <typename T> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };
@@ -52,13 +64,13 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // of the issue slots of the FP32 stage kernel).
 template <typename T>
 struct Coef {
-  T Ms, cx, cy, kan;
+  T Ms, cx, cy, cz, kan;
   T ku[3], B_bias[3], rf_dir[3];
   T alpha, alpha_edge;   // Gilbert damping inside and at the absorbing edge
   T absorb_w, inv_absorb_w;  // ramp width in nodes and its reciprocal
   T gp0;                 // -gamma/(1+alpha^2) for the interior damping
   T wbox[2];
-  T A, V, escale, ihx2, ihy2;
+  T A, V, escale, ihx2, ihy2, ihz2;
 };
 
 // Per-instance descriptor (device copy).  Offsets are in elements of the
@@ -67,9 +79,11 @@ struct DevInst {
   int nx, ny, nz;
   int Lx, Py;            // complex row FFT length (Px/2) and column FFT length
   int log2Lx, log2Py;
+  int Pz;                // padded z length: 1 for a film (nz = 1), else 2^k >= 2 nz
   int shape;             // index of the demag spectrum table
   int ntile, tile_off;   // row tiles of this instance, index of its first row tile
   long long nodes;       // nx*ny*nz
+  long long layer;       // nx*ny: node stride between z layers
   long long node_off;    // offset into node arrays (per component block: 3*nodes)
   long long spec_off;    // offset into the spectrum pool, complex elements
   long long tens_off;    // offset into the tensor pool, real elements
@@ -90,7 +104,7 @@ struct DevInst {
   int boxes[2][4];
   double wbox[2];               // w_b / |box b|
   double V;                     // cell volume
-  double ihx2, ihy2;            // 1/dx^2, 1/dy^2
+  double ihx2, ihy2, ihz2;      // 1/dx^2, 1/dy^2, 1/dz^2
   double escale;                // 1/(K_d V_domain)
   double A;                     // exchange constant
   double area_target, penalty_w;
@@ -106,7 +120,7 @@ template <> __device__ __forceinline__ const Coef<float>& coef<float>(const DevI
 // formed with one fused multiply-add, as the device forms -gamma/(1+a^2).
 template <typename T>
 inline void fill_coef_t(Coef<T>& k, const DevInst& d) {
-  k.Ms = (T)d.Ms; k.cx = (T)d.cex_x; k.cy = (T)d.cex_y; k.kan = (T)d.kan;
+  k.Ms = (T)d.Ms; k.cx = (T)d.cex_x; k.cy = (T)d.cex_y; k.cz = (T)d.cex_z; k.kan = (T)d.kan;
   for (int c = 0; c < 3; ++c) {
     k.ku[c] = (T)d.ku[c];
     k.B_bias[c] = (T)d.B_bias[c];
@@ -119,7 +133,8 @@ inline void fill_coef_t(Coef<T>& k, const DevInst& d) {
   k.gp0 = -(T)kGamma / std::fma(k.alpha, k.alpha, (T)1);
   k.wbox[0] = (T)d.wbox[0];
   k.wbox[1] = (T)d.wbox[1];
-  k.A = (T)d.A; k.V = (T)d.V; k.escale = (T)d.escale; k.ihx2 = (T)d.ihx2; k.ihy2 = (T)d.ihy2;
+  k.A = (T)d.A; k.V = (T)d.V; k.escale = (T)d.escale;
+  k.ihx2 = (T)d.ihx2; k.ihy2 = (T)d.ihy2; k.ihz2 = (T)d.ihz2;
 }
 inline void fill_coef(DevInst& d) {
   fill_coef_t(d.cd, d);
@@ -158,10 +173,16 @@ __host__ __device__ constexpr size_t adj_smem_bytes(int L, int nx) {
 }
 
 
-// Row tile: rows y0 .. y0+nrows-1 of instance `inst`; k is the tile's index
-// within its instance (the slot of its partial sums, which are added in tile
-// order afterwards so that J does not depend on the order tiles finish).
-struct RowTile { int inst, y0, nrows, k; };
+// Row tile: rows y0 .. y0+nrows-1 of layer z of instance `inst` (a tile never
+// spans two layers); k is the tile's index within its instance (the slot of
+// its partial sums, which are added in tile order afterwards so that J does
+// not depend on the order tiles finish).
+struct RowTile { int inst, z, y0, nrows, k; };
+
+// First node of a row tile in the instance-pooled node arrays.
+__host__ __device__ __forceinline__ long long tile_base(const DevInst& I, const RowTile& t) {
+  return I.node_off + ((long long)t.z * I.ny + t.y0) * I.nx;
+}
 // Column tile: complex columns kx0 .. kx0+ncols-1 of instance `inst`.
 struct ColTile { int inst, kx0, ncols, pad; };
 

@@ -90,6 +90,25 @@ template <typename T>
 void launch_rows(const RowArgs<T>& a, int mode, int ntiles, size_t smem, cudaStream_t st);
 template <typename T>
 void launch_cols(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+// column pass of 3D grids (nz > 1)
+template <typename T>
+void launch_cols3(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+template <typename T>
+void smem_cols3(size_t smem);
+
+// Columns per 3D column tile: enough (component, layer) sequences to fill the
+// block with FFT groups, at least one column.
+__host__ __device__ constexpr int cols3_per_tile(int Py, int nz, int Lx) {
+  return (1024 / (Py * nz)) < 1 ? 1 : ((1024 / (Py * nz)) > Lx ? Lx : 1024 / (Py * nz));
+}
+
+// Dynamic shared memory: 3 nz ncols sequences of (padded Py + 1), W_Py^k for
+// k < Py and W_Pz^k for k < 16.
+template <typename T>
+__host__ __device__ constexpr size_t cols3_smem_bytes(int Py, int nz, int ncols) {
+  return ((size_t)3 * nz * ncols * (rf_padded_len(Py) + 1) + Py + 16) * sizeof(cplx<T>);
+}
+
 template <typename T>
 void launch_adj(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
 template <typename T, int MODE>
@@ -119,7 +138,9 @@ int cols_threads();
 int adj_threads();
 
 template <typename T>
-cudaError_t build_tensor_spectrum(T* table, double2* G, int nx, int ny, int Px, int Py, double dx,
-                                  double dy, double dz, const double2* tw, cudaStream_t st);
+cudaError_t build_tensor_spectrum(T* table, double2* G, int nx, int ny, int nz, int Px, int Py, int Pz,
+                                  double dx, double dy, double dz, const double2* tw, cudaStream_t st);
+long long tensor_table_len(int Px, int Py, int Pz);
+long long tensor_scratch_len(int Px, int Py, int Pz);
 
 }  // namespace llg

@@ -106,84 +106,6 @@ __device__ __forceinline__ void kahan_add(T& sum, T& comp, T v) {
   sum = t;
 }
 
-// ---------------------------------------------------------------------------
-// node-pair access helpers.  A thread owns the adjacent nodes x0 = 2j and
-// x0 + 1 of one row, matching the complex slot z_j = (x[2j], x[2j+1]) of the
-// packed real row FFT.  Pairs are 8-byte (FP32) / 16-byte (FP64) aligned.
-// ---------------------------------------------------------------------------
-
-template <typename T> struct Vec2;
-template <> struct Vec2<float> { using type = float2; };
-template <> struct Vec2<double> { using type = double2; };
-
-template <typename T>
-__device__ __forceinline__ void ld2(const T* p, T& a, T& b) {
-  const typename Vec2<T>::type v = *reinterpret_cast<const typename Vec2<T>::type*>(p);
-  a = v.x;
-  b = v.y;
-}
-template <typename T>
-__device__ __forceinline__ void st2(T* p, T a, T b) {
-  typename Vec2<T>::type v;
-  v.x = a;
-  v.y = b;
-  *reinterpret_cast<typename Vec2<T>::type*>(p) = v;
-}
-
-// Neighbour data of a node pair: index 0 = node x0, 1 = node x0+1.
-// nbr order: +x, -x, +y, -y.
-template <typename T>
-struct PairNbr {
-  T y[2][3];          // own values
-  T p[2];             // own psi
-  T yn[2][4][3];      // neighbour values
-  T pn[2][4];         // neighbour psi
-  bool ok[2][4];      // neighbour exists
-};
-
-// Gather a 3-vector field F (layout [c][node]) and psi around the pair.
-template <typename T>
-__device__ __forceinline__ void gather_pair(const T* __restrict__ F, const T* __restrict__ ps, long long nodes,
-                                            int nx, int ny, int x0, int y, PairNbr<T>& q) {
-  const long long n0 = (long long)y * nx + x0;
-  const bool has_l = x0 > 0, has_r = x0 + 2 < nx, has_u = y + 1 < ny, has_d = y > 0;
-  ld2(ps + n0, q.p[0], q.p[1]);
-  T pu0 = 0, pu1 = 0, pd0 = 0, pd1 = 0;
-  if (has_u) ld2(ps + n0 + nx, pu0, pu1);
-  if (has_d) ld2(ps + n0 - nx, pd0, pd1);
-  const T pl = has_l ? ps[n0 - 1] : (T)0;
-  const T pr = has_r ? ps[n0 + 2] : (T)0;
-  q.pn[0][0] = q.p[1]; q.pn[0][1] = pl; q.pn[0][2] = pu0; q.pn[0][3] = pd0;
-  q.pn[1][0] = pr;     q.pn[1][1] = q.p[0]; q.pn[1][2] = pu1; q.pn[1][3] = pd1;
-  q.ok[0][0] = true;  q.ok[0][1] = has_l; q.ok[0][2] = has_u; q.ok[0][3] = has_d;
-  q.ok[1][0] = has_r; q.ok[1][1] = true;  q.ok[1][2] = has_u; q.ok[1][3] = has_d;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const T* Fc = F + c * nodes;
-    ld2(Fc + n0, q.y[0][c], q.y[1][c]);
-    T u0 = 0, u1 = 0, d0 = 0, d1 = 0;
-    if (has_u) ld2(Fc + n0 + nx, u0, u1);
-    if (has_d) ld2(Fc + n0 - nx, d0, d1);
-    const T l = has_l ? Fc[n0 - 1] : (T)0;
-    const T r = has_r ? Fc[n0 + 2] : (T)0;
-    q.yn[0][0][c] = q.y[1][c]; q.yn[0][1][c] = l; q.yn[0][2][c] = u0; q.yn[0][3][c] = d0;
-    q.yn[1][0][c] = r;         q.yn[1][1][c] = q.y[0][c]; q.yn[1][2][c] = u1; q.yn[1][3][c] = d1;
-  }
-}
-
-// B_ex,i = sum_j c_d w_ij (Y_j - Y_i)
-template <typename T>
-__device__ __forceinline__ void exchange_node(const PairNbr<T>& q, int i, T cx, T cy, T B[3]) {
-  const T cc[4] = {cx, cx, cy, cy};
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    if (!q.ok[i][d]) continue;
-    const T w = cc[d] * edge_weight(q.p[i], q.pn[i][d]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) B[c] += w * (q.yn[i][d][c] - q.y[i][c]);
-  }
-}
-
 template <typename C>
 __device__ __forceinline__ C unpack_one(const C* __restrict__ X, int kk, int L, const C* __restrict__ tw2) {
   // Z[k] = (X_k + conj X_{L-k}) + i W_P^{-k} (X_k - conj X_{L-k}),  P = 2L;  tw2[k] = W_P^k
@@ -404,36 +326,6 @@ __global__ void __launch_bounds__(kColThreads) cols_kernel(ColArgs<T> a) {
 // staged halo rows
 // ---------------------------------------------------------------------------
 
-// Neighbour data of the pair at (x0, row rr of the staged halo arrays).
-template <typename T>
-__device__ __forceinline__ void gather_pair_smem(const T* sF, int cstride, const T* sP, int nx, int ny, int x0,
-                                                 int y, int rr, PairNbr<T>& q) {
-  const bool has_l = x0 > 0, has_r = x0 + 2 < nx, has_u = y + 1 < ny, has_d = y > 0;
-  const int o = rr * nx + x0;
-  ld2(sP + o, q.p[0], q.p[1]);
-  T pu0 = 0, pu1 = 0, pd0 = 0, pd1 = 0;
-  if (has_u) ld2(sP + o + nx, pu0, pu1);
-  if (has_d) ld2(sP + o - nx, pd0, pd1);
-  const T pl = has_l ? sP[o - 1] : (T)0;
-  const T pr = has_r ? sP[o + 2] : (T)0;
-  q.pn[0][0] = q.p[1]; q.pn[0][1] = pl; q.pn[0][2] = pu0; q.pn[0][3] = pd0;
-  q.pn[1][0] = pr;     q.pn[1][1] = q.p[0]; q.pn[1][2] = pu1; q.pn[1][3] = pd1;
-  q.ok[0][0] = true;  q.ok[0][1] = has_l; q.ok[0][2] = has_u; q.ok[0][3] = has_d;
-  q.ok[1][0] = has_r; q.ok[1][1] = true;  q.ok[1][2] = has_u; q.ok[1][3] = has_d;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const T* F = sF + c * cstride + o;
-    ld2(F, q.y[0][c], q.y[1][c]);
-    T u0 = 0, u1 = 0, d0 = 0, d1 = 0;
-    if (has_u) ld2(F + nx, u0, u1);
-    if (has_d) ld2(F - nx, d0, d1);
-    const T l = has_l ? F[-1] : (T)0;
-    const T r = has_r ? F[2] : (T)0;
-    q.yn[0][0][c] = q.y[1][c]; q.yn[0][1][c] = l; q.yn[0][2][c] = u0; q.yn[0][3][c] = d0;
-    q.yn[1][0][c] = r;         q.yn[1][1][c] = q.y[0][c]; q.yn[1][2][c] = u1; q.yn[1][3][c] = d1;
-  }
-}
-
 // Issue the halo copies (rows ylo..yhi-1 of `ncomp` components of F) into a
 // staged array with rows y0-1 .. y0+R; returns the bytes issued.
 template <typename T>
@@ -477,17 +369,19 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
   const bool active = g.rl < tile.nrows;
   const int nx = I.nx, ny = I.ny;
   const int y = tile.y0 + (active ? g.rl : 0);
-  const long long nodes = I.nodes;
+  const int z = tile.z, nz = I.nz;
+  const long long nodes = I.nodes, layer = I.layer;
+  const long long zoff = (long long)z * layer;   // first node of the tile's layer
   C* sE = smem + g.rl * 3 * GS;        // the three sequences of this row slot
   C* grp = sE + g.c * GS;
   T* sEr = reinterpret_cast<T*>(sE);
   C* tw2 = smem + kExch;
-  C* row = a.spec + I.spec_off + (long long)y * 3 * L;
+  C* row = a.spec + I.spec_off + ((long long)z * ny + y) * 3 * L;
   const long long off3 = 3 * I.node_off;
   const T* __restrict__ Y = a.Yin + off3;
   const T* __restrict__ ps = a.psi + I.node_off;
   const Coef<T>& K = coef<T>(I);
-  const T Ms = K.Ms, cx = K.cx, cy = K.cy, kan = K.kan;
+  const T Ms = K.Ms, cx = K.cx, cy = K.cy, cz = K.cz, kan = K.kan;
   const T ku[3] = {K.ku[0], K.ku[1], K.ku[2]};
   load_twiddles(tw2, a.tw, 2 * L);
   __syncthreads();
@@ -499,7 +393,7 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
   double vsum = 0.0;
 #pragma unroll 1
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
-    const long long n0 = (long long)y * nx + x;
+    const long long n0 = zoff + (long long)y * nx + x;
     const int sl = node_slot<T>(x);
     if (MODE == ROW_FFT_ONLY) {
       const T p = ps[n0];
@@ -515,21 +409,23 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
       for (int c = 0; c < 3; ++c) a.Bout[off3 + c * nodes + n0] = Bd[c];
       continue;
     }
-    // own value and the four neighbours (+x, -x, +y, -y) from global memory
+    // own value and the neighbours (+x, -x, +y, -y, +z, -z) from global memory
     T yi[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) yi[c] = Y[c * nodes + n0];
     const T pi = ps[n0];
     T Bex[3] = {0, 0, 0};
     T qpsi = 0, eex = 0;
-    const T hh[4] = {K.ihx2, K.ihx2, K.ihy2, K.ihy2};
+    const T hh[6] = {K.ihx2, K.ihx2, K.ihy2, K.ihy2, K.ihz2, K.ihz2};
+    const T cc[6] = {cx, cx, cy, cy, cz, cz};
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      const bool ok = d == 0 ? x + 1 < nx : d == 1 ? x > 0 : d == 2 ? y + 1 < ny : y > 0;
+    for (int d = 0; d < 6; ++d) {
+      const bool ok = d == 0 ? x + 1 < nx : d == 1 ? x > 0 : d == 2 ? y + 1 < ny : d == 3 ? y > 0
+                    : d == 4 ? z + 1 < nz : z > 0;
       if (!ok) continue;
-      const long long j = n0 + (d == 0 ? 1 : d == 1 ? -1 : d == 2 ? nx : -nx);
+      const long long j = n0 + (d == 0 ? 1 : d == 1 ? -1 : d == 2 ? nx : d == 3 ? -nx : d == 4 ? layer : -layer);
       const T pj = ps[j];
-      const T w = (d < 2 ? cx : cy) * edge_weight(pi, pj);
+      const T w = cc[d] * edge_weight(pi, pj);
       T dm2 = 0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -622,7 +518,9 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
   const bool active = g.rl < nr;
   const int nx = I.nx, ny = I.ny, y0 = tile.y0;
   const int y = y0 + (active ? g.rl : 0);
-  const long long nodes = I.nodes;
+  const int z = tile.z, nz = I.nz;
+  const long long nodes = I.nodes, layer = I.layer;
+  const long long zoff = (long long)z * layer;   // first node of the tile's layer
   C* sx = reinterpret_cast<C*>(smem_raw);
   T* sY = reinterpret_cast<T*>(sx + kExch);
   T* sP = sY + 3 * (RM + 2) * nx;
@@ -631,7 +529,7 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
   C* grp = sE + g.c * GS;
   T* sEr = reinterpret_cast<T*>(sE);
   const long long off3 = 3 * I.node_off;
-  C* row0 = a.spec + I.spec_off + (long long)y0 * 3 * L;
+  C* row0 = a.spec + I.spec_off + ((long long)z * ny + y0) * 3 * L;
   const int s = a.stage;
   const long long n = (a.step_base ? *a.step_base : 0) + a.local_step;
   const int ylo = max(0, y0 - 1), yhi = min(ny, y0 + nr + 1);
@@ -655,8 +553,8 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
       for (int c = 0; c < 3; ++c) bulk_load(sx + (r * 3 + c) * GS, row0 + (r * 3 + c) * L, rowb, &bars[0]);
     const unsigned hb = (unsigned)((yhi - ylo) * nx * sizeof(T));
     mbar_arrive_expect(&bars[1], 4 * hb);
-    stage_halo(sY, RM, a.Yin + off3, nodes, 3, nx, y0, ylo, yhi, &bars[1]);
-    stage_halo(sP, RM, a.psi + I.node_off, nodes, 1, nx, y0, ylo, yhi, &bars[1]);
+    stage_halo(sY, RM, a.Yin + off3 + zoff, nodes, 3, nx, y0, ylo, yhi, &bars[1]);
+    stage_halo(sP, RM, a.psi + I.node_off + zoff, nodes, 1, nx, y0, ylo, yhi, &bars[1]);
   }
   mbar_wait(&bars[0], 0, a.err);
   {
@@ -667,7 +565,7 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
   __syncthreads();
 
   const Coef<T>& K = coef<T>(I);
-  const T Ms = K.Ms, cx = K.cx, cy = K.cy, kan = K.kan;
+  const T Ms = K.Ms, cx = K.cx, cy = K.cy, cz = K.cz, kan = K.kan;
   const T ku[3] = {K.ku[0], K.ku[1], K.ku[2]};
   const T dt = (T)a.dt;
   const T hs = (s == 1 || s == 2) ? (T)0.5 * dt : dt;     // Y_{s+1} = m + hs k_s
@@ -676,7 +574,7 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
   const bool objective_step = s == 4 && a.slots != nullptr && I.objective == 0 && (n + 1) >= a.n_from;
 #pragma unroll 1
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
-    const long long n0 = (long long)y * nx + x;
+    const long long n0 = zoff + (long long)y * nx + x;
     const int sl = node_slot<T>(x);
     const int oi = (g.rl + 1) * nx + x;
     const T pi = sP[oi];
@@ -695,6 +593,15 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
       const T w = (d < 2 ? cx : cy) * edge_weight(pi, sP[oj]);
 #pragma unroll
       for (int c = 0; c < 3; ++c) B[c] += w * (sY[c * cs + oj] - yi[c]);
+    }
+    // the layers above and below (3D), from global memory
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      if (d == 0 ? z + 1 >= nz : z == 0) continue;
+      const long long j = n0 + (d == 0 ? layer : -layer);
+      const T w = cz * edge_weight(pi, a.psi[I.node_off + j]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) B[c] += w * (a.Yin[off3 + c * nodes + j] - yi[c]);
     }
     if (kan != (T)0) {
       const T dd = dot3(yi, ku);
@@ -747,7 +654,8 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
     }
   }
   __syncthreads();
-  row_forward_comp<T, L>(grp, nx / 2, a.spec + I.spec_off + (long long)y * 3 * L + g.c * L, active, g.t, tw2);
+  row_forward_comp<T, L>(grp, nx / 2, a.spec + I.spec_off + ((long long)z * ny + y) * 3 * L + g.c * L, active, g.t,
+                         tw2);
 }
 
 template <typename T, int MODE>
@@ -824,7 +732,9 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   const bool active = g.rl < nr;
   const int nx = I.nx, ny = I.ny, y0 = tile.y0;
   const int y = y0 + (active ? g.rl : 0);
-  const long long nodes = I.nodes;
+  const int z = tile.z, nz = I.nz;
+  const long long nodes = I.nodes, layer = I.layer;
+  const long long zoff = (long long)z * layer;   // first node of the tile's layer
   C* sx = reinterpret_cast<C*>(smem_raw);
   T* sYs = reinterpret_cast<T*>(sx + kExch);
   T* sBb = sYs + 3 * (RM + 2) * nx;
@@ -833,12 +743,12 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   C* sE = sx + g.rl * 3 * GS;
   C* grp = sE + g.c * GS;
   T* sEr = reinterpret_cast<T*>(sE);
-  C* row0 = a.spec + I.spec_off + (long long)y0 * 3 * L;
+  C* row0 = a.spec + I.spec_off + ((long long)z * ny + y0) * 3 * L;
   const long long n = (a.step_base ? *a.step_base : 0) + a.local_step;
   const int s = a.stage;
   const long long off3 = 3 * I.node_off;
   const Coef<T>& K = coef<T>(I);
-  const T Ms = K.Ms, cx = K.cx, cy = K.cy, kan = K.kan;
+  const T Ms = K.Ms, cx = K.cx, cy = K.cy, cz = K.cz, kan = K.kan;
   const T ku[3] = {K.ku[0], K.ku[1], K.ku[2]};
   const T dt = (T)a.dt;
   T ca = 0, cb = 0;   // u_{s-1} = ca lambda + cb g_s
@@ -873,9 +783,9 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
     }
     mbar_arrive_expect(&bars[1], bytes);
     if (!seed) {
-      stage_halo(sYs, RM, a.Ys + off3, nodes, 3, nx, y0, ylo, yhi, &bars[1]);
-      stage_halo(sBb, RM, a.Bbar + off3, nodes, 3, nx, y0, ylo, yhi, &bars[1]);
-      stage_halo(sP, RM, a.psi + I.node_off, nodes, 1, nx, y0, ylo, yhi, &bars[1]);
+      stage_halo(sYs, RM, a.Ys + off3 + zoff, nodes, 3, nx, y0, ylo, yhi, &bars[1]);
+      stage_halo(sBb, RM, a.Bbar + off3 + zoff, nodes, 3, nx, y0, ylo, yhi, &bars[1]);
+      stage_halo(sP, RM, a.psi + I.node_off + zoff, nodes, 1, nx, y0, ylo, yhi, &bars[1]);
     }
   }
   if (!seed) {
@@ -890,7 +800,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   const T cc[4] = {cx, cx, cy, cy};
 #pragma unroll 1
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
-    const long long n0 = (long long)y * nx + x;
+    const long long n0 = zoff + (long long)y * nx + x;
     const int sl = node_slot<T>(x);
     T lam[3];
 #pragma unroll
@@ -929,6 +839,25 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
           eji += bj * (yi[c] - yj);
         }
         qpsi += cc[d] * wij * r * (eji - eij);          // d w_ij/d psi_i = -2 psi_j/(psi_i+psi_j)^2
+      }
+      // the same across the layers above and below (3D), from global memory
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        if (d == 0 ? z + 1 >= nz : z == 0) continue;
+        const long long j = n0 + (d == 0 ? layer : -layer);
+        const T pj = a.psi[I.node_off + j];
+        const T sp = pi + pj;
+        const T r = sp > (T)0 ? (T)1 / sp : (T)0;
+        const T wij = (T)2 * pj * r, wji = (T)2 * pi * r;
+        T eij = 0, eji = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const T yj = a.Ys[off3 + c * nodes + j], bj = a.Bbar[off3 + c * nodes + j];
+          gg[c] += cz * (wji * bj - wij * bi[c]);
+          eij += bi[c] * (yj - yi[c]);
+          eji += bj * (yi[c] - yj);
+        }
+        qpsi += cz * wij * r * (eji - eij);
       }
       // demag transpose Ms psi_i (N * Bbar)_i and its psi derivative
       T D[3];
@@ -995,7 +924,8 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   }
   if (!emit) return;
   __syncthreads();
-  row_forward_comp<T, L>(grp, nx / 2, a.spec + I.spec_off + (long long)y * 3 * L + g.c * L, active, g.t, tw2);
+  row_forward_comp<T, L>(grp, nx / 2, a.spec + I.spec_off + ((long long)z * ny + y) * 3 * L + g.c * L, active, g.t,
+                         tw2);
 }
 
 template <typename T>
@@ -1029,7 +959,7 @@ __global__ void material_kernel(const DevInst* inst, const RowTile* tiles, const
   __shared__ double red[32];
   const RowTile tile = tiles[blockIdx.x];
   const DevInst& I = inst[tile.inst];
-  const long long base = I.node_off + (long long)tile.y0 * I.nx;
+  const long long base = tile_base(I, tile);
   const int cnt = tile.nrows * I.nx;
   double acc = 0.0;
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
@@ -1048,7 +978,7 @@ __global__ void grad_finish_kernel(const DevInst* inst, const RowTile* tiles, co
                                    const T* psic, T* out) {
   const RowTile tile = tiles[blockIdx.x];
   const DevInst& I = inst[tile.inst];
-  const long long base = I.node_off + (long long)tile.y0 * I.nx;
+  const long long base = tile_base(I, tile);
   const int cnt = tile.nrows * I.nx;
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
     const double g = ((double)psib[base + e] - (double)psic[base + e]) * (double)dpsi[base + e];
@@ -1068,7 +998,7 @@ __global__ void levelset_update_kernel(const DevInst* inst, const RowTile* tiles
                                        const unsigned char* mask, T lr, unsigned int* maxbits) {
   const RowTile tile = tiles[blockIdx.x];
   const DevInst& I = inst[tile.inst];
-  const long long base = I.node_off + (long long)tile.y0 * I.nx;
+  const long long base = tile_base(I, tile);
   const int cnt = tile.nrows * I.nx;
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
     if (!mask[base + e]) continue;
@@ -1088,7 +1018,7 @@ __global__ void levelset_scale_kernel(const DevInst* inst, const RowTile* tiles,
                                       const unsigned char* mask, const unsigned int* maxbits) {
   const RowTile tile = tiles[blockIdx.x];
   const DevInst& I = inst[tile.inst];
-  const long long base = I.node_off + (long long)tile.y0 * I.nx;
+  const long long base = tile_base(I, tile);
   const int cnt = tile.nrows * I.nx;
   const T mx = max_from_bits(maxbits + 2 * tile.inst, (T*)nullptr);
   if (!(mx > (T)0)) return;

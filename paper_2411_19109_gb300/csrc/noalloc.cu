@@ -154,10 +154,11 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   const int Py = std::max(8, pow2_at_least(2 * p.ny));
   DevInst d;
   std::memset(&d, 0, sizeof d);
-  d.nx = p.nx; d.ny = p.ny; d.nz = 1;
+  d.nx = p.nx; d.ny = p.ny; d.nz = 1; d.Pz = 1;
   d.Lx = Px / 2; d.Py = Py;
   d.log2Lx = log2_of(d.Lx); d.log2Py = log2_of(Py);
   d.nodes = (long long)p.nx * p.ny;
+  d.layer = d.nodes;
   d.Ms = p.Ms;
   d.cex_x = 2.0 * p.A / (p.Ms * p.dx * p.dx);
   d.cex_y = 2.0 * p.A / (p.Ms * p.dy * p.dy);
@@ -183,7 +184,7 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   ColTile ct[NA_MAX_COL_TILES];
   int nrt = 0, nct = 0;
   const int rows = rows_per_tile(d.Lx);
-  for (int y0 = 0; y0 < p.ny; y0 += rows, ++nrt) rt[nrt] = {0, y0, std::min(rows, p.ny - y0), nrt};
+  for (int y0 = 0; y0 < p.ny; y0 += rows, ++nrt) rt[nrt] = {0, 0, y0, std::min(rows, p.ny - y0), nrt};
   d.ntile = nrt;
   d.tile_off = 0;
   const int tx = std::max(1, std::min(1024 / Py, d.Lx));
@@ -207,7 +208,7 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   if (e == cudaSuccess) e = cudaMemcpyAsync(dCT, ct, sizeof(ColTile) * nct, cudaMemcpyHostToDevice, st);
   // the demag spectrum of this grid, FP64 on the device (G is cleared inside)
   if (e == cudaSuccess)
-    e = build_tensor_spectrum<float>(tens, G, p.nx, p.ny, Px, Py, p.dx, p.dy, p.dz, tw64, st);
+    e = build_tensor_spectrum<float>(tens, G, p.nx, p.ny, 1, Px, Py, 1, p.dx, p.dy, p.dz, tw64, st);
   // psi from phi (the per-tile psi partials are not used by the field)
   if (e != cudaSuccess) {
     if (err_msg) *err_msg = "llg_field_noalloc: set-up copies or tensor build failed";

@@ -19,8 +19,6 @@
 
 namespace llg {
 
-__host__ __device__ constexpr int rf_pad(int i) { return i + (i >> 3); }
-__host__ __device__ constexpr int rf_padded_len(int L) { return L + (L >> 3); }
 
 template <typename C, int DIR>
 __device__ __forceinline__ C rf_tw(const C* __restrict__ tw, int m, int stride) {
@@ -115,13 +113,14 @@ __device__ __forceinline__ void rf_pass(C v[8], int t, int Ns, const C* __restri
 // Synchronisation of the threads that exchange one sequence: the whole block,
 // one warp (the group lies inside it), or a named barrier over `n` threads.
 struct GroupSync {
-  int id;   // 0: whole block; < 0: warp; > 0: named barrier id
-  int n;    // threads in the named barrier
+  int id;            // 0: whole block; < 0: the group's lanes of one warp; > 0: named barrier id
+  int n;             // threads in the named barrier
+  unsigned mask;     // id < 0: the lanes of the group
   __device__ __forceinline__ void operator()() const {
     if (id == 0) {
       __syncthreads();
     } else if (id < 0) {
-      __syncwarp();
+      __syncwarp(mask);
     } else {
       asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
     }
@@ -129,12 +128,16 @@ struct GroupSync {
 };
 
 // Group sync for groups of TT consecutive threads (group index tid / TT):
-// warp-level when a group fits in a warp, a named barrier otherwise.
+// the group's own lanes of its warp when a group fits in a warp, a named
+// barrier otherwise.  Either way only the group's threads take part, so a
+// group may skip a transform while other groups of its warp or block run one.
 __device__ __forceinline__ GroupSync group_sync(int TT) {
   GroupSync g;
+  g.mask = 0xffffffffu;
   if (TT <= 32) {
     g.id = -1;
     g.n = 32;
+    if (TT < 32) g.mask = ((1u << TT) - 1u) << ((threadIdx.x & 31) / TT * TT);
   } else {
     g.id = 1 + (int)(threadIdx.x / TT);
     g.n = TT;

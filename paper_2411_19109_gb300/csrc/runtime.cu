@@ -105,12 +105,13 @@ struct Engine final : llg_ctx {
 
   std::vector<DevInst> H;
   std::vector<RowTile> rt;
-  std::vector<ColTile> ct;
+  std::vector<ColTile> ct, ct3;    // column tiles of films and of 3D grids
   DevInst* dI = nullptr;
   RowTile* dRT = nullptr;
   ColTile* dCT = nullptr;
+  ColTile* dCT3 = nullptr;
   int R = 2, TX = 8;
-  size_t smem = 0, smem_rows = 0, smem_cols = 0, smem_adj = 0, smem_misc = 0;
+  size_t smem = 0, smem_rows = 0, smem_cols = 0, smem_c3 = 0, smem_adj = 0, smem_misc = 0;
   int* errw = nullptr;
   long long total_nodes = 0, total_spec = 0, total_tens = 0;
   long long K = 1, nckpt = 0, rec_steps = 0;
@@ -256,7 +257,10 @@ struct Engine final : llg_ctx {
         snprintf(buf, sizeof buf, "instance %d: ny=%d must be in [1, %d]", i, p.ny, kMaxPy / 2);
         return fail(LLG_EINVAL, buf);
       }
-      if (p.nz != 1) return fail(LLG_EINVAL, "only single-layer films (nz == 1) are supported");
+      if (p.nz < 1 || p.nz > kMaxNz) {
+        snprintf(buf, sizeof buf, "instance %d: nz=%d must be in [1, %d]", i, p.nz, kMaxNz);
+        return fail(LLG_EINVAL, buf);
+      }
       if (!(p.dx > 0 && p.dy > 0 && p.dz > 0 && p.Ms > 0 && p.dt > 0 && p.A >= 0))
         return fail(LLG_EINVAL, "dx, dy, dz, Ms, dt must be > 0 and A >= 0");
       if (p.nsteps < 0 || p.nsteps != N || p.n_from != n_from || p.dt != dt)
@@ -286,17 +290,22 @@ struct Engine final : llg_ctx {
     for (int i = 0; i < n; ++i) {
       const int Lx = std::max(16, next_pow2(2 * P[i].nx)) / 2;
       const int Py = std::max(8, next_pow2(2 * P[i].ny));
-      smem_cols = std::max(smem_cols, (size_t)(kExch + Py) * sizeof(C));
+      if (P[i].nz > 1)
+        smem_c3 = std::max(smem_c3, cols3_smem_bytes<T>(Py, P[i].nz, cols3_per_tile(Py, P[i].nz, Lx)));
+      else
+        smem_cols = std::max(smem_cols, (size_t)(kExch + Py) * sizeof(C));
       smem_misc = std::max(smem_misc, (size_t)(kExch + 2 * Lx) * sizeof(C));
       smem_rows = std::max(smem_rows, stage_smem_bytes<T>(Lx, P[i].nx));
       smem_adj = std::max(smem_adj, adj_smem_bytes<T>(Lx, P[i].nx));
     }
-    smem = std::max(std::max(smem_rows, smem_adj), std::max(smem_cols, smem_misc));
-    if (smem > 220 * 1024) return fail(LLG_EINVAL, "row tile does not fit in shared memory");
+    smem = std::max(std::max(smem_rows, smem_adj), std::max(std::max(smem_cols, smem_c3), smem_misc));
+    if (smem > 220 * 1024)
+      return fail(LLG_EINVAL, "a row or column tile does not fit in shared memory (3D: nz * 2ny too large for "
+                              "this precision)");
     (void)Lx_max;
     (void)Py_max;
     // descriptors, shapes, tiles
-    struct Shape { int nx, ny; double dx, dy, dz; long long off; int Px, Py; };
+    struct Shape { int nx, ny, nz; double dx, dy, dz; long long off; int Px, Py, Pz; };
     std::vector<Shape> shapes;
     H.resize(n);
     long long node_off = 0, spec_off = 0, tens_off = 0;
@@ -304,7 +313,8 @@ struct Engine final : llg_ctx {
       const llg_problem& p = P[i];
       DevInst d;
       std::memset(&d, 0, sizeof d);
-      d.nx = p.nx; d.ny = p.ny; d.nz = 1;
+      d.nx = p.nx; d.ny = p.ny; d.nz = p.nz;
+      d.Pz = pz_of(p.nz);
       const int Px = std::max(16, next_pow2(2 * p.nx));
       d.Lx = Px / 2;
       d.Py = std::max(8, next_pow2(2 * p.ny));
@@ -312,22 +322,23 @@ struct Engine final : llg_ctx {
       d.log2Py = ilog2(d.Py);
       int sid = -1;
       for (size_t s = 0; s < shapes.size(); ++s)
-        if (shapes[s].nx == p.nx && shapes[s].ny == p.ny && shapes[s].dx == p.dx && shapes[s].dy == p.dy &&
-            shapes[s].dz == p.dz)
+        if (shapes[s].nx == p.nx && shapes[s].ny == p.ny && shapes[s].nz == p.nz && shapes[s].dx == p.dx &&
+            shapes[s].dy == p.dy && shapes[s].dz == p.dz)
           sid = (int)s;
       if (sid < 0) {
-        shapes.push_back({p.nx, p.ny, p.dx, p.dy, p.dz, tens_off, Px, d.Py});
-        tens_off += (long long)(Px / 2 + 1) * (d.Py / 2 + 1) * 4;
+        shapes.push_back({p.nx, p.ny, p.nz, p.dx, p.dy, p.dz, tens_off, Px, d.Py, d.Pz});
+        tens_off += tensor_table_len(Px, d.Py, d.Pz);
         sid = (int)shapes.size() - 1;
       }
       d.shape = sid;
       d.tens_off = shapes[sid].off;
-      d.nodes = (long long)p.nx * p.ny;
+      d.layer = (long long)p.nx * p.ny;
+      d.nodes = d.layer * p.nz;
       d.node_off = node_off;
       node_off += d.nodes;
       d.spec_off = spec_off;
-      spec_off += (long long)p.ny * 3 * d.Lx;
-      d.ntile = (p.ny + rows_per_tile(d.Lx) - 1) / rows_per_tile(d.Lx);
+      spec_off += (long long)p.nz * p.ny * 3 * d.Lx;
+      d.ntile = p.nz * ((p.ny + rows_per_tile(d.Lx) - 1) / rows_per_tile(d.Lx));
       d.tile_off = (int)rt.size();
       d.slot_off = total_slots;
       total_slots += (long long)d.ntile * (N + 1);
@@ -361,12 +372,13 @@ struct Engine final : llg_ctx {
         if (x1 < x0) x1 = x0;
         if (y1 < y0) y1 = y0;
         d.boxes[b][0] = x0; d.boxes[b][1] = x1; d.boxes[b][2] = y0; d.boxes[b][3] = y1;
-        const long long cnt = (long long)(x1 - x0) * (y1 - y0);
+        const long long cnt = (long long)(x1 - x0) * (y1 - y0) * p.nz;   // boxes span every layer
         d.wbox[b] = cnt > 0 ? p.weights[b] / (double)cnt : 0.0;
       }
       d.V = p.dx * p.dy * p.dz;
       d.ihx2 = 1.0 / (p.dx * p.dx);
       d.ihy2 = 1.0 / (p.dy * p.dy);
+      d.ihz2 = 1.0 / (p.dz * p.dz);
       d.escale = 1.0 / (0.5 * kMu0 * p.Ms * p.Ms * d.V * (double)d.nodes);
       d.A = p.A;
       d.area_target = p.area_target;
@@ -374,9 +386,10 @@ struct Engine final : llg_ctx {
       fill_coef(d);
       H[i] = d;
       const int rows = rows_per_tile(d.Lx);
-      for (int y0 = 0, k = 0; y0 < p.ny; y0 += rows, ++k) rt.push_back({i, y0, std::min(rows, p.ny - y0), k});
-      const int tx = std::max(1, std::min(1024 / d.Py, d.Lx));
-      for (int k0 = 0; k0 < d.Lx; k0 += tx) ct.push_back({i, k0, tx, 0});
+      for (int z = 0, k = 0; z < p.nz; ++z)
+        for (int y0 = 0; y0 < p.ny; y0 += rows, ++k) rt.push_back({i, z, y0, std::min(rows, p.ny - y0), k});
+      const int tx = p.nz > 1 ? cols3_per_tile(d.Py, p.nz, d.Lx) : std::max(1, std::min(1024 / d.Py, d.Lx));
+      for (int k0 = 0; k0 < d.Lx; k0 += tx) (p.nz > 1 ? ct3 : ct).push_back({i, k0, std::min(tx, d.Lx - k0), 0});
       TX = std::max(TX, tx);
     }
     total_nodes = node_off;
@@ -396,7 +409,8 @@ struct Engine final : llg_ctx {
       if (a.op == RECORD) rec_steps = std::max(rec_steps, a.b - a.a);
 
     const size_t S = slot();
-    bool ok = alloc(&dI, n) && alloc(&dRT, rt.size()) && alloc(&dCT, ct.size()) && alloc(&psi, total_nodes) &&
+    bool ok = alloc(&dI, n) && alloc(&dRT, rt.size()) && alloc(&dCT, std::max<size_t>(1, ct.size())) &&
+              alloc(&dCT3, std::max<size_t>(1, ct3.size())) && alloc(&psi, total_nodes) &&
               alloc(&dpsi, total_nodes) && alloc(&m, S) && alloc(&Ya, S) && alloc(&Yb, S) && alloc(&acc, S) &&
               alloc(&tens, total_tens) && alloc(&spec, total_spec) && alloc(&tw, kTwiddleN) &&
               alloc(&tw64, kTwiddleN) && alloc(&recY, S * (4 * rec_steps + 1)) &&
@@ -413,8 +427,13 @@ struct Engine final : llg_ctx {
     if ((e = cudaMemcpyAsync(dRT, rt.data(), sizeof(RowTile) * rt.size(), cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
       return cuda_fail(e, "upload row tiles");
-    if ((e = cudaMemcpyAsync(dCT, ct.data(), sizeof(ColTile) * ct.size(), cudaMemcpyHostToDevice, st)) !=
-        cudaSuccess)
+    if (!ct.empty() &&
+        (e = cudaMemcpyAsync(dCT, ct.data(), sizeof(ColTile) * ct.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+      return cuda_fail(e, "upload column tiles");
+    if (!ct3.empty() &&
+        (e = cudaMemcpyAsync(dCT3, ct3.data(), sizeof(ColTile) * ct3.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
       return cuda_fail(e, "upload column tiles");
     {
       std::vector<double2> h64(kTwiddleN);
@@ -448,15 +467,16 @@ struct Engine final : llg_ctx {
     }
     // demag spectra, FP64 scratch of the largest shape
     size_t gmax = 0;
-    for (const Shape& s : shapes) gmax = std::max(gmax, (size_t)4 * s.Px * s.Py);
+    for (const Shape& s : shapes) gmax = std::max(gmax, (size_t)tensor_scratch_len(s.Px, s.Py, s.Pz));
     double2* Gs = nullptr;
     if (cudaMalloc(&Gs, gmax * sizeof(double2)) != cudaSuccess) {
       cudaGetLastError();
       return fail(LLG_ENOMEM, "tensor scratch allocation failed");
     }
     for (const Shape& s : shapes) {
-      e = build_tensor_spectrum<T>(tens + s.off, Gs, s.nx, s.ny, s.Px, s.Py, s.dx, s.dy, s.dz, tw64, st);
-      nlaunch += 5;
+      e = build_tensor_spectrum<T>(tens + s.off, Gs, s.nx, s.ny, s.nz, s.Px, s.Py, s.Pz, s.dx, s.dy, s.dz, tw64,
+                                   st);
+      nlaunch += s.Pz > 1 ? 6 : 5;
       if (e != cudaSuccess) {
         cudaFree(Gs);
         return cuda_fail(e, "demag tensor");
@@ -466,6 +486,7 @@ struct Engine final : llg_ctx {
     cudaFree(Gs);
     if (e != cudaSuccess) return cuda_fail(e, "demag tensor");
     set_smem_limits<T>(smem_rows, smem_misc, smem_cols, smem_adj);
+    smem_cols3<T>(smem_c3);
     cudaMemsetAsync(errw, 0, sizeof(int), st);
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
@@ -506,9 +527,16 @@ struct Engine final : llg_ctx {
     c.tens = tens;
     c.cols_max = TX;
     time_begin(1);
-    launch_cols<T>(c, (int)ct.size(), smem_cols, st);
+    if (!ct.empty()) {
+      launch_cols<T>(c, (int)ct.size(), smem_cols, st);
+      ++nlaunch;
+    }
+    if (!ct3.empty()) {
+      c.tiles = dCT3;
+      launch_cols3<T>(c, (int)ct3.size(), smem_c3, st);
+      ++nlaunch;
+    }
     time_end(1);
-    ++nlaunch;
   }
   void set_step(long long v) {
     launch_set_step(step_base, v, st);

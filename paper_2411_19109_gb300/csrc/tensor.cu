@@ -126,27 +126,32 @@ __device__ void tensor_at(int ix, int iy, int iz, double dx, double dy, double d
   for (int i = 0; i < 6; ++i) out[i] = V * acc[i];
 }
 
-// Real-space tensor on the padded grid G[4][Py][Px] (complex, imag = 0),
-// from the octant ix in [0,nx), iy in [0,ny) (iz = 0: one layer).
-__global__ void tensor_fill_kernel(double2* G, int nx, int ny, int Px, int Py, double dx, double dy,
-                                   double dz) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nx * ny) return;
-  const int ix = idx % nx, iy = idx / nx;
+// Real-space tensor on the padded grid G[NC][Pz][Py][Px] (complex, imag = 0),
+// from the octant ix in [0,nx), iy in [0,ny), iz in [0,nz), mirrored to the
+// negative offsets with each component's parity.  NC = 4 (film: xx, yy, zz,
+// xy, one layer) or 6 (3D: xx, yy, zz, xy, xz, yz).
+__global__ void tensor_fill_kernel(double2* G, int NC, int nx, int ny, int nz, int Px, int Py, int Pz, double dx,
+                                   double dy, double dz) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nx * ny * nz) return;
+  const int ix = (int)(idx % nx), iy = (int)((idx / nx) % ny), iz = (int)(idx / ((long long)nx * ny));
   double t[6];
-  tensor_at(ix, iy, 0, dx, dy, dz, t);
-  const double comp[4] = {t[0], t[1], t[2], t[3]};
-  const long long plane = (long long)Px * Py;
+  tensor_at(ix, iy, iz, dx, dy, dz, t);
+  const long long plane = (long long)Px * Py, vol = plane * Pz;
   for (int sx = 0; sx < 2; ++sx) {
     if (sx == 1 && ix == 0) continue;
     for (int sy = 0; sy < 2; ++sy) {
       if (sy == 1 && iy == 0) continue;
-      const int px = sx ? Px - ix : ix;
-      const int py = sy ? Py - iy : iy;
-      const double sxy = (sx ^ sy) ? -1.0 : 1.0;
-      for (int c = 0; c < 4; ++c) {
-        const double v = (c == 3) ? sxy * comp[c] : comp[c];
-        G[c * plane + (long long)py * Px + px] = make_double2(v, 0.0);
+      for (int sz = 0; sz < 2; ++sz) {
+        if (sz == 1 && iz == 0) continue;
+        const int px = sx ? Px - ix : ix;
+        const int py = sy ? Py - iy : iy;
+        const int pz = sz ? Pz - iz : iz;
+        // xy odd in x and y, xz odd in x and z, yz odd in y and z
+        const double sgn[6] = {1.0, 1.0, 1.0, (sx ^ sy) ? -1.0 : 1.0, (sx ^ sz) ? -1.0 : 1.0,
+                               (sy ^ sz) ? -1.0 : 1.0};
+        const long long o = (long long)pz * plane + (long long)py * Px + px;
+        for (int c = 0; c < NC; ++c) G[c * vol + o] = make_double2(sgn[c] * t[c], 0.0);
       }
     }
   }
@@ -189,38 +194,85 @@ __global__ void tensor_pack_kernel(const double2* G, T* table, int Px, int Py) {
   }
 }
 
+// 3D table [kz 0..Pz/2][kx 0..Px/2][ky 0..Py/2][8]: xx, yy, zz, xy, xz, yz
+// of -mu0/(Px Py Pz) * Re(G^), then two zeros (32/64-byte records).  An odd
+// component vanishes exactly where the sine of one of its odd coordinates
+// does (index 0 or the Nyquist index); those entries are set to zero.
+template <typename T>
+__global__ void tensor_pack3_kernel(const double2* G, T* table, int Px, int Py, int Pz) {
+  const int nkx = Px / 2 + 1, nky = Py / 2 + 1, nkz = Pz / 2 + 1;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nkx * nky * nkz) return;
+  const int ky = (int)(idx % nky), kx = (int)((idx / nky) % nkx), kz = (int)(idx / ((long long)nky * nkx));
+  const long long plane = (long long)Px * Py, vol = plane * Pz;
+  const double scale = -kMu0 / ((double)Px * (double)Py * (double)Pz);
+  const bool ex = kx == 0 || kx == Px / 2, ey = ky == 0 || ky == Py / 2, ez = kz == 0 || kz == Pz / 2;
+  const bool zero[6] = {false, false, false, ex || ey, ex || ez, ey || ez};
+  const long long o = (long long)kz * plane + (long long)ky * Px + kx;
+  for (int c = 0; c < 6; ++c) table[idx * 8 + c] = zero[c] ? (T)0 : (T)(G[c * vol + o].x * scale);
+  table[idx * 8 + 6] = (T)0;
+  table[idx * 8 + 7] = (T)0;
+}
+
 template __global__ void tensor_pack_kernel<float>(const double2*, float*, int, int);
 template __global__ void tensor_pack_kernel<double>(const double2*, double*, int, int);
+template __global__ void tensor_pack3_kernel<float>(const double2*, float*, int, int, int);
+template __global__ void tensor_pack3_kernel<double>(const double2*, double*, int, int, int);
+
+// Elements of T in the packed spectrum table of one grid shape.
+long long tensor_table_len(int Px, int Py, int Pz) {
+  if (Pz <= 1) return (long long)(Px / 2 + 1) * (Py / 2 + 1) * 4;
+  return (long long)(Px / 2 + 1) * (Py / 2 + 1) * (Pz / 2 + 1) * 8;
+}
+
+// Complex FP64 scratch the build of one grid shape needs.
+long long tensor_scratch_len(int Px, int Py, int Pz) {
+  return (long long)(Pz <= 1 ? 4 : 6) * Px * Py * (Pz <= 1 ? 1 : Pz);
+}
 
 // Host entry: build the packed spectrum of one grid shape into `table`
-// (device, (Px/2+1)*(Py/2+1)*4 elements of T).  G is FP64 scratch of
-// 4*Px*Py complex values; tw the FP64 twiddle table.
+// (device, tensor_table_len(Px, Py, Pz) elements of T; Pz = 1 for a film).
+// G is FP64 scratch of tensor_scratch_len(Px, Py, Pz) complex values; tw the
+// FP64 twiddle table.
 template <typename T>
-cudaError_t build_tensor_spectrum(T* table, double2* G, int nx, int ny, int Px, int Py, double dx,
-                                  double dy, double dz, const double2* tw, cudaStream_t st) {
-  const long long plane = (long long)Px * Py;
-  cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double2) * 4 * plane, st);
+cudaError_t build_tensor_spectrum(T* table, double2* G, int nx, int ny, int nz, int Px, int Py, int Pz,
+                                  double dx, double dy, double dz, const double2* tw, cudaStream_t st) {
+  const int NC = Pz <= 1 ? 4 : 6;
+  if (Pz < 1) Pz = 1;
+  const long long plane = (long long)Px * Py, vol = plane * Pz;
+  cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double2) * NC * vol, st);
   if (e != cudaSuccess) return e;
-  const int n = nx * ny;
-  tensor_fill_kernel<<<(n + 127) / 128, 128, 0, st>>>(G, nx, ny, Px, Py, dx, dy, dz);
-  int lx = 0, ly = 0;
+  const long long n = (long long)nx * ny * nz;
+  tensor_fill_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(G, NC, nx, ny, nz, Px, Py, Pz, dx, dy, dz);
+  int lx = 0, ly = 0, lz = 0;
   while ((1 << lx) < Px) ++lx;
   while ((1 << ly) < Py) ++ly;
+  while ((1 << lz) < Pz) ++lz;
   const size_t shx = 2 * sizeof(double2) * Px, shy = 2 * sizeof(double2) * Py;
   cudaFuncSetAttribute(fft_lines_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(shx > shy ? shx : shy));
-  // rows: 4*Py lines, contiguous
-  fft_lines_kernel<<<4 * Py, 256, shx, st>>>(G, lx, 4 * Py, 1, 4 * Py, Px, 0, tw);
-  // columns: 4*Px lines, stride Px; line l -> component l / Px, column l % Px
-  fft_lines_kernel<<<4 * Px, 256, shy, st>>>(G, ly, 4 * Px, Px, Px, 1, plane, tw);
-  const int nk = (Px / 2 + 1) * (Py / 2 + 1);
-  tensor_pack_kernel<T><<<(nk + 255) / 256, 256, 0, st>>>(G, table, Px, Py);
+  // x lines: NC Pz Py contiguous lines
+  const int nlx = (int)(NC * Pz * Py);
+  fft_lines_kernel<<<nlx, 256, shx, st>>>(G, lx, nlx, 1, nlx, Px, 0, tw);
+  // y lines, stride Px: line l -> plane l / Px (component and layer), column l % Px
+  const int nly = (int)(NC * Pz * Px);
+  fft_lines_kernel<<<nly, 256, shy, st>>>(G, ly, nly, Px, Px, 1, plane, tw);
+  if (Pz > 1) {
+    // z lines, stride Px Py: line l -> component l / plane, point l % plane
+    const int nlz = (int)(NC * plane);
+    fft_lines_kernel<<<nlz, 64, 2 * sizeof(double2) * Pz, st>>>(G, lz, nlz, plane, (int)plane, 1, vol, tw);
+    const long long nk = (long long)(Px / 2 + 1) * (Py / 2 + 1) * (Pz / 2 + 1);
+    tensor_pack3_kernel<T><<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(G, table, Px, Py, Pz);
+  } else {
+    const int nk = (Px / 2 + 1) * (Py / 2 + 1);
+    tensor_pack_kernel<T><<<(nk + 255) / 256, 256, 0, st>>>(G, table, Px, Py);
+  }
   return cudaGetLastError();
 }
 
-template cudaError_t build_tensor_spectrum<float>(float*, double2*, int, int, int, int, double, double,
+template cudaError_t build_tensor_spectrum<float>(float*, double2*, int, int, int, int, int, int, double, double,
                                                   double, const double2*, cudaStream_t);
-template cudaError_t build_tensor_spectrum<double>(double*, double2*, int, int, int, int, double, double,
+template cudaError_t build_tensor_spectrum<double>(double*, double2*, int, int, int, int, int, int, double, double,
                                                    double, const double2*, cudaStream_t);
 
 }  // namespace llg
