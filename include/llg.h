@@ -17,7 +17,9 @@
  *            (harmonic-mean edge coupling, free boundaries);
  *   B_an   = (2 Ku/Ms)(m.u)u;  B_z = B_bias + b_rf sin(2 pi f t) e_rf on src;
  *   B_d    = -mu0 N * (Ms psi m), N the cell-averaged (Newell) tensor,
- *            evaluated by zero-padded FFT convolution;
+ *            evaluated by zero-padded FFT convolution (padded extents
+ *            Px, Py from llg_padded_extents; Pz = 1 for a film, else the
+ *            power of two >= 2 nz: 6 tensor components);
  *   dm/dt  = -gamma/(1+alpha_i^2) [m x B + alpha_i m x (m x B)];
  *   classic RK4 at fixed dt, t_n = n dt, no renormalisation of m.
  *
@@ -32,8 +34,12 @@
  * records); it allocates them in llg_create and frees them in llg_destroy.
  *
  * Streams.  All work runs on the stream given to llg_create.  llg_forward
- * synchronises that stream before it returns (it copies J to the host);
- * llg_adjoint and levelset_step return as soon as the work is queued.
+ * and llg_adjoint synchronise that stream before they return (they copy J
+ * and the device error word to the host); levelset_step and llg_field
+ * return as soon as the work is queued.  With llg_options.use_graph the
+ * RK4 segments are replayed from CUDA graphs captured on a private stream
+ * of the context (once per segment kind and length) and launched on the
+ * context's stream, so the caller's stream may be the legacy default one.
  *
  * Errors.  Functions return llg_status; no exception crosses the ABI.  On a
  * non-OK status llg_last_error(ctx) holds a one-line description.  A device
@@ -65,7 +71,8 @@ enum { LLG_CKPT_STORE_ALL = 0, LLG_CKPT_PERIODIC = 1 };
 
 /* One instance.  SI units (m, A/m, J/m, J/m^3, T, Hz, s). */
 typedef struct {
-  int nx, ny, nz;            /* nodes; nx % 4 == 0, nz == 1 (2D film)          */
+  int nx, ny, nz;            /* nodes; nx % 4 == 0, 4 <= nx <= 1024,
+                                1 <= ny <= 512, 1 <= nz <= 8 (1 = film)        */
   double dx, dy, dz;         /* node spacing = cell size                       */
   double Ms, A, Ku;          /* saturation magnetisation, exchange, anisotropy */
   double ku[3];              /* anisotropy axis (normalised by the library)    */
@@ -76,7 +83,8 @@ typedef struct {
   double B_bias[3];          /* static field                                   */
   double b_rf, f_rf;         /* RF amplitude and frequency                     */
   double rf_dir[3];          /* RF direction                                   */
-  int src[4];                /* RF source box x0,x1,y0,y1 (half open)          */
+  int src[4];                /* RF source box x0,x1,y0,y1 (half open; boxes span
+                                every z layer)                                 */
   double dt;                 /* time step                                      */
   long long nsteps;          /* number of RK4 steps N                          */
   double sigmoid_a;          /* a of Eq. 4                                     */
@@ -96,7 +104,8 @@ typedef struct {
   int precision;   /* LLG_FP32 or LLG_FP64                                     */
   int ckpt;        /* LLG_CKPT_PERIODIC (O(sqrt N) memory) or LLG_CKPT_STORE_ALL */
   int seg_len;     /* periodic segment length K; 0 = ceil(sqrt(max nsteps))     */
-  int use_graph;   /* 1 = replay captured CUDA graphs of whole segments         */
+  int use_graph;   /* 1 = replay captured CUDA graphs of whole segments
+                      (ignored while time_kernels = 1)                        */
   int rows_per_cta;/* reserved (tile rows follow from the row FFT length)      */
   int cols_per_cta;/* reserved (tile columns follow from the column FFT length) */
   int time_kernels;/* 1 = bracket every stage-kernel launch with CUDA events    */
@@ -108,8 +117,11 @@ typedef struct llg_ctx llg_ctx;
  * device, stored in the working precision), pick tile shapes and allocate all
  * scratch.  `cuda_stream` is a cudaStream_t (NULL = default stream).
  * Every instance must have the same nsteps, n_from and dt.
- * Returns LLG_EINVAL for unsupported sizes (nx % 4 != 0, nz != 1, nx > 2048,
- * ny > 512), LLG_ENOMEM if the scratch does not fit. */
+ * Returns LLG_EINVAL for unsupported sizes (nx % 4 != 0, nx outside [4, 1024],
+ * ny outside [1, 512], nz outside [1, 8], or a row or column tile that does
+ * not fit in shared memory: a 3D grid's column tile holds all nz layers of
+ * one padded column, so nz * Py <= 4096 in FP32 and <= 2048 in FP64, Py the
+ * padded y extent), and LLG_ENOMEM if the scratch does not fit. */
 llg_status llg_create(const llg_problem* inst, int n_inst, const llg_options* opt,
                       void* cuda_stream, llg_ctx** out);
 
@@ -185,7 +197,8 @@ llg_status llg_field_noalloc(const llg_problem* prob, const void* phi_dev, const
 long long llg_schedule(long long nsteps, int ckpt, int seg_len, long long* actions,
                        long long max_actions, long long* n_forward);
 
-/* Host-only: padded FFT extents the library uses for a grid (Px, Py). */
+/* Host-only: padded in-plane FFT extents the library uses for a grid (Px,
+ * Py); the padded z extent of a 3D grid is the power of two >= 2 nz. */
 int llg_padded_extents(int nx, int ny, int* Px, int* Py);
 
 int llg_abi_version(void);
