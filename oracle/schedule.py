@@ -18,6 +18,21 @@ checkpoints at n = 0, K, 2K, ...; the forward records the last segment
 directly; the reverse restores, re-records and reverses each earlier segment.
 Memory: ceil(N/K) checkpoints plus K recorded steps, O(sqrt N) at the default.
 Store-all is the periodic schedule with K = 1: all N states are kept.
+
+Binomial schedule with s snapshot slots besides the one holding m_0
+(Griewank's binomial checkpointing, as used by revolve): reversing l steps
+from a snapshotted start with s free slots, where no step may be advanced
+more than r times, is possible exactly when l <= beta(s, r) = C(s + r, s).
+The reversal takes the smallest such r, advances m steps and snapshots
+there, reverses the right part (l - m steps) with s - 1 slots, then the
+left part (m steps) with s slots.  The right part gets as many steps as its
+budget beta(s - 1, r) allows (m = l - min(beta(s - 1, r), l - 1)), which
+keeps m <= beta(s, r - 1) since beta(s, r) = beta(s, r - 1) + beta(s - 1, r).
+With no free slot the steps are re-advanced from the start one by one.
+Each step is recorded (one step at a time) just before it is reversed.
+The first descent of the recursion (advance, snapshot, advance, ..., record
+the last step) covers steps 0..N-1 once in order and is the forward pass.
+Memory: s + 1 checkpoints plus one recorded step.
 """
 from __future__ import annotations
 
@@ -62,6 +77,67 @@ def store_all(nsteps: int):
     """Every state m_n is kept (K = 1); each reverse step re-records its own
     stages from m_n."""
     return periodic(nsteps, 1)
+
+
+def beta(s: int, r: int, cap: int = 1 << 62) -> int:
+    """C(s + r, s), saturated at `cap`."""
+    v = 1
+    for k in range(1, min(s, r) + 1):
+        v = v * (s + r - min(s, r) + k) // k
+        if v >= cap:
+            return cap
+    return v
+
+
+def binomial(nsteps: int, snaps: int = 0):
+    """(forward_actions, reverse_actions) for the binomial schedule with
+    `snaps` free checkpoint slots (0 = default_segment(nsteps))."""
+    N = nsteps
+    if N <= 0:
+        return [], []
+    s0 = snaps if snaps > 0 else default_segment(N)
+    out = [(SNAP, 0, 0)]
+    state = {"cur": 0}          # step the working state holds with a valid spectrum, or -1
+
+    def goto(a, slot):
+        if state["cur"] != a:
+            out.append((RESTORE, slot, a))
+            state["cur"] = a
+
+    def rec_rev(n):
+        out.append((RECORD, n, n + 1))
+        out.append((REVERSE, n + 1, n))
+        state["cur"] = -1
+
+    # tasks (a, length, free slots, slot holding m_a), processed last in,
+    # first out: a split pushes the left part, then the right part
+    tasks = [(0, N, s0, 0)]
+    while tasks:
+        a, length, s, slot = tasks.pop()
+        if length == 1:
+            goto(a, slot)
+            rec_rev(a)
+        elif s == 0:
+            for k in range(length - 1, -1, -1):
+                goto(a, slot)
+                if k > 0:
+                    out.append((ADVANCE, a, a + k))
+                    state["cur"] = a + k
+                rec_rev(a + k)
+        else:
+            r = 1
+            while beta(s, r) < length:
+                r += 1
+            right = min(beta(s - 1, r), length - 1)
+            mid = a + length - right
+            goto(a, slot)
+            out.append((ADVANCE, a, mid))
+            state["cur"] = mid
+            out.append((SNAP, mid, slot + 1))
+            tasks.append((a, length - right, s, slot))
+            tasks.append((mid, right, s - 1, slot + 1))
+    first = next(i for i, act in enumerate(out) if act[0] == RECORD)
+    return out[:first + 1], out[first + 1:]
 
 
 def peak_states(fwd, rev):
@@ -118,7 +194,9 @@ def run_adjoint(model, m0, fwd, rev):
     if p.objective == J_PORT and p.nsteps >= p.n_from:
         lam = lam + model.port_term_grad(mN)
     for op, a, b in rev:
-        if op == RESTORE:
+        if op == SNAP:
+            slots[b] = m
+        elif op == RESTORE:
             m = slots[a]
             cur = b
         elif op == RECORD:

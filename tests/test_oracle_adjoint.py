@@ -140,6 +140,18 @@ def test_checkpoint_schedules_reproduce_store_all(seg):
     np.testing.assert_array_equal(gm1, gm0)
 
 
+@pytest.mark.parametrize("snaps", [0, 1, 2, 5])
+def test_binomial_schedules_reproduce_store_all(snaps):
+    inst = W.random_small(5, 4, 1, seed=8, nsteps=17)
+    mod = llg.Model(inst.problem, inst.phi)
+    J0, g0, gm0 = llg.gradient(inst)
+    fwd, rev = schedule.binomial(inst.problem.nsteps, snaps)
+    J1, g1, gm1 = schedule.run_adjoint(mod, inst.m0, fwd, rev)
+    assert J1 == J0
+    np.testing.assert_array_equal(g1, g0)
+    np.testing.assert_array_equal(gm1, gm0)
+
+
 def test_levelset_step():
     rng = np.random.default_rng(3)
     phi = rng.uniform(-1, 1, (1, 6, 7))
