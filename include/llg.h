@@ -67,7 +67,7 @@ typedef enum {
 
 enum { LLG_J_PORT = 0, LLG_J_ENERGY_AREA = 1 };
 enum { LLG_FP32 = 0, LLG_FP64 = 1 };
-enum { LLG_CKPT_STORE_ALL = 0, LLG_CKPT_PERIODIC = 1 };
+enum { LLG_CKPT_STORE_ALL = 0, LLG_CKPT_PERIODIC = 1, LLG_CKPT_BINOMIAL = 2 };
 
 /* One instance.  SI units (m, A/m, J/m, J/m^3, T, Hz, s). */
 typedef struct {
@@ -102,8 +102,12 @@ typedef struct {
 
 typedef struct {
   int precision;   /* LLG_FP32 or LLG_FP64                                     */
-  int ckpt;        /* LLG_CKPT_PERIODIC (O(sqrt N) memory) or LLG_CKPT_STORE_ALL */
-  int seg_len;     /* periodic segment length K; 0 = ceil(sqrt(max nsteps))     */
+  int ckpt;        /* LLG_CKPT_PERIODIC (O(sqrt N) memory), LLG_CKPT_STORE_ALL,
+                      or LLG_CKPT_BINOMIAL (seg_len + 1 stored states, each
+                      step advanced at most r + 1 times, r the smallest
+                      with C(seg_len + r, r) >= nsteps)                      */
+  int seg_len;     /* periodic: segment length K; binomial: free snapshot
+                      slots s; 0 = ceil(sqrt(nsteps)) for both               */
   int use_graph;   /* 1 = replay captured CUDA graphs of whole segments
                       (ignored while time_kernels = 1)                        */
   int rows_per_cta;/* reserved (tile rows follow from the row FFT length)      */
@@ -193,7 +197,10 @@ llg_status llg_field_noalloc(const llg_problem* prob, const void* phi_dev, const
  * max_actions triples (op, a, b) to `actions` (forward actions first, then
  * reverse), sets *n_forward to the number of forward actions and returns the
  * total count (or -1 on bad arguments).  ops: 0 SNAP (n, slot), 1 ADVANCE
- * (n0, n1), 2 RESTORE (slot, n), 3 RECORD (n0, n1), 4 REVERSE (n1, n0). */
+ * (n0, n1), 2 RESTORE (slot, n), 3 RECORD (n0, n1), 4 REVERSE (n1, n0).
+ * Every list works on one working state: RESTORE loads it from a slot,
+ * ADVANCE moves it, SNAP stores it, RECORD records its next steps' stage
+ * data; the objective accumulates only in the forward actions. */
 long long llg_schedule(long long nsteps, int ckpt, int seg_len, long long* actions,
                        long long max_actions, long long* n_forward);
 

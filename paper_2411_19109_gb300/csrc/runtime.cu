@@ -11,7 +11,9 @@
 //   * the checkpoint action list it executes.
 // Checkpointing follows the paper's memory argument (Introduction and the
 // adjoint-state section): only every K-th state is kept and each segment is
-// recomputed once during the reverse sweep, O(sqrt N) states at the default K.
+// recomputed once during the reverse sweep, O(sqrt N) states at the default K;
+// or binomial checkpointing with a fixed number of snapshot slots, which
+// trades more recomputation for memory independent of the segment length.
 #include <algorithm>
 #include <map>
 #include <cmath>
@@ -39,6 +41,78 @@ long long isqrt_ceil(long long n) {
   return k;
 }
 
+// C(s + r, s), saturated at 2^62.
+long long binom_sat(long long s, long long r) {
+  const long long cap = 1LL << 62;
+  const long long k = std::min(s, r), base = s + r - k;
+  long long v = 1;
+  for (long long j = 1; j <= k; ++j) {
+    const __int128 w = (__int128)v * (base + j) / j;
+    if (w >= cap) return cap;
+    v = (long long)w;
+  }
+  return v;
+}
+
+// Binomial schedule with s free snapshot slots (slot 0 holds m_0).  Reversing
+// l steps from a snapshot at a with s free slots, each step advanced at most r
+// times, works exactly when l <= C(s + r, s): take the smallest such r, put
+// right = min(C(s - 1 + r, s - 1), l - 1) steps after the split, advance to
+// the split and snapshot there, reverse the right part with s - 1 slots, then
+// the left part with s.  With no free slot, re-advance from a for every step.
+// Each step is recorded singly just before it is reversed.  The first descent
+// (advance, snapshot, ..., record the last step) is the forward pass.
+void make_binomial(long long N, long long s0, std::vector<Action>& fwd, std::vector<Action>& rev) {
+  std::vector<Action> out;
+  out.push_back({SNAP, 0, 0});
+  long long cur = 0;   // step the working state holds with a valid spectrum, -1 if none
+  auto go = [&](long long a, long long slot) {
+    if (cur != a) {
+      out.push_back({RESTORE, slot, a});
+      cur = a;
+    }
+  };
+  auto rec_rev = [&](long long n) {
+    out.push_back({RECORD, n, n + 1});
+    out.push_back({REVERSE, n + 1, n});
+    cur = -1;
+  };
+  struct Task { long long a, len, s, slot; };
+  std::vector<Task> tasks{{0, N, s0, 0}};
+  while (!tasks.empty()) {
+    const Task t = tasks.back();
+    tasks.pop_back();
+    if (t.len == 1) {
+      go(t.a, t.slot);
+      rec_rev(t.a);
+    } else if (t.s == 0) {
+      for (long long k = t.len - 1; k >= 0; --k) {
+        go(t.a, t.slot);
+        if (k > 0) {
+          out.push_back({ADVANCE, t.a, t.a + k});
+          cur = t.a + k;
+        }
+        rec_rev(t.a + k);
+      }
+    } else {
+      long long r = 1;
+      while (binom_sat(t.s, r) < t.len) ++r;
+      const long long right = std::min(binom_sat(t.s - 1, r), t.len - 1);
+      const long long mid = t.a + t.len - right;
+      go(t.a, t.slot);
+      out.push_back({ADVANCE, t.a, mid});
+      cur = mid;
+      out.push_back({SNAP, mid, t.slot + 1});
+      tasks.push_back({t.a, t.len - right, t.s, t.slot});
+      tasks.push_back({mid, right, t.s - 1, t.slot + 1});
+    }
+  }
+  size_t first = 0;
+  while (out[first].op != RECORD) ++first;
+  fwd.assign(out.begin(), out.begin() + first + 1);
+  rev.assign(out.begin() + first + 1, out.end());
+}
+
 // Periodic schedule: snapshots at n = 0, K, 2K, ..; the forward records the
 // last segment; the reverse restores, re-records and reverses each earlier
 // segment.  Store-all is the same schedule with K = 1 (every state kept).
@@ -46,6 +120,10 @@ void make_schedule(long long N, int ckpt, int seg_len, std::vector<Action>& fwd,
   fwd.clear();
   rev.clear();
   if (N <= 0) return;
+  if (ckpt == LLG_CKPT_BINOMIAL) {
+    make_binomial(N, seg_len > 0 ? seg_len : isqrt_ceil(N), fwd, rev);
+    return;
+  }
   long long K = (ckpt == LLG_CKPT_STORE_ALL) ? 1 : (seg_len > 0 ? seg_len : isqrt_ceil(N));
   const long long nseg = (N + K - 1) / K;
   for (long long c = 0; c < nseg; ++c) {
@@ -141,7 +219,10 @@ struct Engine final : llg_ctx {
   // segment's launches depend only on its kind and length (the first step
   // number is read from *step_base), so one capture serves every segment of
   // that shape.  Value: the executable graph and the launches it holds.
-  enum SegKind { SEG_ADVANCE = 0, SEG_RECORD_FWD = 1, SEG_RECORD_ADJ = 2, SEG_REVERSE = 3 };
+  // ADVANCE_ADJ: recomputation during the reverse sweep (no objective terms).
+  // The cache holds at most kMaxGraphs graphs; other shapes run directly.
+  enum SegKind { SEG_ADVANCE = 0, SEG_RECORD_FWD = 1, SEG_RECORD_ADJ = 2, SEG_REVERSE = 3, SEG_ADVANCE_ADJ = 4 };
+  static constexpr size_t kMaxGraphs = 64;
   std::map<std::pair<int, long long>, std::pair<cudaGraphExec_t, long long>> graphs;
   cudaStream_t cap_st = nullptr;   // private stream the captures are recorded on
 
@@ -277,8 +358,9 @@ struct Engine final : llg_ctx {
     }
     if (opt.precision != LLG_FP32 && opt.precision != LLG_FP64)
       return fail(LLG_EINVAL, "precision must be LLG_FP32 or LLG_FP64");
-    if (opt.ckpt != LLG_CKPT_PERIODIC && opt.ckpt != LLG_CKPT_STORE_ALL)
-      return fail(LLG_EINVAL, "ckpt must be LLG_CKPT_PERIODIC or LLG_CKPT_STORE_ALL");
+    if (opt.ckpt != LLG_CKPT_PERIODIC && opt.ckpt != LLG_CKPT_STORE_ALL && opt.ckpt != LLG_CKPT_BINOMIAL)
+      return fail(LLG_EINVAL, "ckpt must be LLG_CKPT_PERIODIC, LLG_CKPT_STORE_ALL or LLG_CKPT_BINOMIAL");
+    if (opt.seg_len < 0) return fail(LLG_EINVAL, "seg_len must be >= 0");
 
     // Tile shapes follow from the register FFTs: one component of a row FFT
     // of length Lx takes Lx/8 threads, so a 384-thread block covers 1024/Lx
@@ -621,7 +703,9 @@ struct Engine final : llg_ctx {
       reverse_segment(len);
       return;
     }
-    for (long long l = 0; l < len; ++l) step((int)l, kind != SEG_ADVANCE, kind != SEG_RECORD_ADJ);
+    const bool record = kind == SEG_RECORD_FWD || kind == SEG_RECORD_ADJ;
+    const bool objective = kind == SEG_ADVANCE || kind == SEG_RECORD_FWD;
+    for (long long l = 0; l < len; ++l) step((int)l, record, objective);
   }
 
   // Runs one segment whose first step number is already in *step_base:
@@ -634,6 +718,10 @@ struct Engine final : llg_ctx {
     }
     const auto key = std::make_pair(kind, len);
     auto it = graphs.find(key);
+    if (it == graphs.end() && graphs.size() >= kMaxGraphs) {
+      segment_body(kind, len);
+      return LLG_OK;
+    }
     if (it == graphs.end()) {
       // capture on a private stream (the caller's may be the legacy default
       // stream, which cannot be captured); nothing runs during capture
@@ -754,12 +842,19 @@ struct Engine final : llg_ctx {
     if (!have_fwd) return fail(LLG_ESTATE, "llg_adjoint needs a preceding llg_forward");
     if (!dphi) return fail(LLG_EINVAL, "dJdphi must not be NULL");
     cudaEventRecord(ev0, st);
+    // The working state m (with the spectrum of its stage-1 input) is what
+    // RESTORE loads, ADVANCE moves, SNAP saves and RECORD starts from.
     for (const Action& ac : rev) {
       if (ac.op == RESTORE) {
-        cudaMemcpyAsync(recY_slot(0), ckpt + (size_t)ac.a * slot(), sizeof(T) * slot(), cudaMemcpyDeviceToDevice,
-                        st);
-        fft_only(recY_slot(0));
+        cudaMemcpyAsync(m, ckpt + (size_t)ac.a * slot(), sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
+        fft_only(m);
+      } else if (ac.op == SNAP) {
+        cudaMemcpyAsync(ckpt + (size_t)ac.b * slot(), m, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
+      } else if (ac.op == ADVANCE) {
+        set_step(ac.a);
+        if (llg_status s = run_segment(SEG_ADVANCE_ADJ, ac.b - ac.a)) return s;
       } else if (ac.op == RECORD) {
+        cudaMemcpyAsync(recY_slot(0), m, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
         set_step(ac.a);
         if (llg_status s = run_segment(SEG_RECORD_ADJ, ac.b - ac.a)) return s;
       } else if (ac.op == REVERSE) {
@@ -894,7 +989,9 @@ void llg_destroy(llg_ctx* ctx) { delete ctx; }
 
 long long llg_schedule(long long nsteps, int ckpt, int seg_len, long long* actions, long long max_actions,
                        long long* n_forward) {
-  if (nsteps < 0 || seg_len < 0 || (ckpt != LLG_CKPT_PERIODIC && ckpt != LLG_CKPT_STORE_ALL)) return -1;
+  if (nsteps < 0 || seg_len < 0 ||
+      (ckpt != LLG_CKPT_PERIODIC && ckpt != LLG_CKPT_STORE_ALL && ckpt != LLG_CKPT_BINOMIAL))
+    return -1;
   std::vector<Action> f, r;
   make_schedule(nsteps, ckpt, seg_len, f, r);
   const long long tot = (long long)(f.size() + r.size());

@@ -23,7 +23,7 @@ c_int, c_double, c_ll, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_longlo
 LLG_OK, LLG_EINVAL, LLG_ENOMEM, LLG_ECUDA, LLG_ETIMEOUT, LLG_ENONFINITE, LLG_ESTATE = range(7)
 LLG_J_PORT, LLG_J_ENERGY_AREA = 0, 1
 LLG_FP32, LLG_FP64 = 0, 1
-LLG_CKPT_STORE_ALL, LLG_CKPT_PERIODIC = 0, 1
+LLG_CKPT_STORE_ALL, LLG_CKPT_PERIODIC, LLG_CKPT_BINOMIAL = 0, 1, 2
 
 EXPORTED = ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query",
             "llg_launch_count", "llg_kernel_time", "llg_last_error", "llg_destroy", "llg_schedule",
@@ -247,7 +247,7 @@ class Solver:
         self.problems = list(problems)
         self.dtype = torch.float32 if precision == "fp32" else torch.float64
         prec = LLG_FP32 if precision == "fp32" else LLG_FP64
-        ck = LLG_CKPT_PERIODIC if ckpt == "periodic" else LLG_CKPT_STORE_ALL
+        ck = {"periodic": LLG_CKPT_PERIODIC, "store_all": LLG_CKPT_STORE_ALL, "binomial": LLG_CKPT_BINOMIAL}[ckpt]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ctx = llg_create(self.problems, prec, ck, seg_len, self.stream.cuda_stream,
                               rows_per_cta, cols_per_cta, int(use_graph), int(time_kernels))

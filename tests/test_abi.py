@@ -58,6 +58,13 @@ def test_schedule_matches_oracle(lib, N, seg):
     assert llg_schedule(N, LLG_CKPT_STORE_ALL, 0) == S.store_all(N)
 
 
+@pytest.mark.parametrize("N,snaps", [(1, 0), (2, 0), (3, 1), (10, 0), (10, 2), (17, 3), (100, 1), (1000, 10),
+                                     (10000, 0), (50000, 64), (7, 30)])
+def test_binomial_schedule_matches_oracle(lib, N, snaps):
+    from paper_2411_19109_gb300 import LLG_CKPT_BINOMIAL, llg_schedule
+    assert llg_schedule(N, LLG_CKPT_BINOMIAL, snaps) == S.binomial(N, snaps)
+
+
 def test_padded_extents(lib):
     from paper_2411_19109_gb300 import llg_padded_extents
     for nx, ny in [(4, 1), (32, 32), (36, 20), (128, 64), (512, 128), (1024, 512)]:

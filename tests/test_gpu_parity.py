@@ -95,8 +95,9 @@ def test_batch_of_uneven_grids_matches_single_runs():
 def test_schedules_give_identical_gradients(precision):
     inst = W.random_small(12, 8, 1, seed=5, nsteps=23)
     ref = gpu_run([inst], precision, ckpt="store_all")
-    for seg in (0, 1, 4, 23, 40):
-        g = gpu_run([inst], precision, ckpt="periodic", seg_len=seg)
+    for ckpt, seg in (("periodic", 0), ("periodic", 1), ("periodic", 4), ("periodic", 23), ("periodic", 40),
+                      ("binomial", 0), ("binomial", 1), ("binomial", 2), ("binomial", 6)):
+        g = gpu_run([inst], precision, ckpt=ckpt, seg_len=seg, want_dm0=True)
         np.testing.assert_array_equal(g["dphi"][0], ref["dphi"][0])
         assert g["J"][0] == ref["J"][0]
 
