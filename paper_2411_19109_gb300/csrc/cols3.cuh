@@ -123,7 +123,7 @@ __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
         const int y = t + TT * s;
-        v[s] = y < ny ? grp[rf_pad(y)] : mk<C>((T)0, (T)0);
+        v[s] = (s < 4 && y < ny) ? grp[rf_pad(y)] : mk<C>((T)0, (T)0);   // zero padding: s >= 4
       }
       gs();
       fft1<C, L, -1>(v, grp, 1, t, tw1, 1, gs);
@@ -218,7 +218,7 @@ __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
         const int y = t + TT * s;
-        if (y < ny) grp[rf_pad(y)] = v[s];
+        if (s < 4 && y < ny) grp[rf_pad(y)] = v[s];
       }
     }
   }

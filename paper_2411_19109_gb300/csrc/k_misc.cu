@@ -49,12 +49,12 @@ void launch_reduce_slots(const DevInst* inst, int n_inst, const double* slots, l
 }
 
 template <typename T>
-void launch_rows(const RowArgs<T>& a, int mode, int ntiles, size_t smem, cudaStream_t st) {
+void launch_rows(const RowArgs<T>& a, int mode, int ntiles, size_t smem, cudaStream_t st, bool z3) {
   switch (mode) {
-    case ROW_FFT_ONLY: launch_rows_mode<T, ROW_FFT_ONLY>(a, ntiles, smem, st); break;
-    case ROW_STAGE: launch_rows_mode<T, ROW_STAGE>(a, ntiles, smem, st); break;
-    case ROW_FIELD: launch_rows_mode<T, ROW_FIELD>(a, ntiles, smem, st); break;
-    default: launch_rows_mode<T, ROW_TERMINAL>(a, ntiles, smem, st); break;
+    case ROW_FFT_ONLY: launch_rows_mode<T, ROW_FFT_ONLY>(a, ntiles, smem, st, z3); break;
+    case ROW_STAGE: launch_rows_mode<T, ROW_STAGE>(a, ntiles, smem, st, z3); break;
+    case ROW_FIELD: launch_rows_mode<T, ROW_FIELD>(a, ntiles, smem, st, z3); break;
+    default: launch_rows_mode<T, ROW_TERMINAL>(a, ntiles, smem, st, z3); break;
   }
 }
 
@@ -68,8 +68,8 @@ void set_smem_limits(size_t stage, size_t misc, size_t cols, size_t adj) {
   smem_adj<T>(adj);
 }
 
-template void launch_rows<float>(const RowArgs<float>&, int, int, size_t, cudaStream_t);
-template void launch_rows<double>(const RowArgs<double>&, int, int, size_t, cudaStream_t);
+template void launch_rows<float>(const RowArgs<float>&, int, int, size_t, cudaStream_t, bool);
+template void launch_rows<double>(const RowArgs<double>&, int, int, size_t, cudaStream_t, bool);
 template void set_smem_limits<float>(size_t, size_t, size_t, size_t);
 template void set_smem_limits<double>(size_t, size_t, size_t, size_t);
 

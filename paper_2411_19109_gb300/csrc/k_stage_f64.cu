@@ -3,6 +3,6 @@
 #include "kernels_impl.cuh"
 
 namespace llg {
-template void launch_rows_mode<double, ROW_STAGE>(const RowArgs<double>&, int, size_t, cudaStream_t);
+template void launch_rows_mode<double, ROW_STAGE>(const RowArgs<double>&, int, size_t, cudaStream_t, bool);
 template void smem_rows_mode<double, ROW_STAGE>(size_t);
 }  // namespace llg

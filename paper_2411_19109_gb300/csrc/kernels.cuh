@@ -87,7 +87,7 @@ struct AdjArgs {
 };
 
 template <typename T>
-void launch_rows(const RowArgs<T>& a, int mode, int ntiles, size_t smem, cudaStream_t st);
+void launch_rows(const RowArgs<T>& a, int mode, int ntiles, size_t smem, cudaStream_t st, bool z3);
 template <typename T>
 void launch_cols(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
 // column pass of 3D grids (nz > 1)
@@ -110,9 +110,9 @@ __host__ __device__ constexpr size_t cols3_smem_bytes(int Py, int nz, int ncols)
 }
 
 template <typename T>
-void launch_adj(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+void launch_adj(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3);
 template <typename T, int MODE>
-void launch_rows_mode(const RowArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+void launch_rows_mode(const RowArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3);
 template <typename T, int MODE>
 void smem_rows_mode(size_t smem);
 template <typename T>

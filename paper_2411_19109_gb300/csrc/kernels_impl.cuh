@@ -236,18 +236,21 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
   C* spec = a.spec + I.spec_off + tile.kx0;
   const GroupSync gs = group_sync(TT);
   load_twiddles(tw1, a.tw, L);
-  // coalesced load of the tile (ny rows x 3 components x ncols) into the groups
-  for (int e = tid; e < ny * 3 * ncols; e += kColThreads) {
-    const int y = e / (3 * ncols), r = e - y * 3 * ncols;
-    const int cc = r / ncols, cl = r - cc * ncols;
-    smem[(cc * NC + cl) * GSC + rf_pad(y)] = spec[((long long)y * 3 + cc) * Lx + cl];
+  // coalesced load of the tile (ny rows x 3 components x NC column slots,
+  // columns fastest) into the groups; the divisors are compile-time
+  for (int e = tid; e < ny * 3 * NC; e += kColThreads) {
+    const int y = e / (3 * NC), r = e - y * (3 * NC);
+    const int cc = r / NC, cl = r % NC;
+    if (cl < ncols) smem[(cc * NC + cl) * GSC + rf_pad(y)] = spec[((long long)y * 3 + cc) * Lx + cl];
   }
   __syncthreads();
   C v[8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int y = t + TT * s;
-    v[s] = (active && y < ny) ? grp[rf_pad(y)] : mk<C>((T)0, (T)0);
+    // rows y >= ny are the zero padding; ny <= L/2, so s >= 4 is zero
+    // at compile time and the first pass folds
+    v[s] = (s < 4 && active && y < ny) ? grp[rf_pad(y)] : mk<C>((T)0, (T)0);
   }
   gs();
   fft1<C, L, -1>(v, grp, 1, t, tw1, 1, gs);
@@ -290,18 +293,18 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int y = t + TT * s;
-    if (y < ny) grp[rf_pad(y)] = v[s];
+    if (s < 4 && y < ny) grp[rf_pad(y)] = v[s];   // only rows y < ny <= L/2 go back
   }
   __syncthreads();
-  for (int e = tid; e < ny * 3 * ncols; e += kColThreads) {
-    const int y = e / (3 * ncols), r = e - y * 3 * ncols;
-    const int cc = r / ncols, cl = r - cc * ncols;
-    spec[((long long)y * 3 + cc) * Lx + cl] = smem[(cc * NC + cl) * GSC + rf_pad(y)];
+  for (int e = tid; e < ny * 3 * NC; e += kColThreads) {
+    const int y = e / (3 * NC), r = e - y * (3 * NC);
+    const int cc = r / NC, cl = r % NC;
+    if (cl < ncols) spec[((long long)y * 3 + cc) * Lx + cl] = smem[(cc * NC + cl) * GSC + rf_pad(y)];
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kColThreads) cols_kernel(ColArgs<T> a) {
+__global__ void __launch_bounds__(kColThreads, sizeof(T) == 4 ? 3 : 1) cols_kernel(ColArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ DevInst sI;
@@ -359,7 +362,7 @@ struct RowGeom {
 // (kExch complex) then W_{2L}^k, k < 2L.
 // ---------------------------------------------------------------------------
 
-template <typename T, int L, int MODE>
+template <typename T, int L, int MODE, bool Z3>
 __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I, const RowTile& tile,
                                           cplx<T>* smem, double* red, T rf) {
   using C = cplx<T>;
@@ -419,7 +422,7 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
     const T hh[6] = {K.ihx2, K.ihx2, K.ihy2, K.ihy2, K.ihz2, K.ihz2};
     const T cc[6] = {cx, cx, cy, cy, cz, cz};
 #pragma unroll
-    for (int d = 0; d < 6; ++d) {
+    for (int d = 0; d < (Z3 ? 6 : 4); ++d) {
       const bool ok = d == 0 ? x + 1 < nx : d == 1 ? x > 0 : d == 2 ? y + 1 < ny : d == 3 ? y > 0
                     : d == 4 ? z + 1 < nz : z > 0;
       if (!ok) continue;
@@ -505,7 +508,7 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
 // rows][psi halo (R+2) rows][m 3 x R rows][acc 3 x R rows][W_{2L}^k, k < 2L].
 // ---------------------------------------------------------------------------
 
-template <typename T, int L>
+template <typename T, int L, bool Z3>
 __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I, const RowTile& tile,
                                            unsigned char* smem_raw, uint64_t* bars, double* red, T rf) {
   using C = cplx<T>;
@@ -595,13 +598,15 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
       for (int c = 0; c < 3; ++c) B[c] += w * (sY[c * cs + oj] - yi[c]);
     }
     // the layers above and below (3D), from global memory
+    if constexpr (Z3) {
 #pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      if (d == 0 ? z + 1 >= nz : z == 0) continue;
-      const long long j = n0 + (d == 0 ? layer : -layer);
-      const T w = cz * edge_weight(pi, a.psi[I.node_off + j]);
+      for (int d = 0; d < 2; ++d) {
+        if (d == 0 ? z + 1 >= nz : z == 0) continue;
+        const long long j = n0 + (d == 0 ? layer : -layer);
+        const T w = cz * edge_weight(pi, a.psi[I.node_off + j]);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) B[c] += w * (a.Yin[off3 + c * nodes + j] - yi[c]);
+        for (int c = 0; c < 3; ++c) B[c] += w * (a.Yin[off3 + c * nodes + j] - yi[c]);
+      }
     }
     if (kan != (T)0) {
       const T dd = dot3(yi, ku);
@@ -658,8 +663,28 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
                          tw2);
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kRowThreads) rows_kernel(RowArgs<T> a) {
+// Stage body for the row FFT length of the tile's instance; Z3 selects the
+// 3D variant (z neighbours), so film tiles carry none of its registers.
+template <typename T, bool Z3>
+__device__ __forceinline__ void stage_dispatch(const RowArgs<T>& a, const DevInst& I, const RowTile& tile,
+                                               unsigned char* smem_raw, uint64_t* bars, double* red, T rf) {
+  switch (I.log2Lx) {
+    case 3: stage_body<T, 8, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 4: stage_body<T, 16, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 5: stage_body<T, 32, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 6: stage_body<T, 64, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 7: stage_body<T, 128, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 8: stage_body<T, 256, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 9: stage_body<T, 512, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 10: stage_body<T, 1024, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
+    default: break;
+  }
+}
+
+// Z3: the 3D variant (z neighbours); film tiles launch the variant without
+// them, which needs fewer registers.
+template <typename T, int MODE, bool Z3>
+__global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? (Z3 ? 2 : 3) : 1) rows_kernel(RowArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[kRowThreads / 32];
@@ -684,28 +709,18 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowArgs<T> a) {
   C* sm = reinterpret_cast<C*>(smem_raw);
   const T rf = (T)s_rf;
   if (MODE == ROW_STAGE) {
-    switch (sI.log2Lx) {
-      case 3: stage_body<T, 8>(a, sI, tile, smem_raw, bars, red, rf); break;
-      case 4: stage_body<T, 16>(a, sI, tile, smem_raw, bars, red, rf); break;
-      case 5: stage_body<T, 32>(a, sI, tile, smem_raw, bars, red, rf); break;
-      case 6: stage_body<T, 64>(a, sI, tile, smem_raw, bars, red, rf); break;
-      case 7: stage_body<T, 128>(a, sI, tile, smem_raw, bars, red, rf); break;
-      case 8: stage_body<T, 256>(a, sI, tile, smem_raw, bars, red, rf); break;
-      case 9: stage_body<T, 512>(a, sI, tile, smem_raw, bars, red, rf); break;
-      case 10: stage_body<T, 1024>(a, sI, tile, smem_raw, bars, red, rf); break;
-      default: break;
-    }
+    stage_dispatch<T, Z3>(a, sI, tile, smem_raw, bars, red, rf);
     return;
   }
   switch (sI.log2Lx) {
-    case 3: rows_body<T, 8, MODE>(a, sI, tile, sm, red, rf); break;
-    case 4: rows_body<T, 16, MODE>(a, sI, tile, sm, red, rf); break;
-    case 5: rows_body<T, 32, MODE>(a, sI, tile, sm, red, rf); break;
-    case 6: rows_body<T, 64, MODE>(a, sI, tile, sm, red, rf); break;
-    case 7: rows_body<T, 128, MODE>(a, sI, tile, sm, red, rf); break;
-    case 8: rows_body<T, 256, MODE>(a, sI, tile, sm, red, rf); break;
-    case 9: rows_body<T, 512, MODE>(a, sI, tile, sm, red, rf); break;
-    case 10: rows_body<T, 1024, MODE>(a, sI, tile, sm, red, rf); break;
+    case 3: rows_body<T, 8, MODE, Z3>(a, sI, tile, sm, red, rf); break;
+    case 4: rows_body<T, 16, MODE, Z3>(a, sI, tile, sm, red, rf); break;
+    case 5: rows_body<T, 32, MODE, Z3>(a, sI, tile, sm, red, rf); break;
+    case 6: rows_body<T, 64, MODE, Z3>(a, sI, tile, sm, red, rf); break;
+    case 7: rows_body<T, 128, MODE, Z3>(a, sI, tile, sm, red, rf); break;
+    case 8: rows_body<T, 256, MODE, Z3>(a, sI, tile, sm, red, rf); break;
+    case 9: rows_body<T, 512, MODE, Z3>(a, sI, tile, sm, red, rf); break;
+    case 10: rows_body<T, 1024, MODE, Z3>(a, sI, tile, sm, red, rf); break;
     default: break;
   }
 }
@@ -719,7 +734,7 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(RowArgs<T> a) {
 // [W_{2L}^k, k < 2L].
 // ---------------------------------------------------------------------------
 
-template <typename T, int L>
+template <typename T, int L, bool Z3>
 __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, const RowTile& tile,
                                          unsigned char* smem_raw, uint64_t* bars) {
   using C = cplx<T>;
@@ -841,6 +856,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
         qpsi += cc[d] * wij * r * (eji - eij);          // d w_ij/d psi_i = -2 psi_j/(psi_i+psi_j)^2
       }
       // the same across the layers above and below (3D), from global memory
+      if constexpr (Z3) {
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
         if (d == 0 ? z + 1 >= nz : z == 0) continue;
@@ -858,6 +874,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
           eji += bj * (yi[c] - yj);
         }
         qpsi += cz * wij * r * (eji - eij);
+      }
       }
       // demag transpose Ms psi_i (N * Bbar)_i and its psi derivative
       T D[3];
@@ -928,7 +945,23 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
                          tw2);
 }
 
-template <typename T>
+template <typename T, bool Z3>
+__device__ __forceinline__ void adj_dispatch(const AdjArgs<T>& a, const DevInst& I, const RowTile& tile,
+                                             unsigned char* smem_raw, uint64_t* bars) {
+  switch (I.log2Lx) {
+    case 3: adj_body<T, 8, Z3>(a, I, tile, smem_raw, bars); break;
+    case 4: adj_body<T, 16, Z3>(a, I, tile, smem_raw, bars); break;
+    case 5: adj_body<T, 32, Z3>(a, I, tile, smem_raw, bars); break;
+    case 6: adj_body<T, 64, Z3>(a, I, tile, smem_raw, bars); break;
+    case 7: adj_body<T, 128, Z3>(a, I, tile, smem_raw, bars); break;
+    case 8: adj_body<T, 256, Z3>(a, I, tile, smem_raw, bars); break;
+    case 9: adj_body<T, 512, Z3>(a, I, tile, smem_raw, bars); break;
+    case 10: adj_body<T, 1024, Z3>(a, I, tile, smem_raw, bars); break;
+    default: break;
+  }
+}
+
+template <typename T, bool Z3>
 __global__ void __launch_bounds__(kAdjThreads) adj_kernel(AdjArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ DevInst sI;
@@ -936,17 +969,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_kernel(AdjArgs<T> a) {
   const RowTile tile = a.tiles[blockIdx.x];
   load_inst(sI, a.inst + tile.inst);
   __syncthreads();
-  switch (sI.log2Lx) {
-    case 3: adj_body<T, 8>(a, sI, tile, smem_raw, bars); break;
-    case 4: adj_body<T, 16>(a, sI, tile, smem_raw, bars); break;
-    case 5: adj_body<T, 32>(a, sI, tile, smem_raw, bars); break;
-    case 6: adj_body<T, 64>(a, sI, tile, smem_raw, bars); break;
-    case 7: adj_body<T, 128>(a, sI, tile, smem_raw, bars); break;
-    case 8: adj_body<T, 256>(a, sI, tile, smem_raw, bars); break;
-    case 9: adj_body<T, 512>(a, sI, tile, smem_raw, bars); break;
-    case 10: adj_body<T, 1024>(a, sI, tile, smem_raw, bars); break;
-    default: break;
-  }
+  adj_dispatch<T, Z3>(a, sI, tile, smem_raw, bars);
 }
 
 // ---------------------------------------------------------------------------
@@ -1032,8 +1055,9 @@ __global__ void levelset_scale_kernel(const DevInst* inst, const RowTile* tiles,
 // ---------------------------------------------------------------------------
 
 template <typename T, int MODE>
-void launch_rows_mode(const RowArgs<T>& a, int ntiles, size_t smem, cudaStream_t st) {
-  rows_kernel<T, MODE><<<ntiles, kRowThreads, smem, st>>>(a);
+void launch_rows_mode(const RowArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3) {
+  if (z3) rows_kernel<T, MODE, true><<<ntiles, kRowThreads, smem, st>>>(a);
+  else rows_kernel<T, MODE, false><<<ntiles, kRowThreads, smem, st>>>(a);
 }
 // The dynamic shared-memory limit is a process-wide attribute of each kernel:
 // it is only ever raised, so that a context for small grids does not lower it
@@ -1046,8 +1070,9 @@ inline void raise_smem_limit(const void* fn, size_t* cur, size_t smem) {
 }
 template <typename T, int MODE>
 void smem_rows_mode(size_t smem) {
-  static size_t cur = 0;
-  raise_smem_limit(reinterpret_cast<const void*>(rows_kernel<T, MODE>), &cur, smem);
+  static size_t cur = 0, cur3 = 0;
+  raise_smem_limit(reinterpret_cast<const void*>(rows_kernel<T, MODE, false>), &cur, smem);
+  raise_smem_limit(reinterpret_cast<const void*>(rows_kernel<T, MODE, true>), &cur3, smem);
 }
 template <typename T>
 void launch_cols(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st) {
@@ -1059,13 +1084,15 @@ void smem_cols(size_t smem) {
   raise_smem_limit(reinterpret_cast<const void*>(cols_kernel<T>), &cur, smem);
 }
 template <typename T>
-void launch_adj(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st) {
-  adj_kernel<T><<<ntiles, kAdjThreads, smem, st>>>(a);
+void launch_adj(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3) {
+  if (z3) adj_kernel<T, true><<<ntiles, kAdjThreads, smem, st>>>(a);
+  else adj_kernel<T, false><<<ntiles, kAdjThreads, smem, st>>>(a);
 }
 template <typename T>
 void smem_adj(size_t smem) {
-  static size_t cur = 0;
-  raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T>), &cur, smem);
+  static size_t cur = 0, cur3 = 0;
+  raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, false>), &cur, smem);
+  raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, true>), &cur3, smem);
 }
 template <typename T>
 void launch_material_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* phi, T* psi,

@@ -228,7 +228,7 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   // the column kernel): below the 48 KB default, no opt-in attribute needed
   const size_t smem_rows = (size_t)(kExch + 2 * d.Lx) * sizeof(float2);
   const size_t smem_cols = (size_t)(kExch + Py) * sizeof(float2);
-  launch_rows<float>(a, ROW_FFT_ONLY, nrt, smem_rows, st);
+  launch_rows<float>(a, ROW_FFT_ONLY, nrt, smem_rows, st, false);
   ColArgs<float> c;
   c.inst = dI;
   c.tiles = dCT;
@@ -240,7 +240,7 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   a.Bout = static_cast<float*>(B_dev);
   a.t_field = t;
   a.demag_only = demag_only;
-  launch_rows<float>(a, ROW_FIELD, nrt, smem_rows, st);
+  launch_rows<float>(a, ROW_FIELD, nrt, smem_rows, st, false);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     if (err_msg) *err_msg = "llg_field_noalloc: kernel launch failed";

@@ -186,6 +186,10 @@ struct Engine final : llg_ctx {
   std::vector<ColTile> ct, ct3;    // column tiles of films and of 3D grids
   DevInst* dI = nullptr;
   RowTile* dRT = nullptr;
+  // row tiles of films and of 3D grids (the row-family and adjoint kernels
+  // have a variant for each; the elementwise kernels take all tiles)
+  std::vector<RowTile> rt2, rt3;
+  RowTile *dRT2 = nullptr, *dRT3 = nullptr;
   ColTile* dCT = nullptr;
   ColTile* dCT3 = nullptr;
   int R = 2, TX = 8;
@@ -491,7 +495,9 @@ struct Engine final : llg_ctx {
       if (a.op == RECORD) rec_steps = std::max(rec_steps, a.b - a.a);
 
     const size_t S = slot();
-    bool ok = alloc(&dI, n) && alloc(&dRT, rt.size()) && alloc(&dCT, std::max<size_t>(1, ct.size())) &&
+    for (const RowTile& t : rt) (H[t.inst].nz > 1 ? rt3 : rt2).push_back(t);
+    bool ok = alloc(&dI, n) && alloc(&dRT, rt.size()) && alloc(&dRT2, std::max<size_t>(1, rt2.size())) &&
+              alloc(&dRT3, std::max<size_t>(1, rt3.size())) && alloc(&dCT, std::max<size_t>(1, ct.size())) &&
               alloc(&dCT3, std::max<size_t>(1, ct3.size())) && alloc(&psi, total_nodes) &&
               alloc(&dpsi, total_nodes) && alloc(&m, S) && alloc(&Ya, S) && alloc(&Yb, S) && alloc(&acc, S) &&
               alloc(&tens, total_tens) && alloc(&spec, total_spec) && alloc(&tw, kTwiddleN) &&
@@ -506,6 +512,14 @@ struct Engine final : llg_ctx {
     cudaError_t e;
     if ((e = cudaMemcpyAsync(dI, H.data(), sizeof(DevInst) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "upload descriptors");
+    if (!rt2.empty() &&
+        (e = cudaMemcpyAsync(dRT2, rt2.data(), sizeof(RowTile) * rt2.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+      return cuda_fail(e, "upload row tiles");
+    if (!rt3.empty() &&
+        (e = cudaMemcpyAsync(dRT3, rt3.data(), sizeof(RowTile) * rt3.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+      return cuda_fail(e, "upload row tiles");
     if ((e = cudaMemcpyAsync(dRT, rt.data(), sizeof(RowTile) * rt.size(), cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
       return cuda_fail(e, "upload row tiles");
@@ -594,11 +608,21 @@ struct Engine final : llg_ctx {
     a.nsteps = N;
     return a;
   }
-  void rows(const RowArgs<T>& a, int mode) {
+  void rows(const RowArgs<T>& a0, int mode) {
+    RowArgs<T> a = a0;
+    const size_t sm = mode == ROW_STAGE ? smem_rows : smem_misc;
     if (mode == ROW_STAGE) time_begin(0);
-    launch_rows<T>(a, mode, (int)rt.size(), mode == ROW_STAGE ? smem_rows : smem_misc, st);
+    if (!rt2.empty()) {
+      a.tiles = dRT2;
+      launch_rows<T>(a, mode, (int)rt2.size(), sm, st, false);
+      ++nlaunch;
+    }
+    if (!rt3.empty()) {
+      a.tiles = dRT3;
+      launch_rows<T>(a, mode, (int)rt3.size(), sm, st, true);
+      ++nlaunch;
+    }
     if (mode == ROW_STAGE) time_end(0);
-    ++nlaunch;
   }
   void cols() {
     ColArgs<T> c;
@@ -831,11 +855,20 @@ struct Engine final : llg_ctx {
     a.n_from = n_from;
     return a;
   }
-  void adj(const AdjArgs<T>& a) {
+  void adj(const AdjArgs<T>& a0) {
+    AdjArgs<T> a = a0;
     time_begin(2);
-    launch_adj<T>(a, (int)rt.size(), smem_adj, st);
+    if (!rt2.empty()) {
+      a.tiles = dRT2;
+      launch_adj<T>(a, (int)rt2.size(), smem_adj, st, false);
+      ++nlaunch;
+    }
+    if (!rt3.empty()) {
+      a.tiles = dRT3;
+      launch_adj<T>(a, (int)rt3.size(), smem_adj, st, true);
+      ++nlaunch;
+    }
     time_end(2);
-    ++nlaunch;
   }
 
   llg_status adjoint(void* dphi, void* dm0) override {
