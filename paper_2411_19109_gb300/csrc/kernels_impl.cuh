@@ -537,6 +537,7 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
   const long long n = (a.step_base ? *a.step_base : 0) + a.local_step;
   const int ylo = max(0, y0 - 1), yhi = min(ny, y0 + nr + 1);
   T* __restrict__ gacc = a.acc;
+  const T* __restrict__ gm = a.m;
   T* __restrict__ gYout = a.Yout;
   T* __restrict__ gmout = a.mout;
   T* __restrict__ gB = a.Bout;
@@ -580,6 +581,15 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
     const long long n0 = zoff + (long long)y * nx + x;
     const int sl = node_slot<T>(x);
     const int oi = (g.rl + 1) * nx + x;
+    // m_n and the RK accumulator of this node first (their latencies overlap
+    // the field assembly below)
+    T mn[3], ac[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long id = off3 + c * nodes + n0;
+      mn[c] = gm[id];
+      ac[c] = s > 1 ? gacc[id] : (T)0;
+    }
     const T pi = sP[oi];
     T yi[3], B[3];
 #pragma unroll
@@ -625,15 +635,15 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
     for (int c = 0; c < 3; ++c) {
       const long long id = off3 + c * nodes + n0;
       if (gB) gB[id] = B[c];
-      const T m0 = a.m[id];
+      const T m0 = mn[c];
       if (s == 1) {
         gacc[id] = k[c];
         yn[c] = m0 + hs * k[c];
       } else if (s < 4) {
-        gacc[id] = gacc[id] + (T)2 * k[c];
+        gacc[id] = ac[c] + (T)2 * k[c];
         yn[c] = m0 + hs * k[c];
       } else {
-        yn[c] = m0 + dt / (T)6 * (gacc[id] + k[c]);
+        yn[c] = m0 + dt / (T)6 * (ac[c] + k[c]);
         gmout[id] = yn[c];
         if (gck) gck[id] = yn[c];
       }
@@ -778,6 +788,8 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   T* __restrict__ gpsib = a.psib;
   T* __restrict__ gpsic = a.psic;
   T* __restrict__ gbo = a.BbarOut;
+  const T* __restrict__ gYp = a.Yprev;
+  const T* __restrict__ gBp = a.Bprev;
   const int ylo = max(0, y0 - 1), yhi = min(ny, y0 + nr + 1);
   if (tid == 0) {
     mbar_init(&bars[0], 1);
@@ -817,9 +829,27 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
     const long long n0 = zoff + (long long)y * nx + x;
     const int sl = node_slot<T>(x);
-    T lam[3];
+    // every pointwise value of this node first, so that the load latencies
+    // overlap (these arrays are disjoint from the ones this loop writes)
+    T lam[3], gg[3], gsum[3], yp[3], bp[3];
+    T qs = 0, qc = 0;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) lam[c] = glam[off3 + c * nodes + n0];
+    for (int c = 0; c < 3; ++c) {
+      const long long id = off3 + c * nodes + n0;
+      lam[c] = glam[id];
+      if (!seed) {
+        gg[c] = ggp[id];
+        gsum[c] = s < 4 ? gG[id] : (T)0;
+      }
+      if (emit) {
+        yp[c] = gYp[id];
+        bp[c] = gBp[id];
+      }
+    }
+    if (!seed) {
+      qs = gpsib[I.node_off + n0];
+      qc = gpsic[I.node_off + n0];
+    }
     T u[3];
     if (seed) {
 #pragma unroll
@@ -827,12 +857,11 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
     } else {
       const int oi = (g.rl + 1) * nx + x;
       const T pi = sP[oi];
-      T yi[3], bi[3], gg[3];
+      T yi[3], bi[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         yi[c] = sYs[c * cs + oi];
         bi[c] = sBb[c * cs + oi];
-        gg[c] = ggp[off3 + c * nodes + n0];
       }
       T qpsi = 0;
       // exchange transpose (gather form) and its psi derivative
@@ -884,21 +913,18 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
         gg[c] += Ms * pi * D[c];
       }
       qpsi += Ms * dot3(yi, D);
-      {
-        T sum = gpsib[I.node_off + n0], comp = gpsic[I.node_off + n0];
-        kahan_add(sum, comp, qpsi);
-        gpsib[I.node_off + n0] = sum;
-        gpsic[I.node_off + n0] = comp;
-      }
+      kahan_add(qs, qc, qpsi);
+      gpsib[I.node_off + n0] = qs;
+      gpsic[I.node_off + n0] = qc;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const long long id = off3 + c * nodes + n0;
         if (s == 4) {
           gG[id] = gg[c];
         } else if (s > 1) {
-          gG[id] = gG[id] + gg[c];
+          gG[id] = gsum[c] + gg[c];
         } else {
-          lam[c] += gG[id] + gg[c];
+          lam[c] += gsum[c] + gg[c];
         }
       }
       if (s == 1) {
@@ -917,12 +943,6 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
       for (int c = 0; c < 3; ++c) u[c] = (s > 1) ? ca * lam[c] + cb * gg[c] : dt / (T)6 * lam[c];
     }
     if (!emit) continue;
-    T yp[3], bp[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      yp[c] = a.Yprev[off3 + c * nodes + n0];
-      bp[c] = a.Bprev[off3 + c * nodes + n0];
-    }
     T bbar[3], gl[3], al, ga;
     damping_at(I, K, x, y, al, ga);
     rhs_vjp(u, yp, bp, al, ga, bbar, gl);
@@ -962,7 +982,7 @@ __device__ __forceinline__ void adj_dispatch(const AdjArgs<T>& a, const DevInst&
 }
 
 template <typename T, bool Z3>
-__global__ void __launch_bounds__(kAdjThreads) adj_kernel(AdjArgs<T> a) {
+__global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? 2 : 1) adj_kernel(AdjArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ DevInst sI;
   __shared__ uint64_t bars[2];
