@@ -56,7 +56,16 @@ struct ColArgs {
   const cplx<T>* tw;
   const T* tens;      // packed spectrum tables
   int cols_max;
+  int* err;           // error word for bounded waits (nullable)
 };
+
+// Dynamic shared memory of the film column kernel for a column FFT of length
+// Py: FFT groups (within kExch complex), W_Py, and the tensor records of the
+// tile's 1024/Py columns plus the Nyquist column (4 components each).
+template <typename T>
+__host__ __device__ constexpr size_t cols_smem_bytes(int Py) {
+  return (size_t)(kExch + Py) * sizeof(cplx<T>) + (size_t)(1024 / Py + 1) * (Py / 2 + 1) * 4 * sizeof(T);
+}
 
 template <typename T>
 struct AdjArgs {

@@ -211,6 +211,15 @@ __device__ __forceinline__ void load_tensor(const float* tab, long long idx, flo
   const float4 v = __ldg(reinterpret_cast<const float4*>(tab) + idx);
   n[0] = v.x; n[1] = v.y; n[2] = v.z; n[3] = v.w;
 }
+__device__ __forceinline__ void load_tensor_smem(const float* tab, int idx, float n[4]) {
+  const float4 v = reinterpret_cast<const float4*>(tab)[idx];
+  n[0] = v.x; n[1] = v.y; n[2] = v.z; n[3] = v.w;
+}
+__device__ __forceinline__ void load_tensor_smem(const double* tab, int idx, double n[4]) {
+  const double2 a = reinterpret_cast<const double2*>(tab)[2 * idx];
+  const double2 b = reinterpret_cast<const double2*>(tab)[2 * idx + 1];
+  n[0] = a.x; n[1] = a.y; n[2] = b.x; n[3] = b.y;
+}
 __device__ __forceinline__ void load_tensor(const double* tab, long long idx, double n[4]) {
   const double2 a = __ldg(reinterpret_cast<const double2*>(tab) + 2 * idx);
   const double2 b = __ldg(reinterpret_cast<const double2*>(tab) + 2 * idx + 1);
@@ -219,7 +228,7 @@ __device__ __forceinline__ void load_tensor(const double* tab, long long idx, do
 
 template <typename T, int L>
 __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I, const ColTile& tile,
-                                          cplx<T>* smem) {
+                                          cplx<T>* smem, uint64_t* bar) {
   using C = cplx<T>;
   constexpr int TT = L / 8;
   constexpr int NC = 1024 / L;                     // columns per block
@@ -235,6 +244,21 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
   C* tw1 = smem + kExch;
   C* spec = a.spec + I.spec_off + tile.kx0;
   const GroupSync gs = group_sync(TT);
+  // The tile's tensor records ([col][ky][xx,yy,zz,xy], contiguous in the
+  // table) and, for the tile holding kx = 0, those of the Nyquist column go
+  // to shared memory by one bulk copy each, behind the load and forward FFT.
+  constexpr int nky = L / 2 + 1;
+  T* stab = reinterpret_cast<T*>(tw1 + L);
+  const T* tab = a.tens + I.tens_off;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+    const unsigned rb = (unsigned)(ncols * nky * 4 * sizeof(T));
+    const unsigned nb = tile.kx0 == 0 ? (unsigned)(nky * 4 * sizeof(T)) : 0u;
+    mbar_arrive_expect(bar, rb + nb);
+    bulk_load(stab, tab + (long long)tile.kx0 * nky * 4, rb, bar);
+    if (nb) bulk_load(stab + NC * nky * 4, tab + (long long)Lx * nky * 4, nb, bar);
+  }
   load_twiddles(tw1, a.tw, L);
   // coalesced load of the tile (ny rows x 3 components x NC column slots,
   // columns fastest) into the groups; the divisors are compile-time
@@ -258,8 +282,8 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
 #pragma unroll
   for (int s = 0; s < 8; ++s) grp[rf_pad(t + TT * s)] = v[s];
   __syncthreads();
-  const T* tab = a.tens + I.tens_off;
-  constexpr int nky = L / 2 + 1;
+  mbar_wait(bar, 0, a.err);
+  const int cl = active ? col : 0;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int ky = t + TT * s;
@@ -267,7 +291,7 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
     const int kyf = lo ? ky : L - ky;
     if (kx != 0) {
       T n[4];
-      load_tensor(tab, (long long)kx * nky + kyf, n);
+      load_tensor_smem(stab, cl * nky + kyf, n);
       const T nxy = lo ? n[3] : -n[3];
       if (c == 2) {
         v[s] = cscale(v[s], n[2]);
@@ -280,8 +304,8 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
       // packed DC (kx = 0) and Nyquist (kx = Px/2) columns: separate them by
       // Hermitian symmetry in ky, apply each its own (diagonal) tensor
       T nd[4], nq[4];
-      load_tensor(tab, (long long)kyf, nd);
-      load_tensor(tab, (long long)Lx * nky + kyf, nq);
+      load_tensor_smem(stab, kyf, nd);
+      load_tensor_smem(stab, NC * nky + kyf, nq);
       const int km = (L - ky) & (L - 1);
       const T p = (T)0.5 * (nd[c] + nq[c]), q = (T)0.5 * (nd[c] - nq[c]);
       const C vb = cconj(grp[rf_pad(km)]);
@@ -308,19 +332,20 @@ __global__ void __launch_bounds__(kColThreads, sizeof(T) == 4 ? 3 : 1) cols_kern
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ DevInst sI;
+  __shared__ uint64_t bar;
   const ColTile tile = a.tiles[blockIdx.x];
   load_inst(sI, a.inst + tile.inst);
   __syncthreads();
   C* sm = reinterpret_cast<C*>(smem_raw);
   switch (sI.log2Py) {
-    case 3: cols_body<T, 8>(a, sI, tile, sm); break;
-    case 4: cols_body<T, 16>(a, sI, tile, sm); break;
-    case 5: cols_body<T, 32>(a, sI, tile, sm); break;
-    case 6: cols_body<T, 64>(a, sI, tile, sm); break;
-    case 7: cols_body<T, 128>(a, sI, tile, sm); break;
-    case 8: cols_body<T, 256>(a, sI, tile, sm); break;
-    case 9: cols_body<T, 512>(a, sI, tile, sm); break;
-    case 10: cols_body<T, 1024>(a, sI, tile, sm); break;
+    case 3: cols_body<T, 8>(a, sI, tile, sm, &bar); break;
+    case 4: cols_body<T, 16>(a, sI, tile, sm, &bar); break;
+    case 5: cols_body<T, 32>(a, sI, tile, sm, &bar); break;
+    case 6: cols_body<T, 64>(a, sI, tile, sm, &bar); break;
+    case 7: cols_body<T, 128>(a, sI, tile, sm, &bar); break;
+    case 8: cols_body<T, 256>(a, sI, tile, sm, &bar); break;
+    case 9: cols_body<T, 512>(a, sI, tile, sm, &bar); break;
+    case 10: cols_body<T, 1024>(a, sI, tile, sm, &bar); break;
     default: break;
   }
 }

@@ -227,7 +227,7 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   // exchange scratch + twiddle table (W_{2Lx} for the row kernels, W_Py for
   // the column kernel): below the 48 KB default, no opt-in attribute needed
   const size_t smem_rows = (size_t)(kExch + 2 * d.Lx) * sizeof(float2);
-  const size_t smem_cols = (size_t)(kExch + Py) * sizeof(float2);
+  const size_t smem_cols = cols_smem_bytes<float>(Py);
   launch_rows<float>(a, ROW_FFT_ONLY, nrt, smem_rows, st, false);
   ColArgs<float> c;
   c.inst = dI;
@@ -236,6 +236,7 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   c.tw = tw;
   c.tens = tens;
   c.cols_max = tx;
+  c.err = nullptr;
   launch_cols<float>(c, nct, smem_cols, st);
   a.Bout = static_cast<float*>(B_dev);
   a.t_field = t;

@@ -379,7 +379,7 @@ struct Engine final : llg_ctx {
       if (P[i].nz > 1)
         smem_c3 = std::max(smem_c3, cols3_smem_bytes<T>(Py, P[i].nz, cols3_per_tile(Py, P[i].nz, Lx)));
       else
-        smem_cols = std::max(smem_cols, (size_t)(kExch + Py) * sizeof(C));
+        smem_cols = std::max(smem_cols, cols_smem_bytes<T>(Py));
       smem_misc = std::max(smem_misc, (size_t)(kExch + 2 * Lx) * sizeof(C));
       smem_rows = std::max(smem_rows, stage_smem_bytes<T>(Lx, P[i].nx));
       smem_adj = std::max(smem_adj, adj_smem_bytes<T>(Lx, P[i].nx));
@@ -632,6 +632,7 @@ struct Engine final : llg_ctx {
     c.tw = tw;
     c.tens = tens;
     c.cols_max = TX;
+    c.err = errw;
     time_begin(1);
     if (!ct.empty()) {
       launch_cols<T>(c, (int)ct.size(), smem_cols, st);
