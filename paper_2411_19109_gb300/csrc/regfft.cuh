@@ -91,8 +91,27 @@ __device__ __forceinline__ void rf_pass(C v[8], int t, int Ns, const C* __restri
 #pragma unroll
     for (int r = 0; r < RP; ++r) x[r] = v[b + r * NB];
     if (Ns > 1) {
+      using R = decltype(C::x);
+      if constexpr (sizeof(R) == 4 && RP >= 4) {
+        // FP32: load W^step only and form its powers by products (at most
+        // three roundings deep, ~3 ulp), trading shared-memory loads, the
+        // limiting resource of these kernels, for FMAs
+        C w[RP];
+        w[1] = rf_tw<C, DIR>(tw, step, tws);
+        w[2] = cmul(w[1], w[1]);
+        w[3] = cmul(w[2], w[1]);
+        if constexpr (RP == 8) {
+          w[4] = cmul(w[2], w[2]);
+          w[5] = cmul(w[4], w[1]);
+          w[6] = cmul(w[3], w[3]);
+          w[7] = cmul(w[4], w[3]);
+        }
 #pragma unroll
-      for (int r = 1; r < RP; ++r) x[r] = cmul(x[r], rf_tw<C, DIR>(tw, r * step, tws));
+        for (int r = 1; r < RP; ++r) x[r] = cmul(x[r], w[r]);
+      } else {
+#pragma unroll
+        for (int r = 1; r < RP; ++r) x[r] = cmul(x[r], rf_tw<C, DIR>(tw, r * step, tws));
+      }
     }
     if (RP == 2) {
       rf_dft2<C, DIR>(x[0], x[1]);
