@@ -99,6 +99,12 @@ template <typename T>
 void launch_rows(const RowArgs<T>& a, int mode, int ntiles, size_t smem, cudaStream_t st, bool z3);
 template <typename T>
 void launch_cols(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+// film column pass with 16 register elements per lane (FP32, Py = 128, 256, 1024)
+template <typename T>
+void launch_cols16(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+template <typename T>
+void smem_cols16(size_t smem);
+__host__ __device__ constexpr bool cols16_length(int Py) { return Py == 128 || Py == 256 || Py == 1024; }
 // column pass of 3D grids (nz > 1)
 template <typename T>
 void launch_cols3(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);

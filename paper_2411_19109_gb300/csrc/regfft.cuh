@@ -212,6 +212,159 @@ __device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int
   }
 }
 
+// ---------------------------------------------------------------------------
+// 16 elements per thread (TT = L/16 threads per sequence): radix-16 passes,
+// so L = 128, 256 take one shared-memory exchange instead of two and
+// L = 1024 two instead of three.  Same stride layout: thread t holds element
+// t + TT*s in v[s] on entry and on exit.
+// ---------------------------------------------------------------------------
+
+// a * W_16^M with W_16 = exp(DIR * 2 pi i / 16) (DIR = -1 forward), M fixed.
+template <typename C, int DIR, int M>
+__device__ __forceinline__ C rf_w16(C a) {
+  using R = decltype(C::x);
+  constexpr int m = M & 15;
+  const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173, h = (R)0.70710678118654752440;
+  if constexpr (m == 0) {
+    return a;
+  } else if constexpr (m == 4) {
+    return DIR < 0 ? mul_mi(a) : mul_pi(a);
+  } else if constexpr (m == 8) {
+    return mk<C>(-a.x, -a.y);
+  } else if constexpr (m == 12) {
+    return DIR < 0 ? mul_pi(a) : mul_mi(a);
+  } else {
+    // cos and sin of 2 pi m / 16
+    const R cs = (m == 1 || m == 15) ? c1 : (m == 2 || m == 14) ? h : (m == 3 || m == 13) ? s1
+               : (m == 5 || m == 11) ? -s1 : (m == 6 || m == 10) ? -h : -c1;
+    const R sn = (m == 1 || m == 7) ? s1 : (m == 2 || m == 6) ? h : (m == 3 || m == 5) ? c1
+               : (m == 9 || m == 15) ? -s1 : (m == 10 || m == 14) ? -h : -c1;
+    const R wy = DIR < 0 ? -sn : sn;
+    return mk<C>(a.x * cs - a.y * wy, a.x * wy + a.y * cs);
+  }
+}
+
+// 16-point DFT in place as 4 x 4: x[k1 + 4 k2] = sum_n2 W16^{n2 k1} W4^{n2 k2}
+// sum_n1 W4^{n1 k1} x[4 n1 + n2].
+template <typename C, int DIR>
+__device__ __forceinline__ void rf_dft16(C x[16]) {
+  C a[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    C y0 = x[n2], y1 = x[4 + n2], y2 = x[8 + n2], y3 = x[12 + n2];
+    rf_dft4<C, DIR>(y0, y1, y2, y3);
+    a[n2][0] = y0; a[n2][1] = y1; a[n2][2] = y2; a[n2][3] = y3;
+  }
+  a[1][1] = rf_w16<C, DIR, 1>(a[1][1]);
+  a[1][2] = rf_w16<C, DIR, 2>(a[1][2]);
+  a[1][3] = rf_w16<C, DIR, 3>(a[1][3]);
+  a[2][1] = rf_w16<C, DIR, 2>(a[2][1]);
+  a[2][2] = rf_w16<C, DIR, 4>(a[2][2]);
+  a[2][3] = rf_w16<C, DIR, 6>(a[2][3]);
+  a[3][1] = rf_w16<C, DIR, 3>(a[3][1]);
+  a[3][2] = rf_w16<C, DIR, 6>(a[3][2]);
+  a[3][3] = rf_w16<C, DIR, 9>(a[3][3]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C z0 = a[0][k1], z1 = a[1][k1], z2 = a[2][k1], z3 = a[3][k1];
+    rf_dft4<C, DIR>(z0, z1, z2, z3);
+    x[k1] = z0; x[k1 + 4] = z1; x[k1 + 8] = z2; x[k1 + 12] = z3;
+  }
+}
+
+// One Stockham pass of radix RP on the sixteen registers of thread t
+// (butterfly b: j = t + TT*b, inputs v[b + r*(16/RP)]).
+template <typename C, int L, int RP, int DIR>
+__device__ __forceinline__ void rf_pass16(C v[16], int t, int Ns, const C* __restrict__ tw, int tws, int dst[16]) {
+  constexpr int TT = L / 16;
+  constexpr int NB = 16 / RP;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = t + TT * b;
+    const int k = j & (Ns - 1);
+    const int step = (L / (Ns * RP)) * k;         // twiddle W_L^{r*step}
+    C x[RP];
+#pragma unroll
+    for (int r = 0; r < RP; ++r) x[r] = v[b + r * NB];
+    if (Ns > 1) {
+      using R = decltype(C::x);
+      if constexpr (sizeof(R) == 4 && RP == 16) {
+        // FP32: W^step and W^{4 step} loaded, the other powers by products
+        // at most three roundings deep
+        C w[16];
+        w[1] = rf_tw<C, DIR>(tw, step, tws);
+        w[4] = rf_tw<C, DIR>(tw, 4 * step, tws);
+        w[2] = cmul(w[1], w[1]);
+        w[3] = cmul(w[2], w[1]);
+        w[5] = cmul(w[4], w[1]);
+        w[6] = cmul(w[4], w[2]);
+        w[7] = cmul(w[4], w[3]);
+        w[8] = cmul(w[4], w[4]);
+        w[9] = cmul(w[8], w[1]);
+        w[10] = cmul(w[8], w[2]);
+        w[11] = cmul(w[8], w[3]);
+        w[12] = cmul(w[8], w[4]);
+        w[13] = cmul(w[12], w[1]);
+        w[14] = cmul(w[12], w[2]);
+        w[15] = cmul(w[12], w[3]);
+#pragma unroll
+        for (int r = 1; r < RP; ++r) x[r] = cmul(x[r], w[r]);
+      } else {
+#pragma unroll
+        for (int r = 1; r < RP; ++r) x[r] = cmul(x[r], rf_tw<C, DIR>(tw, r * step, tws));
+      }
+    }
+    if constexpr (RP == 2) {
+      rf_dft2<C, DIR>(x[0], x[1]);
+    } else if constexpr (RP == 4) {
+      rf_dft4<C, DIR>(x[0], x[1], x[2], x[3]);
+    } else if constexpr (RP == 8) {
+      rf_dft8<C, DIR>(x);
+    } else {
+      rf_dft16<C, DIR>(x);
+    }
+    const int base = (j / Ns) * Ns * RP + k;
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+      v[b + r * NB] = x[r];
+      dst[b + r * NB] = base + r * Ns;
+    }
+  }
+}
+
+// Full transform of one sequence held 16 elements per thread; element i is
+// exchanged through sm[pad(i)].  First pass radix 2^(log2 L mod 4) (16 when
+// that is 0), then radix-16 passes.
+template <typename C, int L, int DIR>
+__device__ __forceinline__ void regfft16(C (&v)[16], C* sm, int t, const C* __restrict__ tw, int tws, GroupSync sync) {
+  constexpr int M = (L == 16) ? 4 : (L == 32) ? 5 : (L == 64) ? 6 : (L == 128) ? 7 : (L == 256) ? 8
+                  : (L == 512) ? 9 : (L == 1024) ? 10 : 11;
+  static_assert((1 << M) == L, "L must be a power of two in [16, 2048]");
+  constexpr int TT = L / 16;
+  constexpr int R0 = (M % 4 == 0) ? 16 : (1 << (M % 4));
+  constexpr int NPASS = (M % 4 == 0) ? M / 4 : M / 4 + 1;
+  int dst[16];
+  int Ns = 1;
+#pragma unroll
+  for (int p = 0; p < NPASS; ++p) {
+    if (p > 0) {
+#pragma unroll
+      for (int s = 0; s < 16; ++s) sm[rf_pad(dst[s])] = v[s];
+      sync();
+#pragma unroll
+      for (int s = 0; s < 16; ++s) v[s] = sm[rf_pad(t + TT * s)];
+      sync();
+    }
+    if (p == 0) {
+      rf_pass16<C, L, R0, DIR>(v, t, Ns, tw, tws, dst);
+      Ns *= R0;
+    } else {
+      rf_pass16<C, L, 16, DIR>(v, t, Ns, tw, tws, dst);
+      Ns *= 16;
+    }
+  }
+}
+
 // Copy W_P^k, k < P, from the global W_4096 table into shared memory
 // (all threads; the caller synchronises before use).
 template <typename C>

@@ -183,7 +183,8 @@ struct Engine final : llg_ctx {
 
   std::vector<DevInst> H;
   std::vector<RowTile> rt;
-  std::vector<ColTile> ct, ct3;    // column tiles of films and of 3D grids
+  // column tiles of films (8- and 16-element FFT lanes) and of 3D grids
+  std::vector<ColTile> ct, ct16, ct3;
   DevInst* dI = nullptr;
   RowTile* dRT = nullptr;
   // row tiles of films and of 3D grids (the row-family and adjoint kernels
@@ -192,6 +193,7 @@ struct Engine final : llg_ctx {
   RowTile *dRT2 = nullptr, *dRT3 = nullptr;
   ColTile* dCT = nullptr;
   ColTile* dCT3 = nullptr;
+  ColTile* dCT16 = nullptr;
   int R = 2, TX = 8;
   size_t smem = 0, smem_rows = 0, smem_cols = 0, smem_c3 = 0, smem_adj = 0, smem_misc = 0;
   int* errw = nullptr;
@@ -475,7 +477,9 @@ struct Engine final : llg_ctx {
       for (int z = 0, k = 0; z < p.nz; ++z)
         for (int y0 = 0; y0 < p.ny; y0 += rows, ++k) rt.push_back({i, z, y0, std::min(rows, p.ny - y0), k});
       const int tx = p.nz > 1 ? cols3_per_tile(d.Py, p.nz, d.Lx) : std::max(1, std::min(1024 / d.Py, d.Lx));
-      for (int k0 = 0; k0 < d.Lx; k0 += tx) (p.nz > 1 ? ct3 : ct).push_back({i, k0, std::min(tx, d.Lx - k0), 0});
+      const bool c16 = sizeof(T) == 4 && p.nz == 1 && cols16_length(d.Py);
+      for (int k0 = 0; k0 < d.Lx; k0 += tx)
+        (p.nz > 1 ? ct3 : (c16 ? ct16 : ct)).push_back({i, k0, std::min(tx, d.Lx - k0), 0});
       TX = std::max(TX, tx);
     }
     total_nodes = node_off;
@@ -498,7 +502,7 @@ struct Engine final : llg_ctx {
     for (const RowTile& t : rt) (H[t.inst].nz > 1 ? rt3 : rt2).push_back(t);
     bool ok = alloc(&dI, n) && alloc(&dRT, rt.size()) && alloc(&dRT2, std::max<size_t>(1, rt2.size())) &&
               alloc(&dRT3, std::max<size_t>(1, rt3.size())) && alloc(&dCT, std::max<size_t>(1, ct.size())) &&
-              alloc(&dCT3, std::max<size_t>(1, ct3.size())) && alloc(&psi, total_nodes) &&
+              alloc(&dCT3, std::max<size_t>(1, ct3.size())) && alloc(&dCT16, std::max<size_t>(1, ct16.size())) && alloc(&psi, total_nodes) &&
               alloc(&dpsi, total_nodes) && alloc(&m, S) && alloc(&Ya, S) && alloc(&Yb, S) && alloc(&acc, S) &&
               alloc(&tens, total_tens) && alloc(&spec, total_spec) && alloc(&tw, kTwiddleN) &&
               alloc(&tw64, kTwiddleN) && alloc(&recY, S * (4 * rec_steps + 1)) &&
@@ -529,6 +533,10 @@ struct Engine final : llg_ctx {
       return cuda_fail(e, "upload column tiles");
     if (!ct3.empty() &&
         (e = cudaMemcpyAsync(dCT3, ct3.data(), sizeof(ColTile) * ct3.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+      return cuda_fail(e, "upload column tiles");
+    if (!ct16.empty() &&
+        (e = cudaMemcpyAsync(dCT16, ct16.data(), sizeof(ColTile) * ct16.size(), cudaMemcpyHostToDevice, st)) !=
             cudaSuccess)
       return cuda_fail(e, "upload column tiles");
     {
@@ -583,6 +591,7 @@ struct Engine final : llg_ctx {
     if (e != cudaSuccess) return cuda_fail(e, "demag tensor");
     set_smem_limits<T>(smem_rows, smem_misc, smem_cols, smem_adj);
     smem_cols3<T>(smem_c3);
+    if constexpr (sizeof(T) == 4) smem_cols16<T>(smem_cols);
     cudaMemsetAsync(errw, 0, sizeof(int), st);
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
@@ -637,6 +646,13 @@ struct Engine final : llg_ctx {
     if (!ct.empty()) {
       launch_cols<T>(c, (int)ct.size(), smem_cols, st);
       ++nlaunch;
+    }
+    if constexpr (sizeof(T) == 4) {
+      if (!ct16.empty()) {
+        c.tiles = dCT16;
+        launch_cols16<T>(c, (int)ct16.size(), smem_cols, st);
+        ++nlaunch;
+      }
     }
     if (!ct3.empty()) {
       c.tiles = dCT3;

@@ -21,7 +21,9 @@ def _needs_gpu():
     load()
 
 
-FIELD_CASES = [(4, 1), (8, 5), (12, 7), (16, 9), (32, 32), (36, 20), (64, 3)]
+# column lengths 8..64 (8-element FFT lanes) and 128, 256, 1024 (16-element
+# lanes in FP32: ny = 64, 100, 400)
+FIELD_CASES = [(4, 1), (8, 5), (12, 7), (16, 9), (32, 32), (36, 20), (64, 3), (8, 64), (4, 100), (4, 400)]
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 2e-6)])
@@ -45,7 +47,8 @@ def test_field_parity(shape, precision, tol):
 
 @pytest.mark.parametrize("precision,tol_m,tol_g", [("fp64", 1e-10, 1e-9), ("fp32", 1e-5, 1e-4)])
 @pytest.mark.parametrize("shape,objective", [((12, 8), W.J_PORT), ((16, 12), W.J_ENERGY_AREA),
-                                             ((8, 5), W.J_PORT), ((20, 3), W.J_ENERGY_AREA)])
+                                             ((8, 5), W.J_PORT), ((20, 3), W.J_ENERGY_AREA),
+                                             ((8, 64), W.J_PORT)])
 def test_forward_adjoint_parity_small(shape, objective, precision, tol_m, tol_g):
     inst = W.random_small(*shape, 1, seed=3, nsteps=40, objective=objective)
     g = gpu_run([inst], precision, want_dm0=True)
@@ -204,3 +207,15 @@ def test_graph_replay_matches_direct_launches():
                     np.testing.assert_array_equal(x.double().cpu().numpy(), direct["dphi"][k])
         finally:
             s.close()
+
+
+def test_batch_with_both_column_kernels_matches_single_runs():
+    """Column lengths 64 and 128 in one FP32 context: one instance on each
+    column kernel, each identical bit for bit to its run alone."""
+    insts = [W.random_small(12, 32, 1, seed=51, nsteps=12), W.random_small(8, 64, 1, seed=52, nsteps=12)]
+    b = gpu_run(insts, "fp32")
+    for k, inst in enumerate(insts):
+        single = gpu_run([inst], "fp32")
+        np.testing.assert_array_equal(single["dphi"][0], b["dphi"][k])
+        np.testing.assert_array_equal(single["mT"][0], b["mT"][k])
+        assert single["J"][0] == b["J"][k]
