@@ -41,7 +41,7 @@ UNIT = "node-steps/s"
 # at least once: see DESIGN.md, "Kernels and their rooflines".
 BYTES_PER_NODE = {0: 112.0, 1: 48.0, 2: 185.0}
 FAMILY = {0: "rows_kernel<float,ROW_STAGE> (inverse row FFT + field + RK4 stage + forward row FFT)",
-          1: "cols_kernel<float> (column FFT, tensor product, inverse column FFT)",
+          1: "cols16_kernel<float> (column FFT with 16-element lanes, tensor product, inverse column FFT)",
           2: "adj_kernel<float> (adjoint stage: demag/exchange transposes, dJ/dpsi, next Bbar + row FFT)"}
 
 
@@ -74,8 +74,8 @@ def measured_peaks():
 
 
 # the sources the FP32 stage, column and adjoint kernels are compiled from
-KERNEL_SOURCES = ("common.cuh", "kernels.cuh", "kernels_impl.cuh", "regfft.cuh", "tma.cuh",
-                  "k_stage_f32.cu", "k_cols_f32.cu", "k_adj_f32.cu")
+KERNEL_SOURCES = ("common.cuh", "kernels.cuh", "kernels_impl.cuh", "regfft.cuh", "tma.cuh", "cols16.cuh",
+                  "k_stage_f32.cu", "k_cols_f32.cu", "k_cols16_f32.cu", "k_adj_f32.cu")
 
 
 def kernel_source_hash():
