@@ -193,6 +193,51 @@ void llg_destroy(llg_ctx* ctx);
 llg_status llg_field_noalloc(const llg_problem* prob, const void* phi_dev, const void* m_dev, double t,
                              int demag_only, void* B_dev, void* cuda_stream, const char** err_msg);
 
+/* ------------------------------------------------------------------------
+ * RBF parameterisation of the level-set function and the optimiser step.
+ * Phi on a rectangular design box is built from nrx*nry multiquadric cones
+ * g_k(x) = s_k - sqrt(|x - x_k|^2 + c^2) (Eq. 2; centres at the centres of
+ * equal cells of the box, c = the centre spacing), combined by the p-norm of
+ * Eq. 3, F = ||g + dphi||_p - dphi with dphi = |min over RBFs and design
+ * nodes of g|, and renormalised, Phi = F / max_design |F| (Results, "Level-
+ * set method": Phi kept in [-1, 1]).  The amplitudes s (n = nrx*nry
+ * doubles, k = iy*nrx + ix) are what the optimiser updates (Adam, Methods).
+ * All three calls are asynchronous on the given stream and allocate
+ * nothing; they return LLG_EINVAL for invalid arguments (checked before any
+ * device work) and LLG_ECUDA if a launch fails.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int nx, ny;       /* grid of the phi array ([ny][nx], one layer)           */
+  double dx, dy;    /* node spacing                                          */
+  int box[4];       /* design box x0, x1, y0, y1 (node indices, half open)   */
+  int nrx, nry;     /* RBF centres per axis                                  */
+  double p;         /* p-norm exponent (the paper uses 90)                   */
+} llg_rbf;
+
+/* Bytes of device workspace llg_rbf_phi / llg_rbf_grad need (0 if r is
+ * invalid): about 32 bytes per design node plus 16 per RBF. */
+size_t llg_rbf_workspace_bytes(const llg_rbf* r);
+
+/* Phi = F / max|F| on the design nodes of phi_dev ([ny][nx], float for
+ * LLG_FP32, double for LLG_FP64); nodes outside the box are not touched.
+ * s_dev: n amplitudes (double); work_dev: llg_rbf_workspace_bytes(r) bytes. */
+llg_status llg_rbf_phi(const llg_rbf* r, const double* s_dev, void* phi_dev, int precision, void* work_dev,
+                       void* cuda_stream);
+
+/* dJ/ds (n doubles) for dJ/dPhi given in dJdphi_dev ([ny][nx], only design
+ * nodes read): the exact derivative of the map above, through the shift and
+ * the renormalisation (taken at the minimising node/RBF pair and the
+ * maximising node, the first in index order on ties). */
+llg_status llg_rbf_grad(const llg_rbf* r, const double* s_dev, const void* dJdphi_dev, int precision,
+                        double* dJds_dev, void* work_dev, void* cuda_stream);
+
+/* One Adam step (Kingma & Ba) on n parameters, step number t >= 1:
+ * m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
+ * s <- s - lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps).  All arrays double,
+ * device memory, caller-owned; m and v start at zero. */
+llg_status llg_adam_step(double* s_dev, const double* grad_dev, double* m_dev, double* v_dev, int n, long long t,
+                         double lr, double b1, double b2, double eps, void* cuda_stream);
+
 /* Host-only: the checkpoint action list the library executes.  Writes up to
  * max_actions triples (op, a, b) to `actions` (forward actions first, then
  * reverse), sets *n_forward to the number of forward actions and returns the

@@ -27,7 +27,14 @@ LLG_CKPT_STORE_ALL, LLG_CKPT_PERIODIC, LLG_CKPT_BINOMIAL = 0, 1, 2
 
 EXPORTED = ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query",
             "llg_launch_count", "llg_kernel_time", "llg_last_error", "llg_destroy", "llg_schedule",
-            "llg_padded_extents", "llg_abi_version", "llg_field_noalloc")
+            "llg_padded_extents", "llg_abi_version", "llg_field_noalloc", "llg_rbf_workspace_bytes",
+            "llg_rbf_phi", "llg_rbf_grad", "llg_adam_step")
+
+
+class llg_rbf(ctypes.Structure):
+    """RBF level-set layout (C struct llg_rbf)."""
+    _fields_ = [("nx", c_int), ("ny", c_int), ("dx", c_double), ("dy", c_double), ("box", c_int * 4),
+                ("nrx", c_int), ("nry", c_int), ("p", c_double)]
 
 
 class llg_problem(ctypes.Structure):
@@ -94,6 +101,15 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.llg_field_noalloc.argtypes = [P(llg_problem), c_void_p, c_void_p, c_double, c_int, c_void_p, c_void_p,
                                       P(ctypes.c_char_p)]
     lib.llg_field_noalloc.restype = c_int
+    lib.llg_rbf_workspace_bytes.argtypes = [P(llg_rbf)]
+    lib.llg_rbf_workspace_bytes.restype = ctypes.c_size_t
+    lib.llg_rbf_phi.argtypes = [P(llg_rbf), c_void_p, c_void_p, c_int, c_void_p, c_void_p]
+    lib.llg_rbf_phi.restype = c_int
+    lib.llg_rbf_grad.argtypes = [P(llg_rbf), c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]
+    lib.llg_rbf_grad.restype = c_int
+    lib.llg_adam_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_ll, c_double, c_double, c_double,
+                                  c_double, c_void_p]
+    lib.llg_adam_step.restype = c_int
     for f in ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query"):
         getattr(lib, f).restype = c_int
     _lib = lib
@@ -182,6 +198,39 @@ def llg_field_noalloc(problem, phi_ptr: int, m_ptr: int, t: float, demag_only: b
                                c_void_p(B_ptr), c_void_p(stream), ctypes.byref(msg))
     if st != LLG_OK:
         raise LLGError(st, msg.value.decode() if msg.value else "")
+
+
+def make_rbf(nx: int, ny: int, dx: float, dy: float, box, nrx: int, nry: int, p: float = 90.0) -> llg_rbf:
+    return llg_rbf(nx, ny, dx, dy, (c_int * 4)(*box), nrx, nry, p)
+
+
+def llg_rbf_workspace_bytes(r: llg_rbf) -> int:
+    return int(load().llg_rbf_workspace_bytes(ctypes.byref(r)))
+
+
+def _rbf_check(st: int, what: str) -> None:
+    if st != LLG_OK:
+        raise LLGError(st, f"{what}: invalid arguments" if st == LLG_EINVAL else f"{what}: CUDA launch failed")
+
+
+def llg_rbf_phi(r: llg_rbf, s_ptr: int, phi_ptr: int, precision: int, work_ptr: int, stream: int = 0) -> None:
+    """Phi on the design box from the RBF amplitudes (Eq. 2, 3, renormalised)."""
+    _rbf_check(load().llg_rbf_phi(ctypes.byref(r), c_void_p(s_ptr), c_void_p(phi_ptr), precision,
+                                  c_void_p(work_ptr), c_void_p(stream)), "llg_rbf_phi")
+
+
+def llg_rbf_grad(r: llg_rbf, s_ptr: int, dJdphi_ptr: int, precision: int, dJds_ptr: int, work_ptr: int,
+                 stream: int = 0) -> None:
+    """dJ/ds from dJ/dPhi through the RBF map."""
+    _rbf_check(load().llg_rbf_grad(ctypes.byref(r), c_void_p(s_ptr), c_void_p(dJdphi_ptr), precision,
+                                   c_void_p(dJds_ptr), c_void_p(work_ptr), c_void_p(stream)), "llg_rbf_grad")
+
+
+def llg_adam_step(s_ptr: int, grad_ptr: int, m_ptr: int, v_ptr: int, n: int, t: int, lr: float,
+                  b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8, stream: int = 0) -> None:
+    """One Adam step on n double parameters (step number t >= 1)."""
+    _rbf_check(load().llg_adam_step(c_void_p(s_ptr), c_void_p(grad_ptr), c_void_p(m_ptr), c_void_p(v_ptr), n, t,
+                                    lr, b1, b2, eps, c_void_p(stream)), "llg_adam_step")
 
 
 def llg_query(ctx: int):

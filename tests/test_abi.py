@@ -18,7 +18,7 @@ def declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:llg_status|long long|int|void|const char\s*\*)\s*\**\s*(\w+)\s*\(",
+        for m in re.finditer(r"^\s*(?:llg_status|long long|size_t|int|void|const char\s*\*)\s*\**\s*(\w+)\s*\(",
                              text, flags=re.M):
             names.add(m.group(1))
     return names
@@ -78,3 +78,16 @@ def test_schedule_rejects_bad_arguments(lib):
     from paper_2411_19109_gb300 import LLGError, llg_schedule
     with pytest.raises(LLGError):
         llg_schedule(-1)
+
+
+def test_rbf_entry_points_reject_invalid_layouts_before_device_work(lib):
+    from paper_2411_19109_gb300 import LLGError, llg_rbf_phi, llg_rbf_workspace_bytes, make_rbf
+    good = make_rbf(20, 12, 5e-9, 5e-9, (2, 14, 1, 10), 4, 3)
+    assert llg_rbf_workspace_bytes(good) == 8 * (4 * 12 * 9 + 2 * 12 + 7)
+    for bad in (make_rbf(20, 12, 5e-9, 5e-9, (2, 21, 1, 10), 4, 3),     # box beyond the grid
+                make_rbf(20, 12, 5e-9, 5e-9, (5, 5, 1, 10), 4, 3),      # empty box
+                make_rbf(20, 12, 5e-9, 5e-9, (2, 14, 1, 10), 0, 3),     # no RBFs
+                make_rbf(20, 12, 5e-9, 5e-9, (2, 14, 1, 10), 4, 3, 0.5)):  # p < 1
+        assert llg_rbf_workspace_bytes(bad) == 0
+        with pytest.raises(LLGError):
+            llg_rbf_phi(bad, 1, 1, 0, 1)
