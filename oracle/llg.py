@@ -18,6 +18,10 @@ Discretisation (node-as-cell, one cuboid V = dx dy dz per node):
   objective  J_PORT:        sum_{n >= n_from} sum_b w_b mean_{box b}(m_c,n ^ p)
              J_ENERGY_AREA: (E_d + E_ex)(m_N)/(K_d V_dom) + xi (mean psi - s_t)^2,
                             the size term of Eq. 9 on the area fraction
+             J_SPECTRAL:    sum_b w_b sum_q |X_b(f_q)|, X_b(f) = sum_{n >= n_from}
+                            P_b[n] exp(-2 pi i f n dt), P_b[n] = mean_{box b} m_c,n:
+                            Eq. 10's port spectra summed over a frequency window,
+                            evaluated at the window's frequencies f_q
   gradient   the exact derivative of this discrete map (discretise, then
              differentiate): the adjoint recursion of Eq. 6 taken through the
              four RK4 stages, and the parameter integral of Eq. 7 as the sum
@@ -37,6 +41,7 @@ MU0 = dm.MU0
 
 J_PORT = 0
 J_ENERGY_AREA = 1
+J_SPECTRAL = 2
 
 
 def psi_map(phi, a):
@@ -195,6 +200,56 @@ class Model:
             g[p.comp][b] += w * p.power * m[p.comp][b] ** (p.power - 1) / b.sum()
         return g
 
+    def port_means(self, m):
+        """(P_0, P_1): mean of m_comp over each port box (0 for an empty box)."""
+        p = self.p
+        out = []
+        for box in p.boxes:
+            b = self._box_mask(box)
+            out.append(m[p.comp][b].mean() if b.any() else 0.0)
+        return np.array(out)
+
+    def spectral_value(self, series):
+        """Eq. 10 in discrete form for the port series [n][b] of steps
+        n_from..N: sum_b w_b sum_q |sum_n P_b[n] exp(-2 pi i f_q n dt)|."""
+        p = self.p
+        n = np.arange(p.n_from, p.nsteps + 1)
+        J = 0.0
+        for b in range(2):
+            if p.weights[b] == 0.0:
+                continue
+            for f in p.freqs:
+                th = 2.0 * np.pi * f * n * p.dt
+                J += p.weights[b] * abs((series[:, b] * np.exp(-1j * th)).sum())
+        return J
+
+    def spectral_weights(self, series):
+        """dJ/dP_b[n] for the series of spectral_value ([n][b], n = n_from..N)."""
+        p = self.p
+        n = np.arange(p.n_from, p.nsteps + 1)
+        W = np.zeros_like(series)
+        for b in range(2):
+            if p.weights[b] == 0.0:
+                continue
+            for f in p.freqs:
+                th = 2.0 * np.pi * f * n * p.dt
+                xr = (series[:, b] * np.cos(th)).sum()
+                xi = -(series[:, b] * np.sin(th)).sum()
+                a = np.hypot(xr, xi)
+                if a > 0.0:
+                    W[:, b] += p.weights[b] * (xr * np.cos(th) - xi * np.sin(th)) / a
+        return W
+
+    def spectral_source(self, w):
+        """Adjoint source of one step: w_b / |box b| on m_comp over box b."""
+        p = self.p
+        g = np.zeros((3,) + self.shape)
+        for b, box in enumerate(p.boxes):
+            bm = self._box_mask(box)
+            if bm.any() and w[b] != 0.0:
+                g[p.comp][bm] += w[b] / bm.sum()
+        return g
+
     def energy_terms(self, m):
         """(E_demag, E_exchange) in joules."""
         p, psi, V = self.p, self.psi, self.V
@@ -248,6 +303,9 @@ class Model:
         m = np.array(m0, float).reshape((3,) + self.shape)
         traj = [m] if keep else None
         J = 0.0
+        if p.objective == J_SPECTRAL and p.n_from < 1:
+            raise ValueError("the spectral objective needs n_from >= 1")
+        series = []
         if p.objective == J_PORT and p.n_from <= 0:
             J += self.port_term(m)
         for n in range(p.nsteps):
@@ -256,6 +314,11 @@ class Model:
                 traj.append(m)
             if p.objective == J_PORT and n + 1 >= p.n_from:
                 J += self.port_term(m)
+            if p.objective == J_SPECTRAL and n + 1 >= p.n_from:
+                series.append(self.port_means(m))
+        if p.objective == J_SPECTRAL:
+            self.series = np.array(series).reshape(-1, 2)
+            J += self.spectral_value(self.series)
         J += self.terminal(m)
         return J, m, traj
 
@@ -318,6 +381,11 @@ class Model:
         lam, gpsi = self.terminal_grads(traj[N])
         if p.objective == J_PORT and N >= p.n_from:
             lam = lam + self.port_term_grad(traj[N])
+        if p.objective == J_SPECTRAL:
+            series = np.array([self.port_means(traj[k]) for k in range(p.n_from, N + 1)]).reshape(-1, 2)
+            SW = self.spectral_weights(series)             # row k - n_from: step k
+            if N >= p.n_from:
+                lam = lam + self.spectral_source(SW[N - p.n_from])
         for n in range(N - 1, -1, -1):
             Y, B, _ = self.stages(traj[n], n)
             u4 = dt / 6.0 * lam
@@ -332,6 +400,8 @@ class Model:
             lam = lam + g1 + g2 + g3 + g4
             if p.objective == J_PORT and n >= p.n_from:
                 lam = lam + self.port_term_grad(traj[n])
+            if p.objective == J_SPECTRAL and n >= p.n_from:
+                lam = lam + self.spectral_source(SW[n - p.n_from])
         dphi = p.sigmoid_a * self.psi * (1.0 - self.psi) * gpsi
         return dphi, lam, J
 

@@ -32,6 +32,7 @@ import numpy as np
 # objective kinds (mirrors include/llg.h)
 J_PORT = 0      # sum_{n>=n_from} sum_b w_b mean_{box b}(m_c,n ^ p)
 J_ENERGY_AREA = 1  # (E_demag + E_exchange)(m_N)/(K_d V_dom) + xi (mean psi - s_t)^2
+J_SPECTRAL = 2   # sum_b w_b sum_q |DFT of the port-mean series at f_q| (Eq. 10, windowed)
 
 Box = Tuple[int, int, int, int]  # x0, x1, y0, y1 (half open, node indices)
 
@@ -70,6 +71,7 @@ class Problem:
     n_from: int = 1           # first step index n included in the running sum
     area_target: float = 0.3
     penalty_w: float = 1.0
+    freqs: Tuple[float, ...] = ()   # J_SPECTRAL: frequencies of the windowed spectral sum (Hz)
 
     def replace(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)
