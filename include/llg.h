@@ -65,7 +65,7 @@ typedef enum {
   LLG_ESTATE = 6      /* call order violated (adjoint without forward, ...)  */
 } llg_status;
 
-enum { LLG_J_PORT = 0, LLG_J_ENERGY_AREA = 1 };
+enum { LLG_J_PORT = 0, LLG_J_ENERGY_AREA = 1, LLG_J_SPECTRAL = 2 };
 enum { LLG_FP32 = 0, LLG_FP64 = 1 };
 enum { LLG_CKPT_STORE_ALL = 0, LLG_CKPT_PERIODIC = 1, LLG_CKPT_BINOMIAL = 2 };
 
@@ -88,7 +88,7 @@ typedef struct {
   double dt;                 /* time step                                      */
   long long nsteps;          /* number of RK4 steps N                          */
   double sigmoid_a;          /* a of Eq. 4                                     */
-  int objective;             /* LLG_J_PORT or LLG_J_ENERGY_AREA                */
+  int objective;             /* LLG_J_PORT, LLG_J_ENERGY_AREA or LLG_J_SPECTRAL */
   int comp, power;           /* LLG_J_PORT: sampled component, exponent 1 or 2 */
   int boxes[2][4];           /* LLG_J_PORT: boxes x0,x1,y0,y1                   */
   double weights[2];         /* LLG_J_PORT: J = sum_{n>=n_from} sum_b w_b
@@ -98,6 +98,13 @@ typedef struct {
                                 (mu0 Ms^2/2 * V_domain) + penalty_w *
                                 (mean(psi) - area_target)^2  (Eq. 9 size term) */
   double penalty_w;
+  int nfreq;                 /* LLG_J_SPECTRAL: J = sum_b w_b sum_q |X_b(f_q)|,
+                                X_b(f) = sum_{n >= n_from} P_b[n] exp(-2 pi i f n dt),
+                                P_b[n] = mean_{box b} m_comp,n (Eq. 10: port
+                                spectra summed over a frequency window, taken
+                                at the window's frequencies); 1 <= nfreq <= 8,
+                                n_from >= 1                                  */
+  double freqs[8];           /* LLG_J_SPECTRAL: the frequencies f_q (Hz)     */
 } llg_problem;
 
 typedef struct {

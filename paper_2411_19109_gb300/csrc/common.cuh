@@ -89,6 +89,7 @@ struct DevInst {
   long long tens_off;    // offset into the tensor pool, real elements
   long long slot_off;    // offset into the objective partials: (nsteps+1) x ntile
   long long rf_off;      // offset into the RF drive table (3 nsteps + 3 values)
+  long long wt_off;      // spectral objective: offset into the per-step port weights ((nsteps+1) x 2)
   double Ms;
   double cex_x, cex_y, cex_z;   // 2A/(Ms h^2)
   double kan;                   // 2Ku/Ms

@@ -39,6 +39,26 @@ __global__ void reduce_slots_kernel(const DevInst* inst, const double* slots, lo
   }
 }
 
+// Spectral objective: port-box means P_b[n] of m_comp from the per-(step,
+// tile, box) partials, tiles added in order (block per instance).
+__global__ void port_series_kernel(const DevInst* inst, const double* pslots, long long nsteps1, double* P) {
+  const DevInst& I = inst[blockIdx.x];
+  if (I.objective != 2) return;
+  for (long long e = threadIdx.x; e < 2 * nsteps1; e += blockDim.x) {
+    const long long n = e >> 1;
+    const int b = (int)(e & 1);
+    const long long cnt = (long long)(I.boxes[b][1] - I.boxes[b][0]) * (I.boxes[b][3] - I.boxes[b][2]) * I.nz;
+    double s = 0.0;
+    for (int k = 0; k < I.ntile; ++k) s += pslots[2 * (I.slot_off + n * I.ntile + k) + b];
+    P[I.wt_off + e] = cnt > 0 ? s / (double)cnt : 0.0;
+  }
+}
+
+void launch_port_series(const DevInst* inst, int n_inst, const double* pslots, long long nsteps1, double* P,
+                        cudaStream_t st) {
+  port_series_kernel<<<n_inst, 256, 0, st>>>(inst, pslots, nsteps1, P);
+}
+
 void launch_set_step(long long* step_base, long long v, cudaStream_t st) {
   set_step_kernel<<<1, 1, 0, st>>>(step_base, v);
 }

@@ -29,6 +29,8 @@ struct RowArgs {
   T* Bout;            // recorded B_s (nullable) / field output (ROW_FIELD)
   T* ckpt;            // copy of m_{n+1} (stage 4, nullable)
   double* slots;      // objective slots (nullable: do not accumulate)
+  double* pslots;     // spectral objective: per-(step, tile, box) port partials (nullable)
+  const double* wtab; // spectral objective: per-step adjoint weights of the port boxes
   const long long* step_base;
   int* err;           // error word (bounded waits that ran out)
   const double* rf;   // per instance, per step: b_rf sin(2 pi f t) at t = n dt + c dt, c = 0, 1/2, 1
@@ -90,6 +92,7 @@ struct AdjArgs {
   int stage;          // 4..1
   int seed_only;      // 1: only form u_4, Bbar_4 of step n from lambda
   int seed_next;      // stage 1: also seed step n-1 (Yprev/Bprev of its stage 4)
+  const double* wtab; // spectral objective: per-step adjoint weights of the port boxes
   int rows_max;
   double dt;
   long long n_from;
@@ -146,6 +149,8 @@ template <typename T>
 void launch_levelset_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, T* phi, const T* grad,
                            const unsigned char* mask, double lr, unsigned int* maxbits, cudaStream_t st);
 void launch_set_step(long long* step_base, long long v, cudaStream_t st);
+void launch_port_series(const DevInst* inst, int n_inst, const double* pslots, long long nsteps1, double* P,
+                        cudaStream_t st);
 void launch_reduce_slots(const DevInst* inst, int n_inst, const double* slots, long long nslots,
                          const double* jterm, const double* psitile, double* J, cudaStream_t st);
 int rows_threads();

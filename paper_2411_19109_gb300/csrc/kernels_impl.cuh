@@ -482,6 +482,12 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
         qp += (T)(2.0 * I.penalty_w * (meanpsi - I.area_target) / (double)nodes);
 #pragma unroll
         for (int c = 0; c < 3; ++c) lam[c] = -V * Ms * pi * (Bd[c] + Bex[c]) * sc;
+      } else if (I.objective == 2) {
+        if (a.nsteps >= a.n_from) {
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+            if (in_box(I.boxes[b], x, y)) lam[I.comp] += (T)a.wtab[I.wt_off + 2 * a.nsteps + b];
+        }
       } else if (a.nsteps >= a.n_from) {
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
@@ -601,6 +607,9 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
   const int cs = (RM + 2) * nx;                            // component stride of the staged halo
   double vsum = 0.0;
   const bool objective_step = s == 4 && a.slots != nullptr && I.objective == 0 && (n + 1) >= a.n_from;
+  // spectral objective: the port-box sums of m_comp at step n + 1
+  const bool spectral_step = s == 4 && a.pslots != nullptr && I.objective == 2 && (n + 1) >= a.n_from;
+  double psum[2] = {0.0, 0.0};
 #pragma unroll 1
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
     const long long n0 = zoff + (long long)y * nx + x;
@@ -683,6 +692,11 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
         vsum += I.wbox[b] * (double)(I.power == 2 ? vv * vv : vv);
       }
     }
+    if (spectral_step) {
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+        if (in_box(I.boxes[b], x, y)) psum[b] += (double)yn[I.comp];
+    }
   }
   if (objective_step) {
     bool touches = false;
@@ -691,6 +705,15 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
     if (touches) {
       const double tot = block_sum(vsum, red);
       if (threadIdx.x == 0) a.slots[I.slot_off + (long long)(n + 1) * I.ntile + tile.k] = tot;
+    }
+  }
+  if (spectral_step) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      if (!(I.boxes[b][2] < y0 + nr && I.boxes[b][3] > y0 && I.boxes[b][0] < I.boxes[b][1])) continue;
+      const double tot = block_sum(psum[b], red);
+      if (threadIdx.x == 0) a.pslots[2 * (I.slot_off + (long long)(n + 1) * I.ntile + tile.k) + b] = tot;
+      __syncthreads();   // red is reused by the next box
     }
   }
   __syncthreads();
@@ -960,6 +983,10 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
             const T vv = yi[I.comp];
             lam[I.comp] += K.wbox[b] * (I.power == 2 ? (T)2 * vv : (T)1);
           }
+        } else if (I.objective == 2 && n >= a.n_from) {
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+            if (in_box(I.boxes[b], x, y)) lam[I.comp] += (T)a.wtab[I.wt_off + 2 * n + b];
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) glam[off3 + c * nodes + n0] = lam[c];

@@ -210,6 +210,11 @@ struct Engine final : llg_ctx {
   // per-(step, row tile) objective partials, per-row-tile terminal and psi
   // partials, per-instance J
   double *slots = nullptr, *jterm = nullptr, *psitile = nullptr, *Jd = nullptr, *rf = nullptr;
+  // spectral objective: port partials per (step, tile, box), port series and
+  // per-step adjoint weights per (instance, step, box), host copies
+  double *pslots = nullptr, *Pd = nullptr, *wtab = nullptr;
+  bool any_spec = false;
+  std::vector<double> hP, hW, Jspec;
   long long total_slots = 0;
   long long* step_base = nullptr;
   unsigned int* maxbits = nullptr;
@@ -352,8 +357,15 @@ struct Engine final : llg_ctx {
         return fail(LLG_EINVAL, "dx, dy, dz, Ms, dt must be > 0 and A >= 0");
       if (p.nsteps < 0 || p.nsteps != N || p.n_from != n_from || p.dt != dt)
         return fail(LLG_EINVAL, "all instances must share nsteps >= 0, n_from and dt");
-      if (p.objective != LLG_J_PORT && p.objective != LLG_J_ENERGY_AREA)
+      if (p.objective != LLG_J_PORT && p.objective != LLG_J_ENERGY_AREA && p.objective != LLG_J_SPECTRAL)
         return fail(LLG_EINVAL, "unknown objective");
+      if (p.objective == LLG_J_SPECTRAL) {
+        if (p.nfreq < 1 || p.nfreq > 8 || p.n_from < 1 || p.comp < 0 || p.comp > 2)
+          return fail(LLG_EINVAL, "spectral objective needs 1 <= nfreq <= 8, n_from >= 1 and comp in 0..2");
+        for (int q = 0; q < p.nfreq; ++q)
+          if (!std::isfinite(p.freqs[q])) return fail(LLG_EINVAL, "spectral objective: frequencies must be finite");
+        any_spec = true;
+      }
       if (p.objective == LLG_J_PORT && (p.comp < 0 || p.comp > 2 || (p.power != 1 && p.power != 2)))
         return fail(LLG_EINVAL, "port objective needs comp in 0..2 and power 1 or 2");
       if (p.absorb_nodes < 0) return fail(LLG_EINVAL, "absorb_nodes must be >= 0");
@@ -431,6 +443,7 @@ struct Engine final : llg_ctx {
       d.slot_off = total_slots;
       total_slots += (long long)d.ntile * (N + 1);
       d.rf_off = (long long)i * 3 * (N + 1);
+      d.wt_off = (long long)i * 2 * (N + 1);
       d.Ms = p.Ms;
       d.cex_x = 2.0 * p.A / (p.Ms * p.dx * p.dx);
       d.cex_y = 2.0 * p.A / (p.Ms * p.dy * p.dy);
@@ -509,6 +522,8 @@ struct Engine final : llg_ctx {
               alloc(&recB, S * std::max(1LL, 4 * rec_steps)) && alloc(&ckpt, S * std::max(1LL, nckpt)) &&
               alloc(&lam, S) && alloc(&G, S) && alloc(&gpart, S) && alloc(&bb[0], S) && alloc(&bb[1], S) &&
               alloc(&psib, total_nodes) && alloc(&psic, total_nodes) && alloc(&slots, (size_t)total_slots) &&
+              alloc(&pslots, any_spec ? 2 * (size_t)total_slots : 2) && alloc(&Pd, (size_t)n * 2 * (N + 1)) &&
+              alloc(&wtab, (size_t)n * 2 * (N + 1)) &&
               alloc(&jterm, rt.size()) && alloc(&psitile, rt.size()) && alloc(&Jd, n) && alloc(&step_base, 1) &&
               alloc(&maxbits, 2 * n) && alloc(&rf, (size_t)n * 3 * (N + 1)) && alloc(&errw, 1);
     if (!ok) return fail(LLG_ENOMEM, "device allocation failed (" + std::to_string(bytes >> 20) + " MiB so far)");
@@ -590,6 +605,7 @@ struct Engine final : llg_ctx {
     cudaFree(Gs);
     if (e != cudaSuccess) return cuda_fail(e, "demag tensor");
     set_smem_limits<T>(smem_rows, smem_misc, smem_cols, smem_adj);
+    cudaMemsetAsync(wtab, 0, sizeof(double) * n * 2 * (N + 1), st);
     smem_cols3<T>(smem_c3);
     if constexpr (sizeof(T) == 4) smem_cols16<T>(smem_cols);
     cudaMemsetAsync(errw, 0, sizeof(int), st);
@@ -686,6 +702,7 @@ struct Engine final : llg_ctx {
       a.stage = s;
       a.acc = acc;
       a.slots = objective ? slots : nullptr;
+      a.pslots = objective && any_spec ? pslots : nullptr;
       if (record) {
         a.m = recY_slot(4LL * l);
         a.Yin = recY_slot(4LL * l + s - 1);
@@ -792,6 +809,53 @@ struct Engine final : llg_ctx {
     return LLG_OK;
   }
 
+  // Spectral objective (Eq. 10 at the window's frequencies): the port series
+  // P_b[n] of the finished forward come to the host; J_b = sum_q |X_b(f_q)|
+  // and the per-step adjoint weights dJ/dP_b[n] / |box b| are formed in FP64
+  // there (a few thousand numbers per instance) and go back as wtab, which
+  // the terminal and adjoint kernels read.
+  llg_status spectral_weights() {
+    const size_t len = (size_t)n * 2 * (N + 1);
+    hP.assign(len, 0.0);
+    hW.assign(len, 0.0);
+    Jspec.assign(n, 0.0);
+    launch_port_series(dI, n, pslots, N + 1, Pd, st);
+    ++nlaunch;
+    cudaError_t e = cudaMemcpyAsync(hP.data(), Pd, sizeof(double) * len, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "spectral objective: port series");
+    for (int i = 0; i < n; ++i) {
+      const llg_problem& p = P[i];
+      if (p.objective != LLG_J_SPECTRAL) continue;
+      const double* Pi = hP.data() + (size_t)i * 2 * (N + 1);
+      double* Wi = hW.data() + (size_t)i * 2 * (N + 1);
+      for (int b = 0; b < 2; ++b) {
+        const DevInst& d = H[i];
+        const long long cnt = (long long)(d.boxes[b][1] - d.boxes[b][0]) * (d.boxes[b][3] - d.boxes[b][2]) * d.nz;
+        if (p.weights[b] == 0.0 || cnt <= 0) continue;
+        for (int q = 0; q < p.nfreq; ++q) {
+          double xr = 0.0, xi = 0.0;
+          for (long long k = n_from; k <= N; ++k) {
+            const double th = 2.0 * M_PI * p.freqs[q] * (double)k * dt;
+            xr += Pi[2 * k + b] * std::cos(th);
+            xi -= Pi[2 * k + b] * std::sin(th);
+          }
+          const double amp = std::hypot(xr, xi);
+          Jspec[i] += p.weights[b] * amp;
+          if (!(amp > 0.0)) continue;
+          for (long long k = n_from; k <= N; ++k) {
+            const double th = 2.0 * M_PI * p.freqs[q] * (double)k * dt;
+            Wi[2 * k + b] += p.weights[b] * (xr * std::cos(th) - xi * std::sin(th)) / amp / (double)cnt;
+          }
+        }
+      }
+    }
+    e = cudaMemcpyAsync(wtab, hW.data(), sizeof(double) * len, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "spectral objective: weights");
+    return LLG_OK;
+  }
+
   // ------------------------------------------------------------ forward
   llg_status forward(const void* phi_v, const void* m0_v, double* J, void* mT) override {
     if (!phi_v || !m0_v || !J) return fail(LLG_EINVAL, "phi, m0 and J must not be NULL");
@@ -801,6 +865,7 @@ struct Engine final : llg_ctx {
     cudaMemcpyAsync(m, m0_v, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
     cudaMemsetAsync(slots, 0, sizeof(double) * total_slots, st);
     cudaMemsetAsync(jterm, 0, sizeof(double) * rt.size(), st);
+    if (any_spec) cudaMemsetAsync(pslots, 0, sizeof(double) * 2 * total_slots, st);
     fft_only(m);
     const T* cur = m;
     for (const Action& ac : fwd) {
@@ -818,6 +883,8 @@ struct Engine final : llg_ctx {
       }
     }
     mN_ptr = cur;
+    if (any_spec)
+      if (llg_status s = spectral_weights()) return s;
     // terminal: field of m_N, energies, lambda_N, explicit dJ/dpsi
     cols();
     {
@@ -828,6 +895,7 @@ struct Engine final : llg_ctx {
       a.psic = psic;
       a.jterm = jterm;
       a.psitile = psitile;
+      a.wtab = wtab;
       rows(a, ROW_TERMINAL);
     }
     launch_reduce_slots(dI, n, slots, N + 1, jterm, psitile, Jd, st);
@@ -846,6 +914,8 @@ struct Engine final : llg_ctx {
     cudaEventElapsedTime(&f, ev0, ev1);
     ms = f;
     have_fwd = true;
+    if (any_spec)
+      for (int i = 0; i < n; ++i) J[i] += Jspec[i];
     for (int i = 0; i < n; ++i)
       if (!std::isfinite(J[i])) return fail(LLG_ENONFINITE, "J is not finite for instance " + std::to_string(i));
     return LLG_OK;
@@ -870,6 +940,7 @@ struct Engine final : llg_ctx {
     a.rows_max = R;
     a.dt = dt;
     a.n_from = n_from;
+    a.wtab = wtab;
     return a;
   }
   void adj(const AdjArgs<T>& a0) {

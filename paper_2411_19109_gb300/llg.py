@@ -21,7 +21,7 @@ from . import build as _build
 c_int, c_double, c_ll, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p
 
 LLG_OK, LLG_EINVAL, LLG_ENOMEM, LLG_ECUDA, LLG_ETIMEOUT, LLG_ENONFINITE, LLG_ESTATE = range(7)
-LLG_J_PORT, LLG_J_ENERGY_AREA = 0, 1
+LLG_J_PORT, LLG_J_ENERGY_AREA, LLG_J_SPECTRAL = 0, 1, 2
 LLG_FP32, LLG_FP64 = 0, 1
 LLG_CKPT_STORE_ALL, LLG_CKPT_PERIODIC, LLG_CKPT_BINOMIAL = 0, 1, 2
 
@@ -48,7 +48,7 @@ class llg_problem(ctypes.Structure):
                 ("dt", c_double), ("nsteps", c_ll), ("sigmoid_a", c_double),
                 ("objective", c_int), ("comp", c_int), ("power", c_int),
                 ("boxes", (c_int * 4) * 2), ("weights", c_double * 2), ("n_from", c_ll),
-                ("area_target", c_double), ("penalty_w", c_double)]
+                ("area_target", c_double), ("penalty_w", c_double), ("nfreq", c_int), ("freqs", c_double * 8)]
 
 
 class llg_options(ctypes.Structure):
@@ -136,6 +136,9 @@ def to_struct(p) -> llg_problem:
     s.weights[:] = list(p.weights)
     s.n_from = p.n_from
     s.area_target, s.penalty_w = p.area_target, p.penalty_w
+    fq = list(getattr(p, "freqs", ()))
+    s.nfreq = len(fq)
+    s.freqs[:min(len(fq), 8)] = fq[:8]
     return s
 
 

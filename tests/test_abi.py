@@ -91,3 +91,42 @@ def test_rbf_entry_points_reject_invalid_layouts_before_device_work(lib):
         assert llg_rbf_workspace_bytes(bad) == 0
         with pytest.raises(LLGError):
             llg_rbf_phi(bad, 1, 1, 0, 1)
+
+
+def test_binding_structs_have_the_c_layout(tmp_path):
+    """Size and every field offset of the ctypes structs equal the C
+    compiler's for include/llg.h (the spectral fields sit after penalty_w)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2411_19109_gb300 import llg as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [("llg_problem", B.llg_problem), ("llg_options", B.llg_options), ("llg_rbf", B.llg_rbf)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "llg.h"', "int main(void) {"]
+    expect = []
+    for cname, py in structs:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        expect.append(ctypes.sizeof(py))
+        for f in py._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f[0]}));')
+            expect.append(getattr(py, f[0]).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
+
+
+def test_spectral_fields_reach_the_struct():
+    from paper_2411_19109_gb300 import llg as B
+    import workloads as W
+    p = W.random_small(8, 4, 1, objective=W.J_SPECTRAL, freqs=(8e9, 9e9), n_from=3).problem
+    s = B.to_struct(p)
+    assert (s.objective, s.nfreq, s.n_from) == (2, 2, 3)
+    assert list(s.freqs[:2]) == [8e9, 9e9] and list(s.freqs[2:]) == [0.0] * 6
+    s9 = B.to_struct(p.replace(freqs=tuple(range(1, 10))))
+    assert s9.nfreq == 9 and list(s9.freqs) == list(range(1, 9))   # the library rejects nfreq > 8
