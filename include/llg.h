@@ -200,6 +200,16 @@ void llg_destroy(llg_ctx* ctx);
 llg_status llg_field_noalloc(const llg_problem* prob, const void* phi_dev, const void* m_dev, double t,
                              int demag_only, void* B_dev, void* cuda_stream, const char** err_msg);
 
+/* FP64 fused multiply-add throughput of the current device (TFLOP/s), the
+ * denominator of the FP64 path's arithmetic roofline.  There is no
+ * counterpart in the paper: it is a measurement helper.  Runs 6 launches of
+ * an FMA-chain kernel (8 chains x `iters` iterations per thread, 8 blocks of
+ * 256 threads per SM) on cuda_stream and synchronises; the best of the last
+ * four gives *tflops (and its duration in *ms, if non-NULL).  Allocates and
+ * frees a small output buffer.  LLG_EINVAL for iters < 1 or tflops NULL,
+ * LLG_ENOMEM / LLG_ECUDA on CUDA failures. */
+llg_status llg_fp64_fma_rate(int iters, double* tflops, double* ms, void* cuda_stream);
+
 /* ------------------------------------------------------------------------
  * RBF parameterisation of the level-set function and the optimiser step.
  * Phi on a rectangular design box is built from nrx*nry multiquadric cones

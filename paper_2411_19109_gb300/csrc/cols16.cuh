@@ -7,6 +7,22 @@
 //   with the 2D tensor (xx, yy, zz, xy; packed DC/Nyquist column separated
 //   by Hermitian symmetry) -> inverse FFT_y -> store rows < ny.
 // The tensor records of the tile go to shared memory by bulk copy at entry.
+//
+// Shared-memory layout: element i of group g sits at base(g) + pad(i).  An
+// access wavefront serves 16 lanes of 8 bytes, one per bank pair, so every
+// access pattern of the kernel -- natural order t + TT*s, the strided writes
+// of each radix pass, the row copies to and from global memory -- must reach
+// 16 distinct bank pairs (address mod 16 in complex slots) per half-warp:
+//   L = 128 (two groups per half-warp): one pad slot per 8, group stride
+//     152 = 8 mod 16 (the two groups of a half-warp fall in opposite halves),
+//     plus 2 ((g/2) mod 4) + (g/8) mod 2 so that the row copies, where a
+//     half-warp spans 16 groups or parts of two rows, stay distinct;
+//   L = 256 (one group per half-warp): one pad slot per 16 (natural order and
+//     the radix-16 writes 16 t + r both spread over all pairs), group offsets
+//     4 (g mod 4) - g/4 mod 16 for the row copies (12 groups per row);
+//   L = 1024: one pad slot per 16, stride 1099.
+// The length-agnostic padding of the 8-element kernels (one slot per 8, odd
+// group stride) left most accesses here two-way conflicted.
 #pragma once
 
 #include "kernels_impl.cuh"
@@ -15,14 +31,32 @@ namespace llg {
 
 constexpr int kCol16Threads = 192;
 
+template <int L>
+struct Col16Map {
+  static constexpr int GS = L == 128 ? 152 : L == 256 ? 288 : 1099;   // group stride
+  static constexpr int PL = L == 128 ? L + L / 8 : L + L / 16;          // padded length
+  __device__ __forceinline__ static int base(int g) {
+    return L == 128 ? g * GS + 2 * ((g >> 1) & 3) + ((g >> 3) & 1)
+         : L == 256 ? g * GS + ((4 * (g & 3) - (g >> 2)) & 15)
+                    : g * GS;
+  }
+  __host__ __device__ __forceinline__ constexpr int operator()(int i) const {
+    return L == 128 ? i + (i >> 3) : i + (i >> 4);
+  }
+};
+
 template <typename T, int L>
 __device__ __forceinline__ void cols16_body(const ColArgs<T>& a, const DevInst& I, const ColTile& tile,
                                             cplx<T>* smem, uint64_t* bar) {
   using C = cplx<T>;
   constexpr int TT = L / 16;
   constexpr int NC = 1024 / L;                     // columns per block
-  constexpr int GSC = rf_padded_len(L) + 1;        // group stride
+  using Map = Col16Map<L>;
+  constexpr int GSC = Map::GS;
   static_assert(3 * NC * TT == kCol16Threads, "one group per (component, column)");
+  static_assert(3 * NC * GSC + L / 16 <= kExch, "groups and the W^4k table fit the exchange area");
+  static_assert(Map::PL + (L == 128 ? 7 : L == 256 ? 15 : 0) <= GSC,
+                "a group's padded sequence and its offset fit the stride");
   const int tid = threadIdx.x;
   const int t = tid % TT, grp_id = tid / TT;       // group = (component, column)
   const int c = grp_id / NC, col = grp_id % NC;
@@ -30,8 +64,10 @@ __device__ __forceinline__ void cols16_body(const ColArgs<T>& a, const DevInst& 
   const bool active = col < ncols;
   const int kx = tile.kx0 + (active ? col : 0);
   const int Lx = I.Lx, ny = I.ny;
-  C* grp = smem + grp_id * GSC;
+  C* grp = smem + Map::base(grp_id);
+  const Map map;
   C* tw1 = smem + kExch;
+  C* tw4 = smem + 3 * NC * GSC;                    // W_L^{4k}, k < L/16
   C* spec = a.spec + I.spec_off + tile.kx0;
   const GroupSync gs = group_sync(TT);
   constexpr int nky = L / 2 + 1;
@@ -47,10 +83,11 @@ __device__ __forceinline__ void cols16_body(const ColArgs<T>& a, const DevInst& 
     if (nb) bulk_load(stab + NC * nky * 4, tab + (long long)Lx * nky * 4, nb, bar);
   }
   load_twiddles(tw1, a.tw, L);
+  for (int k = tid; k < L / 16; k += kCol16Threads) tw4[k] = a.tw[k * 4 * (kTwiddleN / L)];
   for (int e = tid; e < ny * 3 * NC; e += kCol16Threads) {
     const int y = e / (3 * NC), r = e - y * (3 * NC);
     const int cc = r / NC, cl = r % NC;
-    if (cl < ncols) smem[(cc * NC + cl) * GSC + rf_pad(y)] = spec[((long long)y * 3 + cc) * Lx + cl];
+    if (cl < ncols) smem[Map::base(cc * NC + cl) + map(y)] = spec[((long long)y * 3 + cc) * Lx + cl];
   }
   __syncthreads();
   C v[16];
@@ -58,12 +95,12 @@ __device__ __forceinline__ void cols16_body(const ColArgs<T>& a, const DevInst& 
   for (int s = 0; s < 16; ++s) {
     const int y = t + TT * s;
     // rows y >= ny <= L/2 are the zero padding: s >= 8 is zero at compile time
-    v[s] = (s < 8 && active && y < ny) ? grp[rf_pad(y)] : mk<C>((T)0, (T)0);
+    v[s] = (s < 8 && active && y < ny) ? grp[map(y)] : mk<C>((T)0, (T)0);
   }
   gs();
-  regfft16<C, L, -1>(v, grp, t, tw1, 1, gs);
+  regfft16<C, L, -1>(v, grp, t, tw1, 1, tw4, map, gs);
 #pragma unroll
-  for (int s = 0; s < 16; ++s) grp[rf_pad(t + TT * s)] = v[s];
+  for (int s = 0; s < 16; ++s) grp[map(t + TT * s)] = v[s];
   __syncthreads();
   mbar_wait(bar, 0, a.err);
   const int cl = active ? col : 0;
@@ -79,7 +116,8 @@ __device__ __forceinline__ void cols16_body(const ColArgs<T>& a, const DevInst& 
       if (c == 2) {
         v[s] = cscale(v[s], n[2]);
       } else {
-        const C other = smem[((1 - c) * NC + col) * GSC + rf_pad(ky)];   // the other in-plane component
+        const int go = (1 - c) * NC + col;                              // the other in-plane component
+        const C other = smem[Map::base(go) + map(ky)];
         const T diag = (c == 0) ? n[0] : n[1];
         v[s] = mk<C>(diag * v[s].x + nxy * other.x, diag * v[s].y + nxy * other.y);
       }
@@ -89,22 +127,22 @@ __device__ __forceinline__ void cols16_body(const ColArgs<T>& a, const DevInst& 
       load_tensor_smem(stab, NC * nky + kyf, nq);
       const int km = (L - ky) & (L - 1);
       const T p = (T)0.5 * (nd[c] + nq[c]), q = (T)0.5 * (nd[c] - nq[c]);
-      const C vb = cconj(grp[rf_pad(km)]);
+      const C vb = cconj(grp[map(km)]);
       v[s] = cadd(cscale(v[s], p), cscale(vb, q));
     }
   }
   __syncthreads();
-  regfft16<C, L, 1>(v, grp, t, tw1, 1, gs);
+  regfft16<C, L, 1>(v, grp, t, tw1, 1, tw4, map, gs);
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
     const int y = t + TT * s;
-    if (s < 8 && y < ny) grp[rf_pad(y)] = v[s];   // only rows y < ny <= L/2 go back
+    if (s < 8 && y < ny) grp[map(y)] = v[s];   // only rows y < ny <= L/2 go back
   }
   __syncthreads();
   for (int e = tid; e < ny * 3 * NC; e += kCol16Threads) {
     const int y = e / (3 * NC), r = e - y * (3 * NC);
     const int cc = r / NC, cl = r % NC;
-    if (cl < ncols) spec[((long long)y * 3 + cc) * Lx + cl] = smem[(cc * NC + cl) * GSC + rf_pad(y)];
+    if (cl < ncols) spec[((long long)y * 3 + cc) * Lx + cl] = smem[Map::base(cc * NC + cl) + map(y)];
   }
 }
 

@@ -275,7 +275,8 @@ __device__ __forceinline__ void rf_dft16(C x[16]) {
 // One Stockham pass of radix RP on the sixteen registers of thread t
 // (butterfly b: j = t + TT*b, inputs v[b + r*(16/RP)]).
 template <typename C, int L, int RP, int DIR>
-__device__ __forceinline__ void rf_pass16(C v[16], int t, int Ns, const C* __restrict__ tw, int tws, int dst[16]) {
+__device__ __forceinline__ void rf_pass16(C v[16], int t, int Ns, const C* __restrict__ tw, int tws,
+                                          const C* __restrict__ tw4, int dst[16]) {
   constexpr int TT = L / 16;
   constexpr int NB = 16 / RP;
 #pragma unroll
@@ -289,11 +290,12 @@ __device__ __forceinline__ void rf_pass16(C v[16], int t, int Ns, const C* __res
     if (Ns > 1) {
       using R = decltype(C::x);
       if constexpr (sizeof(R) == 4 && RP == 16) {
-        // FP32: W^step and W^{4 step} loaded, the other powers by products
-        // at most three roundings deep
+        // FP32: W^step and W^{4 step} loaded (the latter from its own
+        // contiguous table when given: tw4[k] = W^{4k}, k < L/16), the other
+        // powers by products at most three roundings deep
         C w[16];
         w[1] = rf_tw<C, DIR>(tw, step, tws);
-        w[4] = rf_tw<C, DIR>(tw, 4 * step, tws);
+        w[4] = tw4 ? rf_tw<C, DIR>(tw4, step, 1) : rf_tw<C, DIR>(tw, 4 * step, tws);
         w[2] = cmul(w[1], w[1]);
         w[3] = cmul(w[2], w[1]);
         w[5] = cmul(w[4], w[1]);
@@ -333,10 +335,12 @@ __device__ __forceinline__ void rf_pass16(C v[16], int t, int Ns, const C* __res
 }
 
 // Full transform of one sequence held 16 elements per thread; element i is
-// exchanged through sm[pad(i)].  First pass radix 2^(log2 L mod 4) (16 when
-// that is 0), then radix-16 passes.
-template <typename C, int L, int DIR>
-__device__ __forceinline__ void regfft16(C (&v)[16], C* sm, int t, const C* __restrict__ tw, int tws, GroupSync sync) {
+// exchanged through sm[map(i)] (map: a permutation of [0, L) into the
+// group's shared-memory slots).  First pass radix 2^(log2 L mod 4) (16 when
+// that is 0), then radix-16 passes.  tw4: optional table of W_L^{4k}.
+template <typename C, int L, int DIR, typename Map>
+__device__ __forceinline__ void regfft16(C (&v)[16], C* sm, int t, const C* __restrict__ tw, int tws,
+                                         const C* __restrict__ tw4, const Map& map, GroupSync sync) {
   constexpr int M = (L == 16) ? 4 : (L == 32) ? 5 : (L == 64) ? 6 : (L == 128) ? 7 : (L == 256) ? 8
                   : (L == 512) ? 9 : (L == 1024) ? 10 : 11;
   static_assert((1 << M) == L, "L must be a power of two in [16, 2048]");
@@ -349,17 +353,17 @@ __device__ __forceinline__ void regfft16(C (&v)[16], C* sm, int t, const C* __re
   for (int p = 0; p < NPASS; ++p) {
     if (p > 0) {
 #pragma unroll
-      for (int s = 0; s < 16; ++s) sm[rf_pad(dst[s])] = v[s];
+      for (int s = 0; s < 16; ++s) sm[map(dst[s])] = v[s];
       sync();
 #pragma unroll
-      for (int s = 0; s < 16; ++s) v[s] = sm[rf_pad(t + TT * s)];
+      for (int s = 0; s < 16; ++s) v[s] = sm[map(t + TT * s)];
       sync();
     }
     if (p == 0) {
-      rf_pass16<C, L, R0, DIR>(v, t, Ns, tw, tws, dst);
+      rf_pass16<C, L, R0, DIR>(v, t, Ns, tw, tws, tw4, dst);
       Ns *= R0;
     } else {
-      rf_pass16<C, L, 16, DIR>(v, t, Ns, tw, tws, dst);
+      rf_pass16<C, L, 16, DIR>(v, t, Ns, tw, tws, tw4, dst);
       Ns *= 16;
     }
   }

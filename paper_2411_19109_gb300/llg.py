@@ -28,7 +28,7 @@ LLG_CKPT_STORE_ALL, LLG_CKPT_PERIODIC, LLG_CKPT_BINOMIAL = 0, 1, 2
 EXPORTED = ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query",
             "llg_launch_count", "llg_kernel_time", "llg_last_error", "llg_destroy", "llg_schedule",
             "llg_padded_extents", "llg_abi_version", "llg_field_noalloc", "llg_rbf_workspace_bytes",
-            "llg_rbf_phi", "llg_rbf_grad", "llg_adam_step")
+            "llg_rbf_phi", "llg_rbf_grad", "llg_adam_step", "llg_fp64_fma_rate")
 
 
 class llg_rbf(ctypes.Structure):
@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.llg_adam_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_ll, c_double, c_double, c_double,
                                   c_double, c_void_p]
     lib.llg_adam_step.restype = c_int
+    lib.llg_fp64_fma_rate.argtypes = [c_int, P(c_double), P(c_double), c_void_p]
+    lib.llg_fp64_fma_rate.restype = c_int
     for f in ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query"):
         getattr(lib, f).restype = c_int
     _lib = lib
@@ -234,6 +236,15 @@ def llg_adam_step(s_ptr: int, grad_ptr: int, m_ptr: int, v_ptr: int, n: int, t: 
     """One Adam step on n double parameters (step number t >= 1)."""
     _rbf_check(load().llg_adam_step(c_void_p(s_ptr), c_void_p(grad_ptr), c_void_p(m_ptr), c_void_p(v_ptr), n, t,
                                     lr, b1, b2, eps, c_void_p(stream)), "llg_adam_step")
+
+
+def llg_fp64_fma_rate(iters: int = 16384, stream: int = 0):
+    """Measured FP64 FMA throughput of the current device: (TFLOP/s, ms of
+    the best launch)."""
+    tf, ms = c_double(), c_double()
+    _rbf_check(load().llg_fp64_fma_rate(iters, ctypes.byref(tf), ctypes.byref(ms), c_void_p(stream)),
+               "llg_fp64_fma_rate")
+    return tf.value, ms.value
 
 
 def llg_query(ctx: int):

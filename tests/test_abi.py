@@ -130,3 +130,23 @@ def test_spectral_fields_reach_the_struct():
     assert list(s.freqs[:2]) == [8e9, 9e9] and list(s.freqs[2:]) == [0.0] * 6
     s9 = B.to_struct(p.replace(freqs=tuple(range(1, 10))))
     assert s9.nfreq == 9 and list(s9.freqs) == list(range(1, 9))   # the library rejects nfreq > 8
+
+
+def test_bench_fft_flop_model_and_reference_arm_line():
+    """bench.py's host-side pieces: the FFT flop model of the FP64 roofline
+    (5 N log2 N per complex transform) and the reference arm's JSON line,
+    run on this host's cores on a short sample."""
+    import json
+    import subprocess
+    import sys
+    import bench
+    import workloads as W
+    inst = W.random_small(8, 4, 1)                   # Px = 16 -> 8-point rows; Py = 8
+    assert bench.fft_flops([inst], 1) == 8 * 6 * 5 * 8 * 3
+    assert bench.fft_flops([inst], 0) == 4 * 6 * 5 * 8 * 3
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, check=True, timeout=600).stdout
+    line = json.loads(out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "node-steps/s"
+    assert line["cpu_baseline"]["cores"] >= 1 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
