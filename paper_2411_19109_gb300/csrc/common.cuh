@@ -19,6 +19,13 @@ constexpr int kMaxNz = 8;                            // layers of a 3D grid (pad
 // eight elements spreads strided accesses over the banks.
 __host__ __device__ constexpr int rf_pad(int i) { return i + (i >> 3); }
 __host__ __device__ constexpr int rf_padded_len(int L) { return L + (L >> 3); }
+// Padding of the row-family sequences and of every register FFT's internal
+// exchanges: one slot per 16 once a sequence's L/8 lanes fill whole
+// half-warps (L >= 128), so that natural-order accesses by 16 consecutive
+// lanes (8-byte elements, 16 bank pairs per wavefront) and the radix-2/4
+// pass writes meet no bank twice; one per 8 below that.
+__host__ __device__ constexpr int row_pad(int L, int i) { return L >= 128 ? i + (i >> 4) : i + (i >> 3); }
+__host__ __device__ constexpr int row_padded_len(int L) { return L >= 128 ? L + (L >> 4) : L + (L >> 3); }
 
 // Padded z length of the demag convolution: 1 for a film, else the power of
 // two >= 2 nz (any length >= 2 nz - 1 gives the same linear convolution).

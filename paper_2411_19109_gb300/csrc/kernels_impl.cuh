@@ -136,7 +136,7 @@ __device__ __forceinline__ void fft1(C (&v)[8], C* grp, int estride, int t, cons
 
 // Row-kernel group stride: the padded length rounded up to even, so that
 // every (row slot, component) sequence starts on a 16-byte boundary.
-__host__ __device__ constexpr int group_stride(int L) { return (rf_padded_len(L) + 1) & ~1; }
+__host__ __device__ constexpr int group_stride(int L) { return (row_padded_len(L) + 1) & ~1; }
 
 // ---------------------------------------------------------------------------
 // Thread layout of the row-family kernels (stage, spectrum/field/terminal,
@@ -162,7 +162,7 @@ __device__ __forceinline__ void row_inverse_comp(cplx<T> (&v)[8], const cplx<T>*
   gs();
   fft1<C, L, 1>(v, grp, 1, t, tw2, 2, gs);
 #pragma unroll
-  for (int s = 0; s < 4; ++s) grp[rf_pad(t + TT * s)] = v[s];
+  for (int s = 0; s < 4; ++s) grp[row_pad(L, t + TT * s)] = v[s];
 }
 
 // Forward FFT of the node-phase output left in grp (slots j < npairs), packed
@@ -177,26 +177,26 @@ __device__ __forceinline__ void row_forward_comp(cplx<T>* grp, int npairs, cplx<
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int j = t + TT * s;
-    v[s] = (s < 4 && j < npairs) ? grp[rf_pad(j)] : mk<C>((T)0, (T)0);
+    v[s] = (s < 4 && j < npairs) ? grp[row_pad(L, j)] : mk<C>((T)0, (T)0);
   }
   gs();
   fft1<C, L, -1>(v, grp, 1, t, tw2, 2, gs);
 #pragma unroll
-  for (int s = 0; s < 8; ++s) grp[rf_pad(t + TT * s)] = v[s];
+  for (int s = 0; s < 8; ++s) grp[row_pad(L, t + TT * s)] = v[s];
   gs();
   if (!active) return;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int kk = t + TT * s;
-    const C zm = cconj(grp[rf_pad((L - kk) & (L - 1))]);
+    const C zm = cconj(grp[row_pad(L, (L - kk) & (L - 1))]);
     out[kk] = pack_one(v[s], zm, kk, tw2);
   }
 }
 
 // Node x of a row slot's three sequences: complex slot x/2, real (x even) or
 // imaginary (x odd) part.
-template <typename T>
-__device__ __forceinline__ int node_slot(int x) { return 2 * rf_pad(x >> 1) + (x & 1); }
+template <typename T, int L>
+__device__ __forceinline__ int node_slot(int x) { return 2 * row_pad(L, x >> 1) + (x & 1); }
 
 // ---------------------------------------------------------------------------
 // column pass: FFT_y, product with the tensor spectrum, inverse FFT_y.
@@ -370,7 +370,7 @@ __device__ __forceinline__ unsigned stage_halo(T* sF, int RM, const T* F, long l
 template <int L>
 struct RowGeom {
   static constexpr int TT = L / 8;
-  static constexpr int SP = rf_padded_len(L);
+  static constexpr int SP = row_padded_len(L);
   static constexpr int RM = rows_per_tile(L);
   int rl, c, t, tr;
   __device__ __forceinline__ RowGeom(int tid) {
@@ -422,7 +422,7 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
 #pragma unroll 1
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
     const long long n0 = zoff + (long long)y * nx + x;
-    const int sl = node_slot<T>(x);
+    const int sl = node_slot<T, L>(x);
     if (MODE == ROW_FFT_ONLY) {
       const T p = ps[n0];
 #pragma unroll
@@ -613,7 +613,7 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
 #pragma unroll 1
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
     const long long n0 = zoff + (long long)y * nx + x;
-    const int sl = node_slot<T>(x);
+    const int sl = node_slot<T, L>(x);
     const int oi = (g.rl + 1) * nx + x;
     // m_n and the RK accumulator of this node first (their latencies overlap
     // the field assembly below)
@@ -876,7 +876,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
 #pragma unroll 1
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
     const long long n0 = zoff + (long long)y * nx + x;
-    const int sl = node_slot<T>(x);
+    const int sl = node_slot<T, L>(x);
     // every pointwise value of this node first, so that the load latencies
     // overlap (these arrays are disjoint from the ones this loop writes)
     T lam[3], gg[3], gsum[3], yp[3], bp[3];

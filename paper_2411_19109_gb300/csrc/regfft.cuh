@@ -188,12 +188,12 @@ __device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int
 #pragma unroll
       for (int c = 0; c < NCOMP; ++c)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) sm[(c * sstride + rf_pad(dst[s])) * estride] = v[c][s];
+        for (int s = 0; s < 8; ++s) sm[(c * sstride + row_pad(L, dst[s])) * estride] = v[c][s];
       sync();
 #pragma unroll
       for (int c = 0; c < NCOMP; ++c)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) v[c][s] = sm[(c * sstride + rf_pad(t + TT * s)) * estride];
+        for (int s = 0; s < 8; ++s) v[c][s] = sm[(c * sstride + row_pad(L, t + TT * s)) * estride];
       sync();
     }
     if (p == 0 && R0 == 2) {
