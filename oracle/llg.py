@@ -9,7 +9,8 @@ Discretisation (node-as-cell, one cuboid V = dx dy dz per node):
              B_ex,i = -(1/(Ms_i V)) dE_ex/dm_i
                     = (2A/Ms) sum_j w_ij (m_j - m_i)/h^2,  w_ij = 2 psi_j/(psi_i + psi_j)
   anisotropy B_an = (2 Ku/Ms)(m.u) u   (Ku scaled by psi like Ms, so psi cancels)
-  Zeeman     B_z = B_bias + b_rf sin(2 pi f t) e_rf on the source box
+  Zeeman     B_z = B_bias + b(t) e_rf on the source box, b(t) = b_rf sin(2 pi f t)
+             or a tabulated drive b(n dt + c dt), c = 0, 1/2, 1, per step n
   demag      B_d = -mu0 N * (Ms psi m)   (oracle.demag)
   dynamics   LL form of Eq. 11: f(m) = -gamma/(1+alpha^2) [m x B + alpha m x (m x B)]
              alpha_i ramps linearly from alpha_edge at an absorbing edge to
@@ -22,6 +23,11 @@ Discretisation (node-as-cell, one cuboid V = dx dy dz per node):
                             P_b[n] exp(-2 pi i f n dt), P_b[n] = mean_{box b} m_c,n:
                             Eq. 10's port spectra summed over a frequency window,
                             evaluated at the window's frequencies f_q
+             J_CURVE:       sum_j w_j |P(m_{n_j}) - T_j| with P = sum psi m_c / sum psi,
+                            the magnetisation curve of Eq. 8 sampled at the end of
+                            each field level, + xi (mean psi - s_t)^2 + nu (|x_c - x_0|
+                            + |y_c - y_0|), the size and centre terms of Eq. 9
+                            (centre = psi-weighted mean node index)
   gradient   the exact derivative of this discrete map (discretise, then
              differentiate): the adjoint recursion of Eq. 6 taken through the
              four RK4 stages, and the parameter integral of Eq. 7 as the sum
@@ -42,6 +48,7 @@ MU0 = dm.MU0
 J_PORT = 0
 J_ENERGY_AREA = 1
 J_SPECTRAL = 2
+J_CURVE = 3
 
 
 def psi_map(phi, a):
@@ -131,19 +138,28 @@ class Model:
         u = self.ku.reshape(3, 1, 1, 1)
         return (2.0 * self.p.Ku / self.p.Ms) * dot(m, u) * u
 
-    def zeeman(self, t):
+    def drive(self, n, ci):
+        """b at t = n dt + (ci/2) dt: the tabulated drive, else the sine."""
+        p = self.p
+        if p.drive is not None:
+            return p.drive[3 * n + ci]
+        if p.b_rf == 0.0:
+            return 0.0
+        return p.b_rf * np.sin(2.0 * np.pi * p.f_rf * (n * p.dt + 0.5 * ci * p.dt))
+
+    def zeeman(self, n, ci):
         p = self.p
         B = np.zeros((3,) + self.shape)
         for c in range(3):
             B[c] += p.B_bias[c]
-        if p.b_rf != 0.0:
-            s = p.b_rf * np.sin(2.0 * np.pi * p.f_rf * t)
+        s = self.drive(n, ci)
+        if s != 0.0:
             for c in range(3):
                 B[c][self.src] += s * p.rf_dir[c]
         return B
 
-    def field(self, m, t):
-        return self.exchange(m) + self.demag(m) + self.anisotropy(m) + self.zeeman(t)
+    def field(self, m, n, ci):
+        return self.exchange(m) + self.demag(m) + self.anisotropy(m) + self.zeeman(n, ci)
 
     def rhs(self, m, B):
         a = self.alpha
@@ -155,11 +171,10 @@ class Model:
     def stages(self, m, n):
         """RK4 stage inputs Y_s, fields B_s and slopes k_s for step n."""
         dt = self.p.dt
-        t = n * dt
         Y, B, K = [], [], []
         y = m
-        for s, (c_t, c_next) in enumerate(((0.0, 0.5), (0.5, 0.5), (0.5, 1.0), (1.0, None))):
-            b = self.field(y, t + c_t * dt)
+        for s, (ci, c_next) in enumerate(((0, 0.5), (1, 0.5), (1, 1.0), (2, None))):
+            b = self.field(y, n, ci)
             k = self.rhs(y, b)
             Y.append(y)
             B.append(b)
@@ -250,6 +265,56 @@ class Model:
                 g[p.comp][bm] += w[b] / bm.sum()
         return g
 
+    def curve_point(self, m):
+        """P = sum psi m_c / sum psi, the particle's mean magnetisation
+        component (M_c / Ms) in Eq. 8."""
+        psi = self.psi
+        return float((psi * m[self.p.comp]).sum() / psi.sum())
+
+    def curve_samples(self):
+        """{step n_j: (target T_j, weight w_j)} of J_CURVE (steps 1..N)."""
+        p = self.p
+        out = {}
+        for n, T, w in zip(p.sample_steps, p.sample_targets, p.sample_weights):
+            if not 1 <= n <= p.nsteps:
+                raise ValueError("curve samples must lie in steps 1..nsteps")
+            out[int(n)] = (float(T), float(w))
+        return out
+
+    def curve_source(self, m, T, w):
+        """(dJ/dm, explicit dJ/dpsi) of w |P(m) - T| (derivative 0 at P = T)."""
+        p, psi = self.p, self.psi
+        P = self.curve_point(m)
+        W = w * np.sign(P - T)
+        S = psi.sum()
+        g = np.zeros_like(m)
+        g[p.comp] = W * psi / S
+        return g, W * (m[p.comp] - P) / S
+
+    def centre(self):
+        """psi-weighted mean node index (x_c, y_c)."""
+        psi = self.psi
+        iy, ix = np.meshgrid(np.arange(self.p.ny), np.arange(self.p.nx), indexing="ij")
+        S = psi.sum()
+        return float((psi * ix).sum() / S), float((psi * iy).sum() / S)
+
+    def penalties(self):
+        """Size and centre terms of Eq. 9 (J_CURVE)."""
+        p = self.p
+        xc, yc = self.centre()
+        size = p.penalty_w * (self.psi.mean() - p.area_target) ** 2
+        return size + p.centre_w * (abs(xc - p.centre_target[0]) + abs(yc - p.centre_target[1]))
+
+    def penalties_grad(self):
+        p, psi = self.p, self.psi
+        xc, yc = self.centre()
+        iy, ix = np.meshgrid(np.arange(p.ny), np.arange(p.nx), indexing="ij")
+        S = psi.sum()
+        g = 2.0 * p.penalty_w * (psi.mean() - p.area_target) / psi.size * np.ones(self.shape)
+        g += p.centre_w * (np.sign(xc - p.centre_target[0]) * (ix - xc)
+                           + np.sign(yc - p.centre_target[1]) * (iy - yc)) / S
+        return g
+
     def energy_terms(self, m):
         """(E_demag, E_exchange) in joules."""
         p, psi, V = self.p, self.psi, self.V
@@ -271,6 +336,8 @@ class Model:
 
     def terminal(self, m):
         p = self.p
+        if p.objective == J_CURVE:
+            return self.penalties()
         if p.objective != J_ENERGY_AREA:
             return 0.0
         Ed, Ee = self.energy_terms(m)
@@ -282,6 +349,8 @@ class Model:
         p, psi, V = self.p, self.psi, self.V
         gm = np.zeros_like(m)
         gpsi = np.zeros(self.shape)
+        if p.objective == J_CURVE:
+            return gm, self.penalties_grad()
         if p.objective != J_ENERGY_AREA:
             return gm, gpsi
         s = self._energy_scale()
@@ -306,6 +375,8 @@ class Model:
         if p.objective == J_SPECTRAL and p.n_from < 1:
             raise ValueError("the spectral objective needs n_from >= 1")
         series = []
+        samples = self.curve_samples() if p.objective == J_CURVE else {}
+        self.curve = []
         if p.objective == J_PORT and p.n_from <= 0:
             J += self.port_term(m)
         for n in range(p.nsteps):
@@ -316,6 +387,11 @@ class Model:
                 J += self.port_term(m)
             if p.objective == J_SPECTRAL and n + 1 >= p.n_from:
                 series.append(self.port_means(m))
+            if n + 1 in samples:
+                T, w = samples[n + 1]
+                P = self.curve_point(m)
+                self.curve.append(P)
+                J += w * abs(P - T)
         if p.objective == J_SPECTRAL:
             self.series = np.array(series).reshape(-1, 2)
             J += self.spectral_value(self.series)
@@ -386,6 +462,10 @@ class Model:
             SW = self.spectral_weights(series)             # row k - n_from: step k
             if N >= p.n_from:
                 lam = lam + self.spectral_source(SW[N - p.n_from])
+        samples = self.curve_samples() if p.objective == J_CURVE else {}
+        if N in samples:
+            g, q = self.curve_source(traj[N], *samples[N])
+            lam, gpsi = lam + g, gpsi + q
         for n in range(N - 1, -1, -1):
             Y, B, _ = self.stages(traj[n], n)
             u4 = dt / 6.0 * lam
@@ -402,6 +482,9 @@ class Model:
                 lam = lam + self.port_term_grad(traj[n])
             if p.objective == J_SPECTRAL and n >= p.n_from:
                 lam = lam + self.spectral_source(SW[n - p.n_from])
+            if n in samples:
+                g, q = self.curve_source(traj[n], *samples[n])
+                lam, gpsi = lam + g, gpsi + q
         dphi = p.sigmoid_a * self.psi * (1.0 - self.psi) * gpsi
         return dphi, lam, J
 

@@ -220,12 +220,38 @@ def test_zeeman_rf_on_source_only():
     inst = W.random_small(6, 4, seed=1)
     mod = llg.Model(inst.problem, inst.phi)
     p = inst.problem
-    t = 3.3e-11
-    B = mod.zeeman(t)
+    n, ci = 330, 1                                  # t = 330.5 dt
+    t = 330.5 * p.dt
+    B = mod.zeeman(n, ci)
     x0, x1, y0, y1 = p.src
     s = p.b_rf * np.sin(2 * np.pi * p.f_rf * t)
-    assert B[1, 0, y0, x0] == pytest.approx(p.B_bias[1] + s, rel=1e-14)
+    assert B[1, 0, y0, x0] == pytest.approx(p.B_bias[1] + s, rel=1e-12)
     assert B[1, 0, 0, x1] == pytest.approx(p.B_bias[1], rel=1e-14)
+
+
+def test_tabulated_drive_replaces_the_sine_and_matches_a_bias():
+    """A drive table that is constant b along z on a source box covering the
+    grid gives the same trajectory as a bias b z (no sine, no box edge)."""
+    base = W.random_small(6, 4, seed=2, nsteps=12)
+    p = base.problem
+    b = 0.013
+    p_tab = p.replace(b_rf=0.0, rf_dir=(0.0, 0.0, 1.0), src=(0, p.nx, 0, p.ny), drive=(b,) * (3 * p.nsteps + 3))
+    p_bias = p.replace(b_rf=0.0, B_bias=(p.B_bias[0], p.B_bias[1], p.B_bias[2] + b))
+    _, m_tab, _ = llg.Model(p_tab, base.phi).forward(base.m0, keep=False)
+    _, m_bias, _ = llg.Model(p_bias, base.phi).forward(base.m0, keep=False)
+    np.testing.assert_allclose(m_tab, m_bias, rtol=0, atol=1e-13)
+    # a table read per (step, stage time): a pulse at one stage time only
+    # changes the trajectory from that step on
+    pulse = [0.0] * (3 * p.nsteps + 3)
+    pulse[3 * 7 + 1] = 0.05
+    p_pulse = p_tab.replace(drive=tuple(pulse))
+    mod = llg.Model(p_pulse, base.phi)
+    m = np.array(base.m0, float)
+    ref = llg.Model(p_tab.replace(drive=(0.0,) * (3 * p.nsteps + 3)), base.phi)
+    mr = m.copy()
+    for n in range(p.nsteps):
+        m, mr = mod.step(m, n), ref.step(mr, n)
+        assert (np.abs(m - mr).max() > 0) == (n >= 7)
 
 
 def test_port_functional_closed_form():

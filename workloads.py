@@ -25,7 +25,7 @@ from __future__ import annotations
 
 import dataclasses
 from dataclasses import dataclass, field
-from typing import List, Tuple
+from typing import List, Optional, Tuple
 
 import numpy as np
 
@@ -33,6 +33,7 @@ import numpy as np
 J_PORT = 0      # sum_{n>=n_from} sum_b w_b mean_{box b}(m_c,n ^ p)
 J_ENERGY_AREA = 1  # (E_demag + E_exchange)(m_N)/(K_d V_dom) + xi (mean psi - s_t)^2
 J_SPECTRAL = 2   # sum_b w_b sum_q |DFT of the port-mean series at f_q| (Eq. 10, windowed)
+J_CURVE = 3      # sum_j w_j |P(m_{n_j}) - T_j| + size and centre penalties (Eq. 8, Eq. 9)
 
 Box = Tuple[int, int, int, int]  # x0, x1, y0, y1 (half open, node indices)
 
@@ -72,6 +73,19 @@ class Problem:
     area_target: float = 0.3
     penalty_w: float = 1.0
     freqs: Tuple[float, ...] = ()   # J_SPECTRAL: frequencies of the windowed spectral sum (Hz)
+    # applied drive b(t) on the source box along rf_dir, tabulated per step n
+    # at t = n dt, n dt + dt/2, n dt + dt (3 nsteps + 3 values, tesla); None:
+    # the sine b_rf sin(2 pi f_rf t)
+    drive: Optional[Tuple[float, ...]] = None
+    # J_CURVE: J = sum_j w_j |P(m_{n_j}) - T_j|, P = sum psi m_comp / sum psi
+    sample_steps: Tuple[int, ...] = ()
+    sample_targets: Tuple[float, ...] = ()
+    sample_weights: Tuple[float, ...] = ()
+    # J_CURVE penalties (Eq. 9): penalty_w (mean psi - area_target)^2 and
+    # centre_w (|x_c - x_0| + |y_c - y_0|), the psi-weighted centre of the
+    # (first) layer's nodes in node-index units
+    centre_w: float = 0.0
+    centre_target: Tuple[float, float] = (0.0, 0.0)
 
     def replace(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)
@@ -258,6 +272,47 @@ def thick512(nsteps: int = 50000, nx: int = 512, ny: int = 512, nz: int = 4) -> 
     return Instance(p, phi, m0, mask, "thick512")
 
 
+def sw_particle(instance: int = 0, levels: int = 30, hold: int = 500, regularised: bool = False,
+                nx: int = 30, ny: int = 30) -> Instance:
+    """Stoner-Wohlfarth hysteresis task (Eq. 8; Eq. 9 when `regularised`):
+    a 30 x 30 x 1 Permalloy mesh of 3 nm cells holding an initially circular
+    particle (radius 10 cells), a uniform field along x raised in `levels`
+    equal steps from 0 to 0.3 Ms (mu0 H), each level held `hold` RK4 steps
+    (alpha 0.5, so the particle relaxes), and M_x/Ms = sum psi m_x / sum psi
+    sampled at the end of levels j = 1..levels against the target 2 H_j/Ms
+    with weights 1/(levels T_j) (zeta/(levels T_j), zeta = 10, with the size
+    penalty xi = 0.05 toward a one-cell-wide wire and the centre penalty
+    nu = 1 toward the mesh centre when `regularised`).  m0 = +y with 1e-3
+    seeded noise."""
+    rng = _rng(6, instance)
+    h = 3e-9
+    Ms = 8e5
+    N = (levels + 1) * hold
+    b_max = 4e-7 * np.pi * 0.3 * Ms                      # mu0 * 0.3 Ms (T)
+    level_of_step = np.minimum(np.arange(N + 1) // hold, levels)
+    b = (b_max * level_of_step / levels).astype(float)
+    drive = tuple(np.repeat(b, 3)[:3 * N + 3].tolist())  # constant within each step
+    js = np.arange(1, levels + 1)
+    targets = 2.0 * 0.3 * js / levels
+    zeta = 10.0 if regularised else 1.0
+    p = Problem(nx=nx, ny=ny, nz=1, dx=h, dy=h, dz=h, Ms=Ms, A=1.3e-11, alpha=0.5, alpha_edge=0.5,
+                B_bias=(0.0, 0.0, 0.0), b_rf=0.0, f_rf=0.0, rf_dir=(1.0, 0.0, 0.0), src=(0, nx, 0, ny),
+                dt=1e-13, nsteps=N, objective=J_CURVE, comp=0, n_from=1, drive=drive,
+                sample_steps=tuple(int(v) for v in (js + 1) * hold),
+                sample_targets=tuple(targets.tolist()),
+                sample_weights=tuple((zeta / (levels * targets)).tolist()),
+                area_target=1.0 / nx, penalty_w=0.05 if regularised else 0.0,
+                centre_w=1.0 if regularised else 0.0, centre_target=((nx - 1) / 2.0, (ny - 1) / 2.0))
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    r = np.hypot(xx - (nx - 1) / 2.0, yy - (ny - 1) / 2.0) * h
+    R = 10 * h
+    phi = (R - r) / R + 0.05 * rng.standard_normal((ny, nx))
+    phi = phi / np.abs(phi).max()
+    m0 = noisy_uniform_m0(rng, nx, ny, 1, direction=(0.0, 1.0, 0.0))
+    mask = np.ones((1, ny, nx), np.uint8)
+    return Instance(p, phi[None], m0, mask, "sw_particle" + ("_reg" if regularised else ""))
+
+
 def random_small(nx: int, ny: int, nz: int = 1, seed: int = 0, nsteps: int = 50,
                  objective: int = J_PORT, **over) -> Instance:
     """Small seeded instance with every field term switched on (bias, RF,
@@ -282,5 +337,5 @@ def random_small(nx: int, ny: int, nz: int = 1, seed: int = 0, nsteps: int = 50,
 
 
 def by_name(name: str, **kw):
-    return {"film32": film32, "particle64": particle64, "demux256": demux256,
+    return {"film32": film32, "particle64": particle64, "demux256": demux256, "sw_particle": sw_particle,
             "batch64": batch64, "thick512": thick512}[name](**kw)
