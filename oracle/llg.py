@@ -147,19 +147,33 @@ class Model:
             return 0.0
         return p.b_rf * np.sin(2.0 * np.pi * p.f_rf * (n * p.dt + 0.5 * ci * p.dt))
 
-    def zeeman(self, n, ci):
+    def _zeeman_of(self, s):
         p = self.p
         B = np.zeros((3,) + self.shape)
         for c in range(3):
             B[c] += p.B_bias[c]
-        s = self.drive(n, ci)
         if s != 0.0:
             for c in range(3):
                 B[c][self.src] += s * p.rf_dir[c]
         return B
 
-    def field(self, m, n, ci):
-        return self.exchange(m) + self.demag(m) + self.anisotropy(m) + self.zeeman(n, ci)
+    def zeeman_stage(self, n, ci):
+        """Zeeman field at the stage time n dt + (ci/2) dt of step n."""
+        return self._zeeman_of(self.drive(n, ci))
+
+    def zeeman(self, t):
+        """Zeeman field at time t (sine drive; a tabulated drive is defined at
+        stage times only, see zeeman_stage)."""
+        p = self.p
+        if p.drive is not None:
+            raise ValueError("a tabulated drive is defined at stage times only")
+        return self._zeeman_of(p.b_rf * np.sin(2.0 * np.pi * p.f_rf * t) if p.b_rf != 0.0 else 0.0)
+
+    def stage_field(self, m, n, ci):
+        return self.exchange(m) + self.demag(m) + self.anisotropy(m) + self.zeeman_stage(n, ci)
+
+    def field(self, m, t):
+        return self.exchange(m) + self.demag(m) + self.anisotropy(m) + self.zeeman(t)
 
     def rhs(self, m, B):
         a = self.alpha
@@ -174,7 +188,7 @@ class Model:
         Y, B, K = [], [], []
         y = m
         for s, (ci, c_next) in enumerate(((0, 0.5), (1, 0.5), (1, 1.0), (2, None))):
-            b = self.field(y, n, ci)
+            b = self.stage_field(y, n, ci)
             k = self.rhs(y, b)
             Y.append(y)
             B.append(b)

@@ -222,8 +222,9 @@ def test_zeeman_rf_on_source_only():
     p = inst.problem
     n, ci = 330, 1                                  # t = 330.5 dt
     t = 330.5 * p.dt
-    B = mod.zeeman(n, ci)
+    B = mod.zeeman_stage(n, ci)
     x0, x1, y0, y1 = p.src
+    np.testing.assert_array_equal(B, mod.zeeman(t))
     s = p.b_rf * np.sin(2 * np.pi * p.f_rf * t)
     assert B[1, 0, y0, x0] == pytest.approx(p.B_bias[1] + s, rel=1e-12)
     assert B[1, 0, 0, x1] == pytest.approx(p.B_bias[1], rel=1e-14)
