@@ -65,7 +65,7 @@ typedef enum {
   LLG_ESTATE = 6      /* call order violated (adjoint without forward, ...)  */
 } llg_status;
 
-enum { LLG_J_PORT = 0, LLG_J_ENERGY_AREA = 1, LLG_J_SPECTRAL = 2 };
+enum { LLG_J_PORT = 0, LLG_J_ENERGY_AREA = 1, LLG_J_SPECTRAL = 2, LLG_J_CURVE = 3 };
 enum { LLG_FP32 = 0, LLG_FP64 = 1 };
 enum { LLG_CKPT_STORE_ALL = 0, LLG_CKPT_PERIODIC = 1, LLG_CKPT_BINOMIAL = 2 };
 
@@ -88,7 +88,7 @@ typedef struct {
   double dt;                 /* time step                                      */
   long long nsteps;          /* number of RK4 steps N                          */
   double sigmoid_a;          /* a of Eq. 4                                     */
-  int objective;             /* LLG_J_PORT, LLG_J_ENERGY_AREA or LLG_J_SPECTRAL */
+  int objective;             /* LLG_J_PORT, LLG_J_ENERGY_AREA, LLG_J_SPECTRAL, LLG_J_CURVE */
   int comp, power;           /* LLG_J_PORT: sampled component, exponent 1 or 2 */
   int boxes[2][4];           /* LLG_J_PORT: boxes x0,x1,y0,y1                   */
   double weights[2];         /* LLG_J_PORT: J = sum_{n>=n_from} sum_b w_b
@@ -105,6 +105,28 @@ typedef struct {
                                 at the window's frequencies); 1 <= nfreq <= 8,
                                 n_from >= 1                                  */
   double freqs[8];           /* LLG_J_SPECTRAL: the frequencies f_q (Hz)     */
+  const double* drive;       /* optional host table of the applied drive b at
+                                t = n dt + c dt, c = 0, 1/2, 1, for n = 0..nsteps
+                                (3 nsteps + 3 values, tesla, index 3n + 2c),
+                                applied on the source box along rf_dir in place
+                                of b_rf sin(2 pi f_rf t); NULL: the sine.  Read
+                                at llg_create only.  llg_field ignores it (its
+                                time argument is not a stage time).          */
+  int nsample;               /* LLG_J_CURVE: J = sum_j w_j |P(m_{n_j}) - T_j|
+                                + penalty_w (mean psi - area_target)^2
+                                + centre_w (|x_c - x_0| + |y_c - y_0|), with
+                                P = sum psi m_comp / sum psi (Eq. 8 sampled at
+                                the end of each field level) and (x_c, y_c) the
+                                psi-weighted mean node index (x, y) (Eq. 9);
+                                nsample >= 1                                 */
+  const long long* sample_step;  /* LLG_J_CURVE: host array [nsample] of steps
+                                n_j, strictly increasing, 1 <= n_j <= nsteps;
+                                the three sample arrays are read at llg_create
+                                only                                         */
+  const double* sample_target;   /* LLG_J_CURVE: host array [nsample], T_j    */
+  const double* sample_weight;   /* LLG_J_CURVE: host array [nsample], w_j    */
+  double centre_w;           /* LLG_J_CURVE: weight of the centre term        */
+  double centre_target[2];   /* LLG_J_CURVE: (x_0, y_0), node-index units     */
 } llg_problem;
 
 typedef struct {

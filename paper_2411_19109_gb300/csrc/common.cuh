@@ -96,7 +96,7 @@ struct DevInst {
   long long tens_off;    // offset into the tensor pool, real elements
   long long slot_off;    // offset into the objective partials: (nsteps+1) x ntile
   long long rf_off;      // offset into the RF drive table (3 nsteps + 3 values)
-  long long wt_off;      // spectral objective: offset into the per-step port weights ((nsteps+1) x 2)
+  long long wt_off;      // spectral / curve objective: offset into the per-step weights ((nsteps+1) x 2)
   double Ms;
   double cex_x, cex_y, cex_z;   // 2A/(Ms h^2)
   double kan;                   // 2Ku/Ms
@@ -116,6 +116,7 @@ struct DevInst {
   double escale;                // 1/(K_d V_domain)
   double A;                     // exchange constant
   double area_target, penalty_w;
+  double centre_w, centre_x0, centre_y0;   // curve objective: centre term (node-index units)
   Coef<double> cd;              // the coefficients above in FP64 ...
   Coef<float> cf;               // ... and rounded to FP32
 };

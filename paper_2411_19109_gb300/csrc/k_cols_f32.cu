@@ -5,7 +5,7 @@
 namespace llg {
 template void launch_cols<float>(const ColArgs<float>&, int, size_t, cudaStream_t);
 template void smem_cols<float>(size_t);
-template void launch_material_tiles<float>(const DevInst*, const RowTile*, int, const float*, float*, float*, double*,
+template void launch_material_tiles<float>(const DevInst*, const RowTile*, int, const float*, float*, float*, double*, double*,
                                          cudaStream_t);
 template void launch_grad_finish_tiles<float>(const DevInst*, const RowTile*, int, const float*, const float*,
                                             const float*, float*, cudaStream_t);

@@ -5,7 +5,7 @@
 namespace llg {
 template void launch_cols<double>(const ColArgs<double>&, int, size_t, cudaStream_t);
 template void smem_cols<double>(size_t);
-template void launch_material_tiles<double>(const DevInst*, const RowTile*, int, const double*, double*, double*, double*,
+template void launch_material_tiles<double>(const DevInst*, const RowTile*, int, const double*, double*, double*, double*, double*,
                                          cudaStream_t);
 template void launch_grad_finish_tiles<double>(const DevInst*, const RowTile*, int, const double*, const double*,
                                             const double*, double*, cudaStream_t);

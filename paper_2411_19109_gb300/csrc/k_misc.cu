@@ -13,7 +13,7 @@ __global__ void set_step_kernel(long long* p, long long v) { *p = v; }
 // penalty on the mean of psi.  Every sum runs in a fixed order, so J is
 // reproducible bit for bit.
 __global__ void reduce_slots_kernel(const DevInst* inst, const double* slots, long long nsteps1,
-                                    const double* jterm, const double* psitile, double* J) {
+                                    const double* jterm, const double* psitile, const double* psimom, double* J) {
   __shared__ double red[32];
   const DevInst& I = inst[blockIdx.x];
   const long long nslots = nsteps1 * I.ntile;
@@ -34,19 +34,41 @@ __global__ void reduce_slots_kernel(const DevInst* inst, const double* slots, lo
     if (I.objective == 1) {
       const double f = ps / (double)I.nodes - I.area_target;
       j += I.penalty_w * f * f;
+    } else if (I.objective == 3) {
+      // size and centre terms of Eq. 9 (the sampled curve is added on the host)
+      double sx = 0.0, sy = 0.0;
+      for (int t = 0; t < I.ntile; ++t) {
+        sx += psimom[2 * (I.tile_off + t)];
+        sy += psimom[2 * (I.tile_off + t) + 1];
+      }
+      const double f = ps / (double)I.nodes - I.area_target;
+      j += I.penalty_w * f * f + I.centre_w * (fabs(sx / ps - I.centre_x0) + fabs(sy / ps - I.centre_y0));
     }
     J[blockIdx.x] = j;
   }
 }
 
-// Spectral objective: port-box means P_b[n] of m_comp from the per-(step,
-// tile, box) partials, tiles added in order (block per instance).
-__global__ void port_series_kernel(const DevInst* inst, const double* pslots, long long nsteps1, double* P) {
+// Series of the spectral and curve objectives from the per-(step, tile,
+// channel) partials, tiles added in order (block per instance).  Spectral:
+// port-box means P_b[n] of m_comp (channel b).  Curve: P[n] = sum psi m_comp
+// / sum psi in channel 0, sum psi in channel 1.
+__global__ void port_series_kernel(const DevInst* inst, const double* pslots, const double* psitile,
+                                   long long nsteps1, double* P) {
   const DevInst& I = inst[blockIdx.x];
-  if (I.objective != 2) return;
+  if (I.objective != 2 && I.objective != 3) return;
+  double S = 0.0;
+  if (I.objective == 3)
+    for (int k = 0; k < I.ntile; ++k) S += psitile[I.tile_off + k];
   for (long long e = threadIdx.x; e < 2 * nsteps1; e += blockDim.x) {
     const long long n = e >> 1;
     const int b = (int)(e & 1);
+    if (I.objective == 3) {
+      double s = 0.0;
+      if (b == 0)
+        for (int k = 0; k < I.ntile; ++k) s += pslots[2 * (I.slot_off + n * I.ntile + k)];
+      P[I.wt_off + e] = b == 0 ? s / S : S;
+      continue;
+    }
     const long long cnt = (long long)(I.boxes[b][1] - I.boxes[b][0]) * (I.boxes[b][3] - I.boxes[b][2]) * I.nz;
     double s = 0.0;
     for (int k = 0; k < I.ntile; ++k) s += pslots[2 * (I.slot_off + n * I.ntile + k) + b];
@@ -54,9 +76,9 @@ __global__ void port_series_kernel(const DevInst* inst, const double* pslots, lo
   }
 }
 
-void launch_port_series(const DevInst* inst, int n_inst, const double* pslots, long long nsteps1, double* P,
-                        cudaStream_t st) {
-  port_series_kernel<<<n_inst, 256, 0, st>>>(inst, pslots, nsteps1, P);
+void launch_port_series(const DevInst* inst, int n_inst, const double* pslots, const double* psitile,
+                        long long nsteps1, double* P, cudaStream_t st) {
+  port_series_kernel<<<n_inst, 256, 0, st>>>(inst, pslots, psitile, nsteps1, P);
 }
 
 void launch_set_step(long long* step_base, long long v, cudaStream_t st) {
@@ -64,8 +86,9 @@ void launch_set_step(long long* step_base, long long v, cudaStream_t st) {
 }
 
 void launch_reduce_slots(const DevInst* inst, int n_inst, const double* slots, long long nsteps1,
-                         const double* jterm, const double* psitile, double* J, cudaStream_t st) {
-  reduce_slots_kernel<<<n_inst, 256, 0, st>>>(inst, slots, nsteps1, jterm, psitile, J);
+                         const double* jterm, const double* psitile, const double* psimom, double* J,
+                         cudaStream_t st) {
+  reduce_slots_kernel<<<n_inst, 256, 0, st>>>(inst, slots, nsteps1, jterm, psitile, psimom, J);
 }
 
 template <typename T>

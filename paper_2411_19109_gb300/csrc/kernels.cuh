@@ -30,7 +30,8 @@ struct RowArgs {
   T* ckpt;            // copy of m_{n+1} (stage 4, nullable)
   double* slots;      // objective slots (nullable: do not accumulate)
   double* pslots;     // spectral objective: per-(step, tile, box) port partials (nullable)
-  const double* wtab; // spectral objective: per-step adjoint weights of the port boxes
+  const double* wtab; // spectral / curve objective: per-step adjoint weights
+  const double* psimom;  // per row tile: sum psi x, sum psi y (curve objective's centre)
   const long long* step_base;
   int* err;           // error word (bounded waits that ran out)
   const double* rf;   // per instance, per step: b_rf sin(2 pi f t) at t = n dt + c dt, c = 0, 1/2, 1
@@ -141,7 +142,7 @@ template <typename T>
 void set_smem_limits(size_t stage, size_t misc, size_t cols, size_t adj);
 template <typename T>
 void launch_material_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* phi, T* psi,
-                           T* dpsi, double* psitile, cudaStream_t st);
+                           T* dpsi, double* psitile, double* psimom, cudaStream_t st);
 template <typename T>
 void launch_grad_finish_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* dpsi,
                               const T* psib, const T* psic, T* out, cudaStream_t st);
@@ -149,10 +150,11 @@ template <typename T>
 void launch_levelset_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, T* phi, const T* grad,
                            const unsigned char* mask, double lr, unsigned int* maxbits, cudaStream_t st);
 void launch_set_step(long long* step_base, long long v, cudaStream_t st);
-void launch_port_series(const DevInst* inst, int n_inst, const double* pslots, long long nsteps1, double* P,
-                        cudaStream_t st);
+void launch_port_series(const DevInst* inst, int n_inst, const double* pslots, const double* psitile,
+                        long long nsteps1, double* P, cudaStream_t st);
 void launch_reduce_slots(const DevInst* inst, int n_inst, const double* slots, long long nslots,
-                         const double* jterm, const double* psitile, double* J, cudaStream_t st);
+                         const double* jterm, const double* psitile, const double* psimom, double* J,
+                         cudaStream_t st);
 int rows_threads();
 int cols_threads();
 int adj_threads();

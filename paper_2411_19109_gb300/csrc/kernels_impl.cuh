@@ -488,6 +488,25 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
           for (int b = 0; b < 2; ++b)
             if (in_box(I.boxes[b], x, y)) lam[I.comp] += (T)a.wtab[I.wt_off + 2 * a.nsteps + b];
         }
+      } else if (I.objective == 3) {
+        // a sample at step N: w sign(P - T)/S on lambda_comp (psi-weighted)
+        // and the quotient-rule term on dJ/dpsi; then the size and centre
+        // terms of Eq. 9, from the per-tile psi moments
+        const double wl = a.wtab[I.wt_off + 2 * a.nsteps];
+        lam[I.comp] = (T)(wl * (double)pi);
+        double q = wl * (double)yi[I.comp] - a.wtab[I.wt_off + 2 * a.nsteps + 1];
+        double S = 0.0, Sx = 0.0, Sy = 0.0;
+        for (int t = 0; t < I.ntile; ++t) {
+          S += a.psitile[I.tile_off + t];
+          Sx += a.psimom[2 * (I.tile_off + t)];
+          Sy += a.psimom[2 * (I.tile_off + t) + 1];
+        }
+        const double xc = Sx / S, yc = Sy / S;
+        const double sgx = xc > I.centre_x0 ? 1.0 : (xc < I.centre_x0 ? -1.0 : 0.0);
+        const double sgy = yc > I.centre_y0 ? 1.0 : (yc < I.centre_y0 ? -1.0 : 0.0);
+        q += 2.0 * I.penalty_w * (S / (double)nodes - I.area_target) / (double)nodes;
+        q += I.centre_w * (sgx * ((double)x - xc) + sgy * ((double)y - yc)) / S;
+        qp = (T)q;
       } else if (a.nsteps >= a.n_from) {
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
@@ -607,8 +626,10 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
   const int cs = (RM + 2) * nx;                            // component stride of the staged halo
   double vsum = 0.0;
   const bool objective_step = s == 4 && a.slots != nullptr && I.objective == 0 && (n + 1) >= a.n_from;
-  // spectral objective: the port-box sums of m_comp at step n + 1
-  const bool spectral_step = s == 4 && a.pslots != nullptr && I.objective == 2 && (n + 1) >= a.n_from;
+  // spectral objective: the port-box sums of m_comp at step n + 1; curve
+  // objective: the tile's sum of psi m_comp (channel 0) at every step
+  const bool spectral_step = s == 4 && a.pslots != nullptr &&
+                             ((I.objective == 2 && (n + 1) >= a.n_from) || I.objective == 3);
   double psum[2] = {0.0, 0.0};
 #pragma unroll 1
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
@@ -693,9 +714,13 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
       }
     }
     if (spectral_step) {
+      if (I.objective == 3) {
+        psum[0] += (double)pi * (double)yn[I.comp];
+      } else {
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
-        if (in_box(I.boxes[b], x, y)) psum[b] += (double)yn[I.comp];
+        for (int b = 0; b < 2; ++b)
+          if (in_box(I.boxes[b], x, y)) psum[b] += (double)yn[I.comp];
+      }
     }
   }
   if (objective_step) {
@@ -710,7 +735,9 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
   if (spectral_step) {
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-      if (!(I.boxes[b][2] < y0 + nr && I.boxes[b][3] > y0 && I.boxes[b][0] < I.boxes[b][1])) continue;
+      if (I.objective == 3 ? b != 0
+                           : !(I.boxes[b][2] < y0 + nr && I.boxes[b][3] > y0 && I.boxes[b][0] < I.boxes[b][1]))
+        continue;
       const double tot = block_sum(psum[b], red);
       if (threadIdx.x == 0) a.pslots[2 * (I.slot_off + (long long)(n + 1) * I.ntile + tile.k) + b] = tot;
       __syncthreads();   // red is reused by the next box
@@ -961,6 +988,11 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
         gg[c] += Ms * pi * D[c];
       }
       qpsi += Ms * dot3(yi, D);
+      if (s == 1 && I.objective == 3) {
+        // curve sample at step n: the quotient-rule term of P = sum psi m / sum psi
+        const double wl = a.wtab[I.wt_off + 2 * n];
+        qpsi += (T)(wl * (double)yi[I.comp] - a.wtab[I.wt_off + 2 * n + 1]);
+      }
       kahan_add(qs, qc, qpsi);
       gpsib[I.node_off + n0] = qs;
       gpsic[I.node_off + n0] = qc;
@@ -987,6 +1019,8 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
 #pragma unroll
           for (int b = 0; b < 2; ++b)
             if (in_box(I.boxes[b], x, y)) lam[I.comp] += (T)a.wtab[I.wt_off + 2 * n + b];
+        } else if (I.objective == 3) {
+          lam[I.comp] += (T)(a.wtab[I.wt_off + 2 * n] * (double)pi);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) glam[off3 + c * nodes + n0] = lam[c];
@@ -1050,22 +1084,32 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? 2 : 1) adj_kerne
 
 template <typename T>
 __global__ void material_kernel(const DevInst* inst, const RowTile* tiles, const T* phi, T* psi, T* dpsi,
-                                double* psitile) {
+                                double* psitile, double* psimom) {
   __shared__ double red[32];
   const RowTile tile = tiles[blockIdx.x];
   const DevInst& I = inst[tile.inst];
   const long long base = tile_base(I, tile);
   const int cnt = tile.nrows * I.nx;
-  double acc = 0.0;
+  double acc = 0.0, ax = 0.0, ay = 0.0;
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
     const double ph = (double)phi[base + e];
     const double p = 1.0 / (1.0 + exp(-I.sigmoid_a * ph));   // Eq. 4
     psi[base + e] = (T)p;
     dpsi[base + e] = (T)(I.sigmoid_a * p * (1.0 - p));
     acc += p;
+    ax += p * (double)(e % I.nx);                             // psi-weighted node index (x, y)
+    ay += p * (double)(tile.y0 + e / I.nx);
   }
   const double tot = block_sum(acc, red);
   if (threadIdx.x == 0) psitile[I.tile_off + tile.k] = tot;
+  if (psimom) {
+    __syncthreads();
+    const double sx = block_sum(ax, red);
+    if (threadIdx.x == 0) psimom[2 * (I.tile_off + tile.k)] = sx;
+    __syncthreads();
+    const double sy = block_sum(ay, red);
+    if (threadIdx.x == 0) psimom[2 * (I.tile_off + tile.k) + 1] = sy;
+  }
 }
 
 template <typename T>
@@ -1168,8 +1212,8 @@ void smem_adj(size_t smem) {
 }
 template <typename T>
 void launch_material_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* phi, T* psi,
-                           T* dpsi, double* psitile, cudaStream_t st) {
-  material_kernel<T><<<ntiles, 256, 0, st>>>(inst, tiles, phi, psi, dpsi, psitile);
+                           T* dpsi, double* psitile, double* psimom, cudaStream_t st) {
+  material_kernel<T><<<ntiles, 256, 0, st>>>(inst, tiles, phi, psi, dpsi, psitile, psimom);
 }
 template <typename T>
 void launch_grad_finish_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* dpsi,

@@ -214,7 +214,7 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
     if (err_msg) *err_msg = "llg_field_noalloc: set-up copies or tensor build failed";
     return LLG_ECUDA;
   }
-  launch_material_tiles<float>(dI, dRT, nrt, static_cast<const float*>(phi_dev), psi, dpsi, psitile, st);
+  launch_material_tiles<float>(dI, dRT, nrt, static_cast<const float*>(phi_dev), psi, dpsi, psitile, nullptr, st);
 
   RowArgs<float> a;
   std::memset(&a, 0, sizeof a);

@@ -213,8 +213,17 @@ struct Engine final : llg_ctx {
   // spectral objective: port partials per (step, tile, box), port series and
   // per-step adjoint weights per (instance, step, box), host copies
   double *pslots = nullptr, *Pd = nullptr, *wtab = nullptr;
-  bool any_spec = false;
+  bool any_spec = false;   // an instance with the spectral or the curve objective
   std::vector<double> hP, hW, Jspec;
+  // per instance: the tabulated drive (empty: sine) and the curve samples,
+  // copied at create (the caller's arrays need not outlive llg_create)
+  std::vector<std::vector<double>> drive_tab;
+  struct CurveSamples {
+    std::vector<long long> step;
+    std::vector<double> target, weight;
+  };
+  std::vector<CurveSamples> curve;
+  double* psimom = nullptr;   // per row tile: sum psi x, sum psi y
   long long total_slots = 0;
   long long* step_base = nullptr;
   unsigned int* maxbits = nullptr;
@@ -357,8 +366,26 @@ struct Engine final : llg_ctx {
         return fail(LLG_EINVAL, "dx, dy, dz, Ms, dt must be > 0 and A >= 0");
       if (p.nsteps < 0 || p.nsteps != N || p.n_from != n_from || p.dt != dt)
         return fail(LLG_EINVAL, "all instances must share nsteps >= 0, n_from and dt");
-      if (p.objective != LLG_J_PORT && p.objective != LLG_J_ENERGY_AREA && p.objective != LLG_J_SPECTRAL)
+      if (p.objective != LLG_J_PORT && p.objective != LLG_J_ENERGY_AREA && p.objective != LLG_J_SPECTRAL &&
+          p.objective != LLG_J_CURVE)
         return fail(LLG_EINVAL, "unknown objective");
+      if (p.objective == LLG_J_CURVE) {
+        if (p.nsample < 1 || !p.sample_step || !p.sample_target || !p.sample_weight || p.comp < 0 || p.comp > 2)
+          return fail(LLG_EINVAL, "curve objective needs nsample >= 1, the three sample arrays and comp in 0..2");
+        for (int j = 0; j < p.nsample; ++j) {
+          if (p.sample_step[j] < 1 || p.sample_step[j] > p.nsteps || (j > 0 && p.sample_step[j] <= p.sample_step[j - 1]))
+            return fail(LLG_EINVAL, "curve objective: sample steps must increase strictly within 1..nsteps");
+          if (!std::isfinite(p.sample_target[j]) || !std::isfinite(p.sample_weight[j]))
+            return fail(LLG_EINVAL, "curve objective: targets and weights must be finite");
+        }
+        if (!std::isfinite(p.centre_w) || !std::isfinite(p.centre_target[0]) || !std::isfinite(p.centre_target[1]) ||
+            !std::isfinite(p.penalty_w) || !std::isfinite(p.area_target))
+          return fail(LLG_EINVAL, "curve objective: penalty weights and targets must be finite");
+        any_spec = true;
+      }
+      if (p.drive && p.nsteps > 0)
+        for (long long k = 0; k < 3 * p.nsteps + 3; ++k)
+          if (!std::isfinite(p.drive[k])) return fail(LLG_EINVAL, "drive table values must be finite");
       if (p.objective == LLG_J_SPECTRAL) {
         if (p.nfreq < 1 || p.nfreq > 8 || p.n_from < 1 || p.comp < 0 || p.comp > 2)
           return fail(LLG_EINVAL, "spectral objective needs 1 <= nfreq <= 8, n_from >= 1 and comp in 0..2");
@@ -408,6 +435,21 @@ struct Engine final : llg_ctx {
     struct Shape { int nx, ny, nz; double dx, dy, dz; long long off; int Px, Py, Pz; };
     std::vector<Shape> shapes;
     H.resize(n);
+    drive_tab.assign(n, {});
+    curve.assign(n, {});
+    for (int i = 0; i < n; ++i) {
+      llg_problem& p = P[i];
+      if (p.drive && N > 0) drive_tab[i].assign(p.drive, p.drive + 3 * N + 3);
+      if (p.objective == LLG_J_CURVE) {
+        curve[i].step.assign(p.sample_step, p.sample_step + p.nsample);
+        curve[i].target.assign(p.sample_target, p.sample_target + p.nsample);
+        curve[i].weight.assign(p.sample_weight, p.sample_weight + p.nsample);
+      }
+      p.drive = nullptr;   // the caller's arrays are not kept
+      p.sample_step = nullptr;
+      p.sample_target = nullptr;
+      p.sample_weight = nullptr;
+    }
     long long node_off = 0, spec_off = 0, tens_off = 0;
     for (int i = 0; i < n; ++i) {
       const llg_problem& p = P[i];
@@ -484,6 +526,9 @@ struct Engine final : llg_ctx {
       d.A = p.A;
       d.area_target = p.area_target;
       d.penalty_w = p.penalty_w;
+      d.centre_w = p.objective == LLG_J_CURVE ? p.centre_w : 0.0;
+      d.centre_x0 = p.centre_target[0];
+      d.centre_y0 = p.centre_target[1];
       fill_coef(d);
       H[i] = d;
       const int rows = rows_per_tile(d.Lx);
@@ -524,7 +569,7 @@ struct Engine final : llg_ctx {
               alloc(&psib, total_nodes) && alloc(&psic, total_nodes) && alloc(&slots, (size_t)total_slots) &&
               alloc(&pslots, any_spec ? 2 * (size_t)total_slots : 2) && alloc(&Pd, (size_t)n * 2 * (N + 1)) &&
               alloc(&wtab, (size_t)n * 2 * (N + 1)) &&
-              alloc(&jterm, rt.size()) && alloc(&psitile, rt.size()) && alloc(&Jd, n) && alloc(&step_base, 1) &&
+              alloc(&jterm, rt.size()) && alloc(&psitile, rt.size()) && alloc(&psimom, 2 * rt.size()) && alloc(&Jd, n) && alloc(&step_base, 1) &&
               alloc(&maxbits, 2 * n) && alloc(&rf, (size_t)n * 3 * (N + 1)) && alloc(&errw, 1);
     if (!ok) return fail(LLG_ENOMEM, "device allocation failed (" + std::to_string(bytes >> 20) + " MiB so far)");
 
@@ -577,7 +622,8 @@ struct Engine final : llg_ctx {
         for (long long s = 0; s <= N; ++s)
           for (int c = 0; c < 3; ++c) {
             const double t = (double)s * dt + 0.5 * c * dt;
-            h[(size_t)i * 3 * (N + 1) + 3 * s + c] = P[i].b_rf * std::sin(2.0 * M_PI * P[i].f_rf * t);
+            h[(size_t)i * 3 * (N + 1) + 3 * s + c] =
+                drive_tab[i].empty() ? P[i].b_rf * std::sin(2.0 * M_PI * P[i].f_rf * t) : drive_tab[i][3 * s + c];
           }
       if ((e = cudaMemcpyAsync(rf, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, st)) !=
           cudaSuccess)
@@ -687,7 +733,7 @@ struct Engine final : llg_ctx {
     rows(a, ROW_FFT_ONLY);
   }
   void material(const T* phi) {
-    launch_material_tiles<T>(dI, dRT, (int)rt.size(), phi, psi, dpsi, psitile, st);
+    launch_material_tiles<T>(dI, dRT, (int)rt.size(), phi, psi, dpsi, psitile, psimom, st);
     ++nlaunch;
   }
 
@@ -809,26 +855,41 @@ struct Engine final : llg_ctx {
     return LLG_OK;
   }
 
-  // Spectral objective (Eq. 10 at the window's frequencies): the port series
-  // P_b[n] of the finished forward come to the host; J_b = sum_q |X_b(f_q)|
-  // and the per-step adjoint weights dJ/dP_b[n] / |box b| are formed in FP64
-  // there (a few thousand numbers per instance) and go back as wtab, which
-  // the terminal and adjoint kernels read.
+  // Spectral objective (Eq. 10 at the window's frequencies) and curve
+  // objective (Eq. 8): the series of the finished forward come to the host
+  // (port means P_b[n], or P[n] = sum psi m_comp / sum psi with sum psi);
+  // J and the per-step adjoint weights are formed there in FP64 (a few
+  // thousand numbers per instance) and go back as wtab, which the terminal
+  // and adjoint kernels read.
   llg_status spectral_weights() {
     const size_t len = (size_t)n * 2 * (N + 1);
     hP.assign(len, 0.0);
     hW.assign(len, 0.0);
     Jspec.assign(n, 0.0);
-    launch_port_series(dI, n, pslots, N + 1, Pd, st);
+    launch_port_series(dI, n, pslots, psitile, N + 1, Pd, st);
     ++nlaunch;
     cudaError_t e = cudaMemcpyAsync(hP.data(), Pd, sizeof(double) * len, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "spectral objective: port series");
     for (int i = 0; i < n; ++i) {
       const llg_problem& p = P[i];
-      if (p.objective != LLG_J_SPECTRAL) continue;
       const double* Pi = hP.data() + (size_t)i * 2 * (N + 1);
       double* Wi = hW.data() + (size_t)i * 2 * (N + 1);
+      if (p.objective == LLG_J_CURVE) {
+        // J = sum_j w_j |P_j - T_j|; dJ/dm_comp = W psi / S and the explicit
+        // dJ/dpsi = W (m_comp - P) / S at each sample, W = w sign(P - T)
+        const CurveSamples& cs = curve[i];
+        for (size_t j = 0; j < cs.step.size(); ++j) {
+          const long long k = cs.step[j];
+          const double Pk = Pi[2 * k], S = Pi[2 * k + 1], d = Pk - cs.target[j];
+          Jspec[i] += cs.weight[j] * std::fabs(d);
+          const double W = cs.weight[j] * (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0));
+          Wi[2 * k] = W / S;
+          Wi[2 * k + 1] = W * Pk / S;
+        }
+        continue;
+      }
+      if (p.objective != LLG_J_SPECTRAL) continue;
       for (int b = 0; b < 2; ++b) {
         const DevInst& d = H[i];
         const long long cnt = (long long)(d.boxes[b][1] - d.boxes[b][0]) * (d.boxes[b][3] - d.boxes[b][2]) * d.nz;
@@ -895,10 +956,11 @@ struct Engine final : llg_ctx {
       a.psic = psic;
       a.jterm = jterm;
       a.psitile = psitile;
+      a.psimom = psimom;
       a.wtab = wtab;
       rows(a, ROW_TERMINAL);
     }
-    launch_reduce_slots(dI, n, slots, N + 1, jterm, psitile, Jd, st);
+    launch_reduce_slots(dI, n, slots, N + 1, jterm, psitile, psimom, Jd, st);
     ++nlaunch;
     if (mT) cudaMemcpyAsync(mT, cur, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
     cudaEventRecord(ev1, st);

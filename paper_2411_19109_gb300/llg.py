@@ -19,9 +19,10 @@ import numpy as np
 from . import build as _build
 
 c_int, c_double, c_ll, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p
+_PD = ctypes.POINTER(c_double)
 
 LLG_OK, LLG_EINVAL, LLG_ENOMEM, LLG_ECUDA, LLG_ETIMEOUT, LLG_ENONFINITE, LLG_ESTATE = range(7)
-LLG_J_PORT, LLG_J_ENERGY_AREA, LLG_J_SPECTRAL = 0, 1, 2
+LLG_J_PORT, LLG_J_ENERGY_AREA, LLG_J_SPECTRAL, LLG_J_CURVE = 0, 1, 2, 3
 LLG_FP32, LLG_FP64 = 0, 1
 LLG_CKPT_STORE_ALL, LLG_CKPT_PERIODIC, LLG_CKPT_BINOMIAL = 0, 1, 2
 
@@ -48,7 +49,10 @@ class llg_problem(ctypes.Structure):
                 ("dt", c_double), ("nsteps", c_ll), ("sigmoid_a", c_double),
                 ("objective", c_int), ("comp", c_int), ("power", c_int),
                 ("boxes", (c_int * 4) * 2), ("weights", c_double * 2), ("n_from", c_ll),
-                ("area_target", c_double), ("penalty_w", c_double), ("nfreq", c_int), ("freqs", c_double * 8)]
+                ("area_target", c_double), ("penalty_w", c_double), ("nfreq", c_int), ("freqs", c_double * 8),
+                ("drive", _PD), ("nsample", c_int), ("sample_step", ctypes.POINTER(c_ll)),
+                ("sample_target", _PD), ("sample_weight", _PD), ("centre_w", c_double),
+                ("centre_target", c_double * 2)]
 
 
 class llg_options(ctypes.Structure):
@@ -141,6 +145,26 @@ def to_struct(p) -> llg_problem:
     fq = list(getattr(p, "freqs", ()))
     s.nfreq = len(fq)
     s.freqs[:min(len(fq), 8)] = fq[:8]
+    # host arrays: kept alive on the struct (the library copies them at create)
+    keep = []
+    drive = getattr(p, "drive", None)
+    if drive is not None:
+        a = (c_double * len(drive))(*drive)
+        keep.append(a)
+        s.drive = ctypes.cast(a, _PD)
+    steps = list(getattr(p, "sample_steps", ()))
+    if steps:
+        st_ = (c_ll * len(steps))(*steps)
+        tg = (c_double * len(steps))(*p.sample_targets)
+        wt = (c_double * len(steps))(*p.sample_weights)
+        keep += [st_, tg, wt]
+        s.sample_step = ctypes.cast(st_, ctypes.POINTER(c_ll))
+        s.sample_target = ctypes.cast(tg, _PD)
+        s.sample_weight = ctypes.cast(wt, _PD)
+    s.nsample = len(steps)
+    s.centre_w = getattr(p, "centre_w", 0.0)
+    s.centre_target[:] = list(getattr(p, "centre_target", (0.0, 0.0)))
+    s._keep = keep
     return s
 
 
@@ -155,7 +179,8 @@ def _check(lib, ctx, st):
 def llg_create(problems: Sequence, precision=LLG_FP32, ckpt=LLG_CKPT_PERIODIC, seg_len=0,
                stream=0, rows_per_cta=0, cols_per_cta=0, use_graph=0, time_kernels=0) -> int:
     lib = load()
-    arr = (llg_problem * len(problems))(*[to_struct(p) for p in problems])
+    structs = [to_struct(p) for p in problems]          # hold the host arrays until create returns
+    arr = (llg_problem * len(problems))(*structs)
     opt = llg_options(precision, ckpt, seg_len, use_graph, rows_per_cta, cols_per_cta, time_kernels)
     ctx = c_void_p()
     st = lib.llg_create(arr, len(problems), ctypes.byref(opt), c_void_p(stream), ctypes.byref(ctx))

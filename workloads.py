@@ -273,17 +273,19 @@ def thick512(nsteps: int = 50000, nx: int = 512, ny: int = 512, nz: int = 4) -> 
 
 
 def sw_particle(instance: int = 0, levels: int = 30, hold: int = 500, regularised: bool = False,
-                nx: int = 30, ny: int = 30) -> Instance:
+                nx: int = 32, ny: int = 30, design: int = 30) -> Instance:
     """Stoner-Wohlfarth hysteresis task (Eq. 8; Eq. 9 when `regularised`):
-    a 30 x 30 x 1 Permalloy mesh of 3 nm cells holding an initially circular
-    particle (radius 10 cells), a uniform field along x raised in `levels`
+    a 30 x 30 x 1 Permalloy design region of 3 nm cells (the mesh is nx = 32
+    wide, a multiple of 4 as the row FFTs need; columns x >= 30 are air,
+    Phi = -1, outside the design mask) holding an initially circular particle
+    (radius 10 cells), a uniform field along x raised in `levels`
     equal steps from 0 to 0.3 Ms (mu0 H), each level held `hold` RK4 steps
     (alpha 0.5, so the particle relaxes), and M_x/Ms = sum psi m_x / sum psi
     sampled at the end of levels j = 1..levels against the target 2 H_j/Ms
     with weights 1/(levels T_j) (zeta/(levels T_j), zeta = 10, with the size
-    penalty xi = 0.05 toward a one-cell-wide wire and the centre penalty
-    nu = 1 toward the mesh centre when `regularised`).  m0 = +y with 1e-3
-    seeded noise."""
+    penalty xi = 0.05 toward a one-cell-wide wire across the design region
+    and the centre penalty nu = 1 toward the design region's centre when
+    `regularised`).  m0 = +y with 1e-3 seeded noise."""
     rng = _rng(6, instance)
     h = 3e-9
     Ms = 8e5
@@ -301,15 +303,17 @@ def sw_particle(instance: int = 0, levels: int = 30, hold: int = 500, regularise
                 sample_steps=tuple(int(v) for v in (js + 1) * hold),
                 sample_targets=tuple(targets.tolist()),
                 sample_weights=tuple((zeta / (levels * targets)).tolist()),
-                area_target=1.0 / nx, penalty_w=0.05 if regularised else 0.0,
-                centre_w=1.0 if regularised else 0.0, centre_target=((nx - 1) / 2.0, (ny - 1) / 2.0))
+                area_target=design / (nx * ny), penalty_w=0.05 if regularised else 0.0,
+                centre_w=1.0 if regularised else 0.0, centre_target=((design - 1) / 2.0, (ny - 1) / 2.0))
     yy, xx = np.mgrid[0:ny, 0:nx]
-    r = np.hypot(xx - (nx - 1) / 2.0, yy - (ny - 1) / 2.0) * h
+    r = np.hypot(xx - (design - 1) / 2.0, yy - (ny - 1) / 2.0) * h
     R = 10 * h
     phi = (R - r) / R + 0.05 * rng.standard_normal((ny, nx))
-    phi = phi / np.abs(phi).max()
+    phi = phi / np.abs(phi[:, :design]).max()
+    phi[:, design:] = -1.0
     m0 = noisy_uniform_m0(rng, nx, ny, 1, direction=(0.0, 1.0, 0.0))
-    mask = np.ones((1, ny, nx), np.uint8)
+    mask = np.zeros((1, ny, nx), np.uint8)
+    mask[:, :, :design] = 1
     return Instance(p, phi[None], m0, mask, "sw_particle" + ("_reg" if regularised else ""))
 
 
