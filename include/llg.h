@@ -68,6 +68,7 @@ typedef enum {
 enum { LLG_J_PORT = 0, LLG_J_ENERGY_AREA = 1, LLG_J_SPECTRAL = 2, LLG_J_CURVE = 3 };
 enum { LLG_FP32 = 0, LLG_FP64 = 1 };
 enum { LLG_CKPT_STORE_ALL = 0, LLG_CKPT_PERIODIC = 1, LLG_CKPT_BINOMIAL = 2 };
+enum { LLG_INT_RK4 = 0, LLG_INT_DOPRI5 = 1 };
 
 /* One instance.  SI units (m, A/m, J/m, J/m^3, T, Hz, s). */
 typedef struct {
@@ -142,6 +143,22 @@ typedef struct {
   int rows_per_cta;/* reserved (tile rows follow from the row FFT length)      */
   int cols_per_cta;/* reserved (tile columns follow from the column FFT length) */
   int time_kernels;/* 1 = bracket every stage-kernel launch with CUDA events    */
+  int integrator;  /* LLG_INT_RK4: fixed step dt for nsteps steps.
+                      LLG_INT_DOPRI5: adaptive step size (Methods), the
+                      Dormand-Prince 5(4) pair from t = 0 to T = nsteps * dt
+                      with initial step dt; each instance has its own step
+                      size: err = sqrt(mean((psi e / (atol + rtol max(|psi
+                      m|, |psi y5|)))^2)) over nodes and components, accept
+                      if err <= 1, h <- h min(5, max(0.2, 0.9 err^-1/5)),
+                      the last step shortened to end at T.  At most nsteps
+                      accepted steps and 4 nsteps attempts per instance
+                      (LLG_ETIMEOUT beyond).  The gradient is the exact
+                      derivative over the accepted steps (their sizes held
+                      fixed), from a store-all checkpoint of every accepted
+                      step.  Needs the LLG_J_ENERGY_AREA objective and the
+                      sine drive (no drive table); ckpt and seg_len are
+                      ignored, use_graph replays captured attempts.          */
+  double rtol, atol; /* LLG_INT_DOPRI5 tolerances                            */
 } llg_options;
 
 typedef struct llg_ctx llg_ctx;
@@ -163,6 +180,13 @@ llg_status llg_create(const llg_problem* inst, int n_inst, const llg_options* op
  * Keeps the checkpoints that llg_adjoint needs. */
 llg_status llg_forward(llg_ctx* ctx, const void* phi_dev, const void* m0_dev,
                        double* J_host, void* mT_dev);
+
+/* LLG_INT_DOPRI5: the accepted steps (t_k, h_k) of instance `inst` in the
+ * last llg_forward, up to `cap` of them into the host arrays t_host, h_host;
+ * *count receives the number of accepted steps.  LLG_ESTATE without a
+ * forward pass or for the RK4 integrator, LLG_EINVAL for a bad instance. */
+llg_status llg_adaptive_steps(llg_ctx* ctx, int inst, double* t_host, double* h_host, long long cap,
+                              long long* count);
 
 /* Reverse sweep after llg_forward on the same inputs: writes dJ/dPhi
  * (all nodes, unmasked) to dJdphi_dev and, if non-NULL, dJ/dm0 to dJdm0_dev.

@@ -97,8 +97,91 @@ void launch_rows(const RowArgs<T>& a, int mode, int ntiles, size_t smem, cudaStr
     case ROW_FFT_ONLY: launch_rows_mode<T, ROW_FFT_ONLY>(a, ntiles, smem, st, z3); break;
     case ROW_STAGE: launch_rows_mode<T, ROW_STAGE>(a, ntiles, smem, st, z3); break;
     case ROW_FIELD: launch_rows_mode<T, ROW_FIELD>(a, ntiles, smem, st, z3); break;
+    case ROW_DP_STAGE: launch_rows_mode<T, ROW_DP_STAGE>(a, ntiles, smem, st, z3); break;
+    case ROW_DP_START: launch_rows_mode<T, ROW_DP_START>(a, ntiles, smem, st, z3); break;
     default: launch_rows_mode<T, ROW_TERMINAL>(a, ntiles, smem, st, z3); break;
   }
+}
+
+// Step control of the Dormand-Prince integrator, one block per instance:
+// err = sqrt(mean of the scaled squared errors of the attempt) from the
+// per-tile sums (added in a fixed order); accept if err <= 1 (then the step
+// (t, h) goes to the schedule, t advances, exactly to T_end on the last
+// step); h <- h min(5, max(0.2, 0.9 err^(-1/5))), shortened to end at T_end.
+// hst per instance: t, h, last (this attempt ends at T_end), done.
+__global__ void dp_control_kernel(const DevInst* inst, const double* eslots, double* hst, int* accept, int* cnt,
+                                  double* sched, long long max_steps, double T_end, int* overflow) {
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  const DevInst& I = inst[i];
+  double v = 0.0;
+  for (int k = threadIdx.x; k < I.ntile; k += blockDim.x) v += eslots[I.tile_off + k];
+  const double S = block_sum(v, red);
+  if (threadIdx.x != 0) return;
+  double* H = hst + 4 * i;
+  if (H[3] != 0.0) {
+    accept[i] = 0;
+    return;
+  }
+  const double err = sqrt(S / (3.0 * (double)I.nodes));
+  const bool ok = err <= 1.0;
+  double t = H[0], h = H[1];
+  if (ok) {
+    const long long k = cnt[i];
+    if (k >= max_steps) {
+      *overflow = 1;
+      H[1] = 0.0;
+      H[3] = 1.0;
+      accept[i] = 0;
+      return;
+    }
+    sched[2 * (k * gridDim.x + i)] = t;
+    sched[2 * (k * gridDim.x + i) + 1] = h;
+    cnt[i] = (int)(k + 1);
+    t = H[2] != 0.0 ? T_end : t + h;
+  }
+  const double fac = err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2)));
+  h *= fac;
+  if (ok && H[2] != 0.0) {
+    h = 0.0;
+    H[2] = 0.0;
+    H[3] = 1.0;
+  } else {
+    const bool last = h >= T_end - t;
+    if (last) h = T_end - t;
+    H[2] = last ? 1.0 : 0.0;
+  }
+  H[0] = t;
+  H[1] = h;
+  accept[i] = ok ? 1 : 0;
+}
+
+void launch_dp_control(const DevInst* inst, int n_inst, const double* eslots, double* hst, int* accept, int* cnt,
+                       double* sched, long long max_steps, double T_end, int* overflow, cudaStream_t st) {
+  dp_control_kernel<<<n_inst, 256, 0, st>>>(inst, eslots, hst, accept, cnt, sched, max_steps, T_end, overflow);
+}
+
+// Reverse step r of the adjoint sweep: each instance reverses its accepted
+// step k = cnt - 1 - r with the recorded (t_k, h_k), or idles (h = 0).
+__global__ void dp_reverse_state_kernel(int n_inst, const double* sched, const int* cnt, long long r, double* hst,
+                                        long long* slot) {
+  for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+    const long long k = (long long)cnt[i] - 1 - r;
+    if (k >= 0) {
+      hst[4 * i] = sched[2 * (k * n_inst + i)];
+      hst[4 * i + 1] = sched[2 * (k * n_inst + i) + 1];
+      slot[i] = k;
+    } else {
+      hst[4 * i] = 0.0;
+      hst[4 * i + 1] = 0.0;
+      slot[i] = -1;
+    }
+  }
+}
+
+void launch_dp_reverse_state(int n_inst, const double* sched, const int* cnt, long long r, double* hst,
+                             long long* slot, cudaStream_t st) {
+  dp_reverse_state_kernel<<<1, 256, 0, st>>>(n_inst, sched, cnt, r, hst, slot);
 }
 
 template <typename T>
@@ -109,6 +192,9 @@ void set_smem_limits(size_t stage, size_t misc, size_t cols, size_t adj) {
   smem_rows_mode<T, ROW_TERMINAL>(misc);
   smem_cols<T>(cols);
   smem_adj<T>(adj);
+  smem_rows_mode<T, ROW_DP_STAGE>(stage);
+  smem_rows_mode<T, ROW_DP_START>(misc);
+  smem_adj_dp<T>(adj);
 }
 
 template void launch_rows<float>(const RowArgs<float>&, int, int, size_t, cudaStream_t, bool);

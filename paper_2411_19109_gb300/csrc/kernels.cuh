@@ -12,6 +12,8 @@ enum RowMode : int {
   ROW_STAGE = 1,      // demag inverse + field + RK4 stage + next-stage spectrum
   ROW_FIELD = 2,      // effective field (or demag only) of Yin -> Bout
   ROW_TERMINAL = 3,   // energies / lambda_N / explicit dJ/dpsi at m_N = Yin
+  ROW_DP_STAGE = 4,   // demag inverse + field + Dormand-Prince stage + next-stage spectrum
+  ROW_DP_START = 5,   // apply the last attempt's acceptance, first DP stage input + spectrum
 };
 
 template <typename T>
@@ -42,6 +44,18 @@ struct RowArgs {
   double t_field;     // ROW_FIELD time
   double dt;
   long long n_from;
+  // Dormand-Prince stages (ROW_DP_STAGE, ROW_DP_START)
+  const double* hst;  // per instance: t, h, last, done of the current attempt
+  T* kbuf;            // slopes k_1..k_7, slot s-1 at kbuf + (s-1) * kstride
+  long long kstride;  // 3 x all nodes
+  T dpa[8];           // a(s+1, j), j = 1..s (stage s < 7); a(2, 1) for ROW_DP_START
+  T dpe[8];           // b_j - b*_j, j = 1..7 (stage 7)
+  double rtol, atol;  // error control (stage 7)
+  double* eslots;     // per row tile: sum of the scaled squared errors (stage 7)
+  const int* accept;  // ROW_DP_START: per instance, the last attempt was accepted
+  const int* cnt;     // ROW_DP_START: per instance, accepted steps so far (checkpoint slot)
+  T* ckall;           // ROW_DP_START: per accepted step, m (slot k at ckall + k * kstride); nullable
+  const T* y5;        // ROW_DP_START: the last attempt's fifth-order solution
   // ROW_TERMINAL outputs
   T* lam;             // lambda_N
   T* psib;            // dJ/dpsi accumulator (sum)
@@ -97,6 +111,12 @@ struct AdjArgs {
   int rows_max;
   double dt;
   long long n_from;
+  // Dormand-Prince adjoint stages (6..1)
+  const double* hst;  // per instance: t, h of the step being reversed (h = 0: idle)
+  T* ebuf;            // eta_1..eta_6 = (df/dY_s)^T kappa_s, slot s-1 at ebuf + (s-1) * kstride
+  long long kstride;
+  T dpb;              // b_{s-1} (b_6 for the seed)
+  T dpa[8];           // dpa[i] = a(i, s-1), i = s..6
 };
 
 template <typename T>
@@ -138,6 +158,18 @@ template <typename T>
 void smem_cols(size_t smem);
 template <typename T>
 void smem_adj(size_t smem);
+// Dormand-Prince adjoint stages, reverse-sweep gather, and step control
+template <typename T>
+void launch_adj_dp(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3);
+template <typename T>
+void smem_adj_dp(size_t smem);
+template <typename T>
+void launch_dp_gather(const DevInst* inst, const RowTile* tiles, int ntiles, const T* ckall, long long kstride,
+                      const long long* slot, T* out, cudaStream_t st);
+void launch_dp_control(const DevInst* inst, int n_inst, const double* eslots, double* hst, int* accept, int* cnt,
+                       double* sched, long long max_steps, double T_end, int* overflow, cudaStream_t st);
+void launch_dp_reverse_state(int n_inst, const double* sched, const int* cnt, long long r, double* hst,
+                             long long* slot, cudaStream_t st);
 template <typename T>
 void set_smem_limits(size_t stage, size_t misc, size_t cols, size_t adj);
 template <typename T>

@@ -19,6 +19,7 @@
 
 #include "kernels.cuh"
 #include "regfft.cuh"
+#include "dopri.cuh"
 #include "tma.cuh"
 
 namespace llg {
@@ -413,11 +414,17 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
   const T ku[3] = {K.ku[0], K.ku[1], K.ku[2]};
   load_twiddles(tw2, a.tw, 2 * L);
   __syncthreads();
-  if (MODE != ROW_FFT_ONLY) {
+  if (MODE != ROW_FFT_ONLY && MODE != ROW_DP_START) {
     C v[8];
     row_inverse_comp<T, L>(v, row + g.c * L, active, grp, g.t, tw2);
     __syncthreads();
   }
+  // Dormand-Prince attempt start: this instance's acceptance of the last
+  // attempt (then m <- y5, k_1 <- k_7, m stored at checkpoint slot cnt) and
+  // the first stage input Y_2 = m + h a(2, 1) k_1
+  const bool dp_acc = MODE == ROW_DP_START && a.accept[tile.inst] != 0;
+  const T dp_h = MODE == ROW_DP_START ? (T)a.hst[4 * tile.inst + 1] : (T)0;
+  const long long dp_slot = MODE == ROW_DP_START && a.ckall ? (long long)a.cnt[tile.inst] * a.kstride : -1;
   double vsum = 0.0;
 #pragma unroll 1
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
@@ -427,6 +434,28 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
       const T p = ps[n0];
 #pragma unroll
       for (int c = 0; c < 3; ++c) sEr[2 * c * GS + sl] = Ms * p * Y[c * nodes + n0];
+      continue;
+    }
+    if (MODE == ROW_DP_START) {
+      const T p = ps[n0];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const long long id = off3 + c * nodes + n0;
+        T mv, k1;
+        if (dp_acc) {
+          mv = a.y5[id];
+          k1 = a.kbuf[6 * a.kstride + id];
+          a.mout[id] = mv;
+          a.kbuf[id] = k1;
+          if (dp_slot >= 0) a.ckall[dp_slot + id] = mv;
+        } else {
+          mv = a.m[id];
+          k1 = a.kbuf[id];
+        }
+        const T y2 = mv + dp_h * a.dpa[0] * k1;
+        a.Yout[id] = y2;
+        sEr[2 * c * GS + sl] = Ms * p * y2;
+      }
       continue;
     }
     T Bd[3];
@@ -558,7 +587,7 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
 // rows][psi halo (R+2) rows][m 3 x R rows][acc 3 x R rows][W_{2L}^k, k < 2L].
 // ---------------------------------------------------------------------------
 
-template <typename T, int L, bool Z3>
+template <typename T, int L, bool Z3, bool DP>
 __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I, const RowTile& tile,
                                            unsigned char* smem_raw, uint64_t* bars, double* red, T rf) {
   using C = cplx<T>;
@@ -625,10 +654,14 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
   const T hs = (s == 1 || s == 2) ? (T)0.5 * dt : dt;     // Y_{s+1} = m + hs k_s
   const int cs = (RM + 2) * nx;                            // component stride of the staged halo
   double vsum = 0.0;
-  const bool objective_step = s == 4 && a.slots != nullptr && I.objective == 0 && (n + 1) >= a.n_from;
+  // Dormand-Prince: this instance's step size h, the slope slots, and the
+  // error sum of stage 7
+  const T hdp = DP ? (T)a.hst[4 * tile.inst + 1] : (T)0;
+  double esum = 0.0;
+  const bool objective_step = !DP && s == 4 && a.slots != nullptr && I.objective == 0 && (n + 1) >= a.n_from;
   // spectral objective: the port-box sums of m_comp at step n + 1; curve
   // objective: the tile's sum of psi m_comp (channel 0) at every step
-  const bool spectral_step = s == 4 && a.pslots != nullptr &&
+  const bool spectral_step = !DP && s == 4 && a.pslots != nullptr &&
                              ((I.objective == 2 && (n + 1) >= a.n_from) || I.objective == 3);
   double psum[2] = {0.0, 0.0};
 #pragma unroll 1
@@ -643,7 +676,7 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
     for (int c = 0; c < 3; ++c) {
       const long long id = off3 + c * nodes + n0;
       mn[c] = gm[id];
-      ac[c] = s > 1 ? gacc[id] : (T)0;
+      ac[c] = (!DP && s > 1) ? gacc[id] : (T)0;
     }
     const T pi = sP[oi];
     T yi[3], B[3];
@@ -685,6 +718,34 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
     T k[3], al, ga;
     damping_at(I, K, x, y, al, ga);
     llg_rhs(yi, B, al, ga, k);
+    if constexpr (DP) {
+      // k_s into its slot; then Y_{s+1} = m + h sum_{j<=s} a(s+1, j) k_j, or
+      // at stage 7 (Y_7 = y5) the error h sum_j e_j k_j scaled per node and
+      // component by atol + rtol max(|psi m|, |psi y5|), measured on psi e
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const long long id = off3 + c * nodes + n0;
+        if (gB) gB[id] = B[c];
+        a.kbuf[(long long)(s - 1) * a.kstride + id] = k[c];
+        if (s < 7) {
+          T acc2 = a.dpa[s - 1] * k[c];
+          for (int j = 1; j < s; ++j)
+            if (a.dpa[j - 1] != (T)0) acc2 += a.dpa[j - 1] * a.kbuf[(long long)(j - 1) * a.kstride + id];
+          const T yv = mn[c] + hdp * acc2;
+          gYout[id] = yv;
+          sEr[2 * c * GS + sl] = Ms * pi * yv;
+        } else {
+          T ec = a.dpe[6] * k[c];
+          for (int j = 1; j < 7; ++j)
+            if (a.dpe[j - 1] != (T)0) ec += a.dpe[j - 1] * a.kbuf[(long long)(j - 1) * a.kstride + id];
+          const double p = (double)pi;
+          const double sc = a.atol + a.rtol * fmax(fabs(p * (double)mn[c]), fabs(p * (double)yi[c]));
+          const double r = p * (double)hdp * (double)ec / sc;
+          esum += r * r;
+        }
+      }
+      continue;
+    }
     T yn[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -732,6 +793,11 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
       if (threadIdx.x == 0) a.slots[I.slot_off + (long long)(n + 1) * I.ntile + tile.k] = tot;
     }
   }
+  if (DP && s == 7) {
+    const double tot = block_sum(esum, red);
+    if (threadIdx.x == 0) a.eslots[I.tile_off + tile.k] = tot;
+    return;   // no next stage: no spectrum to form
+  }
   if (spectral_step) {
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
@@ -750,18 +816,18 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
 
 // Stage body for the row FFT length of the tile's instance; Z3 selects the
 // 3D variant (z neighbours), so film tiles carry none of its registers.
-template <typename T, bool Z3>
+template <typename T, bool Z3, bool DP>
 __device__ __forceinline__ void stage_dispatch(const RowArgs<T>& a, const DevInst& I, const RowTile& tile,
                                                unsigned char* smem_raw, uint64_t* bars, double* red, T rf) {
   switch (I.log2Lx) {
-    case 3: stage_body<T, 8, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
-    case 4: stage_body<T, 16, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
-    case 5: stage_body<T, 32, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
-    case 6: stage_body<T, 64, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
-    case 7: stage_body<T, 128, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
-    case 8: stage_body<T, 256, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
-    case 9: stage_body<T, 512, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
-    case 10: stage_body<T, 1024, Z3>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 3: stage_body<T, 8, Z3, DP>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 4: stage_body<T, 16, Z3, DP>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 5: stage_body<T, 32, Z3, DP>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 6: stage_body<T, 64, Z3, DP>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 7: stage_body<T, 128, Z3, DP>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 8: stage_body<T, 256, Z3, DP>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 9: stage_body<T, 512, Z3, DP>(a, I, tile, smem_raw, bars, red, rf); break;
+    case 10: stage_body<T, 1024, Z3, DP>(a, I, tile, smem_raw, bars, red, rf); break;
     default: break;
   }
 }
@@ -769,7 +835,8 @@ __device__ __forceinline__ void stage_dispatch(const RowArgs<T>& a, const DevIns
 // Z3: the 3D variant (z neighbours); film tiles launch the variant without
 // them, which needs fewer registers.
 template <typename T, int MODE, bool Z3>
-__global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? (Z3 ? 2 : 3) : 1) rows_kernel(RowArgs<T> a) {
+__global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? ((Z3 || MODE >= ROW_DP_STAGE) ? 2 : 3) : 1)
+    rows_kernel(RowArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[kRowThreads / 32];
@@ -786,6 +853,10 @@ __global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? (Z3 ? 2 : 3) : 1
       const long long n = (a.step_base ? *a.step_base : 0) + a.local_step;
       const int c = (a.stage == 1) ? 0 : (a.stage == 4 ? 2 : 1);
       s_rf = a.rf[sI.rf_off + 3 * n + c];
+    } else if (MODE == ROW_DP_STAGE) {
+      // the sine drive at the stage time t + c_s h of this instance's attempt
+      const double t0 = a.hst[4 * tile.inst], h = a.hst[4 * tile.inst + 1];
+      s_rf = sI.b_rf * sin(2.0 * M_PI * sI.f_rf * (t0 + dp::c(a.stage) * h));
     } else {
       s_rf = 0.0;
     }
@@ -793,8 +864,8 @@ __global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? (Z3 ? 2 : 3) : 1
   __syncthreads();
   C* sm = reinterpret_cast<C*>(smem_raw);
   const T rf = (T)s_rf;
-  if (MODE == ROW_STAGE) {
-    stage_dispatch<T, Z3>(a, sI, tile, smem_raw, bars, red, rf);
+  if (MODE == ROW_STAGE || MODE == ROW_DP_STAGE) {
+    stage_dispatch<T, Z3, MODE == ROW_DP_STAGE>(a, sI, tile, smem_raw, bars, red, rf);
     return;
   }
   switch (sI.log2Lx) {
@@ -819,7 +890,7 @@ __global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? (Z3 ? 2 : 3) : 1
 // [W_{2L}^k, k < 2L].
 // ---------------------------------------------------------------------------
 
-template <typename T, int L, bool Z3>
+template <typename T, int L, bool Z3, bool DP>
 __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, const RowTile& tile,
                                          unsigned char* smem_raw, uint64_t* bars) {
   using C = cplx<T>;
@@ -852,6 +923,15 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   const T ku[3] = {K.ku[0], K.ku[1], K.ku[2]};
   const T dt = (T)a.dt;
   T ca = 0, cb = 0;   // u_{s-1} = ca lambda + cb g_s
+  // Dormand-Prince: this instance's step size (0: idle in this reverse step)
+  const T hdp = DP ? (T)a.hst[4 * tile.inst + 1] : (T)0;
+  // per-step adjoint weights of the spectral and curve objectives at stage 1
+  // of step n: one pair per block, converted once (no FP64 work per node)
+  T ow0 = 0, ow1 = 0;
+  if (!DP && s == 1 && a.wtab && ((I.objective == 2 && n >= a.n_from) || I.objective == 3)) {
+    ow0 = (T)a.wtab[I.wt_off + 2 * n];
+    ow1 = (T)a.wtab[I.wt_off + 2 * n + 1];
+  }
   if (s == 4) { ca = dt / (T)3; cb = dt; }
   else if (s == 3) { ca = dt / (T)3; cb = (T)0.5 * dt; }
   else if (s == 2) { ca = dt / (T)6; cb = (T)0.5 * dt; }
@@ -914,7 +994,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
       lam[c] = glam[id];
       if (!seed) {
         gg[c] = ggp[id];
-        gsum[c] = s < 4 ? gG[id] : (T)0;
+        gsum[c] = (!DP && s < 4) ? gG[id] : (T)0;
       }
       if (emit) {
         yp[c] = gYp[id];
@@ -928,7 +1008,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
     T u[3];
     if (seed) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) u[c] = dt / (T)6 * lam[c];
+      for (int c = 0; c < 3; ++c) u[c] = DP ? hdp * a.dpb * lam[c] : dt / (T)6 * lam[c];
     } else {
       const int oi = (g.rl + 1) * nx + x;
       const T pi = sP[oi];
@@ -990,8 +1070,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
       qpsi += Ms * dot3(yi, D);
       if (s == 1 && I.objective == 3) {
         // curve sample at step n: the quotient-rule term of P = sum psi m / sum psi
-        const double wl = a.wtab[I.wt_off + 2 * n];
-        qpsi += (T)(wl * (double)yi[I.comp] - a.wtab[I.wt_off + 2 * n + 1]);
+        qpsi += ow0 * yi[I.comp] - ow1;
       }
       kahan_add(qs, qc, qpsi);
       gpsib[I.node_off + n0] = qs;
@@ -999,7 +1078,15 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const long long id = off3 + c * nodes + n0;
-        if (s == 4) {
+        if constexpr (DP) {
+          // eta_s to its slot; at stage 1 lambda_k = lambda_{k+1} + sum_s eta_s
+          a.ebuf[(long long)(s - 1) * a.kstride + id] = gg[c];
+          if (s == 1) {
+            T sum = gg[c];
+            for (int i = 2; i <= 6; ++i) sum += a.ebuf[(long long)(i - 1) * a.kstride + id];
+            lam[c] += sum;
+          }
+        } else if (s == 4) {
           gG[id] = gg[c];
         } else if (s > 1) {
           gG[id] = gsum[c] + gg[c];
@@ -1016,17 +1103,27 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
             lam[I.comp] += K.wbox[b] * (I.power == 2 ? (T)2 * vv : (T)1);
           }
         } else if (I.objective == 2 && n >= a.n_from) {
-#pragma unroll
-          for (int b = 0; b < 2; ++b)
-            if (in_box(I.boxes[b], x, y)) lam[I.comp] += (T)a.wtab[I.wt_off + 2 * n + b];
+          if (in_box(I.boxes[0], x, y)) lam[I.comp] += ow0;
+          if (in_box(I.boxes[1], x, y)) lam[I.comp] += ow1;
         } else if (I.objective == 3) {
-          lam[I.comp] += (T)(a.wtab[I.wt_off + 2 * n] * (double)pi);
+          lam[I.comp] += ow0 * pi;
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) glam[off3 + c * nodes + n0] = lam[c];
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) u[c] = (s > 1) ? ca * lam[c] + cb * gg[c] : dt / (T)6 * lam[c];
+      for (int c = 0; c < 3; ++c) {
+        if constexpr (DP) {
+          // kappa_{s-1} = h (b_{s-1} lambda + sum_{i >= s} a(i, s-1) eta_i)
+          T kap = a.dpb * lam[c] + a.dpa[s] * gg[c];
+          const long long id = off3 + c * nodes + n0;
+          for (int i = s + 1; i <= 6; ++i)
+            if (a.dpa[i] != (T)0) kap += a.dpa[i] * a.ebuf[(long long)(i - 1) * a.kstride + id];
+          u[c] = hdp * kap;
+        } else {
+          u[c] = (s > 1) ? ca * lam[c] + cb * gg[c] : dt / (T)6 * lam[c];
+        }
+      }
     }
     if (!emit) continue;
     T bbar[3], gl[3], al, ga;
@@ -1051,18 +1148,18 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
                          tw2);
 }
 
-template <typename T, bool Z3>
+template <typename T, bool Z3, bool DP>
 __device__ __forceinline__ void adj_dispatch(const AdjArgs<T>& a, const DevInst& I, const RowTile& tile,
                                              unsigned char* smem_raw, uint64_t* bars) {
   switch (I.log2Lx) {
-    case 3: adj_body<T, 8, Z3>(a, I, tile, smem_raw, bars); break;
-    case 4: adj_body<T, 16, Z3>(a, I, tile, smem_raw, bars); break;
-    case 5: adj_body<T, 32, Z3>(a, I, tile, smem_raw, bars); break;
-    case 6: adj_body<T, 64, Z3>(a, I, tile, smem_raw, bars); break;
-    case 7: adj_body<T, 128, Z3>(a, I, tile, smem_raw, bars); break;
-    case 8: adj_body<T, 256, Z3>(a, I, tile, smem_raw, bars); break;
-    case 9: adj_body<T, 512, Z3>(a, I, tile, smem_raw, bars); break;
-    case 10: adj_body<T, 1024, Z3>(a, I, tile, smem_raw, bars); break;
+    case 3: adj_body<T, 8, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 4: adj_body<T, 16, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 5: adj_body<T, 32, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 6: adj_body<T, 64, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 7: adj_body<T, 128, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 8: adj_body<T, 256, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 9: adj_body<T, 512, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 10: adj_body<T, 1024, Z3, DP>(a, I, tile, smem_raw, bars); break;
     default: break;
   }
 }
@@ -1075,7 +1172,19 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? 2 : 1) adj_kerne
   const RowTile tile = a.tiles[blockIdx.x];
   load_inst(sI, a.inst + tile.inst);
   __syncthreads();
-  adj_dispatch<T, Z3>(a, sI, tile, smem_raw, bars);
+  adj_dispatch<T, Z3, false>(a, sI, tile, smem_raw, bars);
+}
+
+// adjoint stage of a Dormand-Prince step (stages 6..1; the seed at stage 6)
+template <typename T, bool Z3>
+__global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? 2 : 1) adj_dp_kernel(AdjArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ DevInst sI;
+  __shared__ uint64_t bars[2];
+  const RowTile tile = a.tiles[blockIdx.x];
+  load_inst(sI, a.inst + tile.inst);
+  __syncthreads();
+  adj_dispatch<T, Z3, true>(a, sI, tile, smem_raw, bars);
 }
 
 // ---------------------------------------------------------------------------
@@ -1209,6 +1318,40 @@ void smem_adj(size_t smem) {
   static size_t cur = 0, cur3 = 0;
   raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, false>), &cur, smem);
   raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, true>), &cur3, smem);
+}
+template <typename T>
+void launch_adj_dp(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3) {
+  if (z3) adj_dp_kernel<T, true><<<ntiles, kAdjThreads, smem, st>>>(a);
+  else adj_dp_kernel<T, false><<<ntiles, kAdjThreads, smem, st>>>(a);
+}
+template <typename T>
+void smem_adj_dp(size_t smem) {
+  static size_t cur = 0, cur3 = 0;
+  raise_smem_limit(reinterpret_cast<const void*>(adj_dp_kernel<T, false>), &cur, smem);
+  raise_smem_limit(reinterpret_cast<const void*>(adj_dp_kernel<T, true>), &cur3, smem);
+}
+
+// Dormand-Prince reverse sweep: the state m_k of each instance's step being
+// reversed, from its checkpoint slot (slot[inst] < 0: idle, nothing copied)
+template <typename T>
+__global__ void dp_gather_kernel(const DevInst* inst, const RowTile* tiles, const T* ckall, long long kstride,
+                                 const long long* slot, T* out) {
+  const RowTile tile = tiles[blockIdx.x];
+  const DevInst& I = inst[tile.inst];
+  const long long k = slot[tile.inst];
+  if (k < 0) return;
+  const long long base = tile_base(I, tile);
+  const int cnt = tile.nrows * I.nx;
+  for (int c = 0; c < 3; ++c)
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const long long id = 3 * I.node_off + (long long)c * I.nodes + (base - I.node_off) + e;
+      out[id] = ckall[k * kstride + id];
+    }
+}
+template <typename T>
+void launch_dp_gather(const DevInst* inst, const RowTile* tiles, int ntiles, const T* ckall, long long kstride,
+                      const long long* slot, T* out, cudaStream_t st) {
+  dp_gather_kernel<T><<<ntiles, 256, 0, st>>>(inst, tiles, ckall, kstride, slot, out);
 }
 template <typename T>
 void launch_material_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* phi, T* psi,

@@ -25,6 +25,7 @@
 #include "kernels.cuh"
 #include "llg.h"
 #include "regfft.cuh"
+#include "dopri.cuh"
 
 using namespace llg;
 
@@ -163,6 +164,7 @@ struct llg_ctx {
   virtual ~llg_ctx() {}
   virtual llg_status forward(const void* phi, const void* m0, double* J, void* mT) = 0;
   virtual llg_status adjoint(void* dphi, void* dm0) = 0;
+  virtual llg_status adaptive_steps(int inst, double* t, double* h, long long cap, long long* count) = 0;
   virtual llg_status levelset(void* phi, const void* grad, const unsigned char* mask, double lr) = 0;
   virtual llg_status field(const void* phi, const void* m, double t, int demag_only, void* B) = 0;
   virtual size_t device_bytes() const = 0;
@@ -224,6 +226,18 @@ struct Engine final : llg_ctx {
   };
   std::vector<CurveSamples> curve;
   double* psimom = nullptr;   // per row tile: sum psi x, sum psi y
+  // Dormand-Prince integrator: slopes k_1..k_7, the fifth-order solution,
+  // store-all checkpoints of the accepted steps, the reverse sweep's stage
+  // record and eta slots, per-tile error sums, per-instance step state
+  // (t, h, last, done), acceptance, accepted-step counts and schedule
+  bool dp_mode = false;
+  long long dp_maxK = 0;
+  T *dp_k = nullptr, *dp_y5 = nullptr, *dp_ck = nullptr, *dp_recY = nullptr, *dp_recB = nullptr;
+  T *dp_eta = nullptr, *dp_mrev = nullptr;
+  double *dp_e = nullptr, *dp_hst = nullptr, *dp_sched = nullptr;
+  int *dp_acc = nullptr, *dp_cnt = nullptr, *dp_ovf = nullptr;
+  long long* dp_slot = nullptr;
+  std::vector<int> dp_cnt_h;
   long long total_slots = 0;
   long long* step_base = nullptr;
   unsigned int* maxbits = nullptr;
@@ -343,6 +357,15 @@ struct Engine final : llg_ctx {
     st = stream;
     opt = *o;
     P.assign(probs, probs + n_inst);
+    if (opt.integrator != LLG_INT_RK4 && opt.integrator != LLG_INT_DOPRI5) return fail(LLG_EINVAL, "unknown integrator");
+    dp_mode = opt.integrator == LLG_INT_DOPRI5;
+    if (dp_mode) {
+      if (!(opt.rtol > 0 && opt.atol > 0 && std::isfinite(opt.rtol) && std::isfinite(opt.atol)))
+        return fail(LLG_EINVAL, "the adaptive integrator needs finite rtol > 0 and atol > 0");
+      for (int i = 0; i < n_inst; ++i)
+        if (probs[i].objective != LLG_J_ENERGY_AREA || probs[i].drive)
+          return fail(LLG_EINVAL, "the adaptive integrator needs the LLG_J_ENERGY_AREA objective and the sine drive");
+    }
     N = P[0].nsteps;
     n_from = P[0].n_from;
     dt = P[0].dt;
@@ -572,6 +595,18 @@ struct Engine final : llg_ctx {
               alloc(&jterm, rt.size()) && alloc(&psitile, rt.size()) && alloc(&psimom, 2 * rt.size()) && alloc(&Jd, n) && alloc(&step_base, 1) &&
               alloc(&maxbits, 2 * n) && alloc(&rf, (size_t)n * 3 * (N + 1)) && alloc(&errw, 1);
     if (!ok) return fail(LLG_ENOMEM, "device allocation failed (" + std::to_string(bytes >> 20) + " MiB so far)");
+    if (dp_mode) {
+      const long long K7 = 7, R6 = 6;
+      dp_maxK = N;
+      const bool ok2 = alloc(&dp_k, S * K7) && alloc(&dp_y5, S) && alloc(&dp_ck, S * (N + 1)) &&
+                       alloc(&dp_recY, S * R6) && alloc(&dp_recB, S * R6) && alloc(&dp_eta, S * R6) &&
+                       alloc(&dp_mrev, S) && alloc(&dp_e, rt.size()) && alloc(&dp_hst, 4 * (size_t)n) &&
+                       alloc(&dp_sched, 2 * (size_t)n * std::max(1LL, N)) && alloc(&dp_acc, n) && alloc(&dp_cnt, n) &&
+                       alloc(&dp_ovf, 1) && alloc(&dp_slot, n);
+      if (!ok2)
+        return fail(LLG_ENOMEM, "device allocation failed for the adaptive integrator's store-all checkpoints (" +
+                                    std::to_string(bytes >> 20) + " MiB so far)");
+    }
 
     cudaError_t e;
     if ((e = cudaMemcpyAsync(dI, H.data(), sizeof(DevInst) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -681,7 +716,7 @@ struct Engine final : llg_ctx {
   }
   void rows(const RowArgs<T>& a0, int mode) {
     RowArgs<T> a = a0;
-    const size_t sm = mode == ROW_STAGE ? smem_rows : smem_misc;
+    const size_t sm = (mode == ROW_STAGE || mode == ROW_DP_STAGE) ? smem_rows : smem_misc;
     if (mode == ROW_STAGE) time_begin(0);
     if (!rt2.empty()) {
       a.tiles = dRT2;
@@ -918,8 +953,246 @@ struct Engine final : llg_ctx {
   }
 
   // ------------------------------------------------------------ forward
+  // ------------------------------------------------ Dormand-Prince forward
+  // Kernel arguments of DP stage s (1..7): the combination a(s+1, j) of the
+  // next stage input, or at s = 7 the error weights b_j - b*_j.
+  RowArgs<T> dp_args(int s) {
+    RowArgs<T> a = row_args();
+    a.hst = dp_hst;
+    a.kbuf = dp_k;
+    a.kstride = (long long)slot();
+    a.stage = s;
+    if (s < 7)
+      for (int j = 1; j <= s; ++j) a.dpa[j - 1] = (T)dp::a(s + 1, j);
+    else
+      for (int j = 1; j <= 7; ++j) a.dpe[j - 1] = (T)dp::e(j);
+    a.rtol = opt.rtol;
+    a.atol = opt.atol;
+    a.eslots = dp_e;
+    return a;
+  }
+  // stage s: field and slope at Y_s (whose spectrum the last row pass left),
+  // next stage input Y_{s+1} and its spectrum (s < 7)
+  void dp_stage(int s, const T* Yin, const T* mm, T* Yout, T* Bout) {
+    cols();
+    RowArgs<T> a = dp_args(s);
+    a.Yin = Yin;
+    a.m = mm;
+    a.Yout = Yout;
+    a.Bout = Bout;
+    rows(a, ROW_DP_STAGE);
+  }
+  // apply the controller's decision (m <- y5, k_1 <- k_7, checkpoint) and
+  // form Y_2 = m + h a(2, 1) k_1 with its spectrum
+  void dp_start() {
+    RowArgs<T> a = row_args();
+    a.hst = dp_hst;
+    a.kbuf = dp_k;
+    a.kstride = (long long)slot();
+    a.dpa[0] = (T)dp::a(2, 1);
+    a.accept = dp_acc;
+    a.cnt = dp_cnt;
+    a.ckall = dp_ck;
+    a.y5 = dp_y5;
+    a.m = m;
+    a.mout = m;
+    a.Yin = m;
+    a.Yout = Ya;
+    rows(a, ROW_DP_START);
+  }
+  void dp_attempt() {
+    dp_stage(2, Ya, m, Yb, nullptr);
+    dp_stage(3, Yb, m, Ya, nullptr);
+    dp_stage(4, Ya, m, Yb, nullptr);
+    dp_stage(5, Yb, m, Ya, nullptr);
+    dp_stage(6, Ya, m, dp_y5, nullptr);
+    dp_stage(7, dp_y5, m, nullptr, nullptr);
+    launch_dp_control(dI, n, dp_e, dp_hst, dp_acc, dp_cnt, dp_sched, dp_maxK, (double)N * dt, dp_ovf, st);
+    ++nlaunch;
+    dp_start();
+  }
+
+  llg_status forward_dp(const T* phi, const void* m0_v, double* J, void* mT) {
+    cudaEventRecord(ev0, st);
+    material(phi);
+    cudaMemcpyAsync(m, m0_v, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(dp_ck, m0_v, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(jterm, 0, sizeof(double) * rt.size(), st);
+    cudaMemsetAsync(slots, 0, sizeof(double) * total_slots, st);
+    cudaMemsetAsync(dp_acc, 0, sizeof(int) * n, st);
+    cudaMemsetAsync(dp_cnt, 0, sizeof(int) * n, st);
+    cudaMemsetAsync(dp_ovf, 0, sizeof(int), st);
+    const double Tend = (double)N * dt;
+    {
+      std::vector<double> h0(4 * (size_t)n);
+      for (int i = 0; i < n; ++i) {
+        const bool last = dt >= Tend;
+        h0[4 * i] = 0.0;
+        h0[4 * i + 1] = N > 0 ? (last ? Tend : dt) : 0.0;
+        h0[4 * i + 2] = last ? 1.0 : 0.0;
+        h0[4 * i + 3] = N > 0 ? 0.0 : 1.0;
+      }
+      cudaError_t e = cudaMemcpyAsync(dp_hst, h0.data(), sizeof(double) * h0.size(), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "adaptive integrator: initial state");
+    }
+    // first attempt: k_1 = f(m, 0) and Y_2
+    fft_only(m);
+    dp_stage(1, m, m, Ya, nullptr);
+    const long long max_att = 4 * std::max(1LL, N);
+    std::vector<double> hh(4 * (size_t)n);
+    int ovf = 0;
+    bool done = N == 0;
+    for (long long att = 0; !done && att < max_att;) {
+      for (int k = 0; k < 4; ++k, ++att) dp_attempt();
+      cudaMemcpyAsync(hh.data(), dp_hst, sizeof(double) * hh.size(), cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(&ovf, dp_ovf, sizeof(int), cudaMemcpyDeviceToHost, st);
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "adaptive integrator");
+      done = true;
+      for (int i = 0; i < n; ++i) done &= hh[4 * i + 3] != 0.0;
+      if (ovf) return fail(LLG_ETIMEOUT, "adaptive integrator: more than nsteps accepted steps");
+    }
+    if (!done) return fail(LLG_ETIMEOUT, "adaptive integrator: no end of the interval within 4 nsteps attempts");
+    dp_cnt_h.assign(n, 0);
+    cudaMemcpyAsync(dp_cnt_h.data(), dp_cnt, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+    // terminal: field of m_T, energies, lambda_T, explicit dJ/dpsi
+    fft_only(m);
+    cols();
+    {
+      RowArgs<T> a = row_args();
+      a.Yin = m;
+      a.lam = lam;
+      a.psib = psib;
+      a.psic = psic;
+      a.jterm = jterm;
+      a.psitile = psitile;
+      a.psimom = psimom;
+      a.wtab = wtab;
+      rows(a, ROW_TERMINAL);
+    }
+    launch_reduce_slots(dI, n, slots, N + 1, jterm, psitile, psimom, Jd, st);
+    ++nlaunch;
+    mN_ptr = m;
+    if (mT) cudaMemcpyAsync(mT, m, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
+    cudaEventRecord(ev1, st);
+    cudaMemcpyAsync(J, Jd, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    int herr = 0;
+    cudaMemcpyAsync(&herr, errw, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "llg_forward");
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "llg_forward");
+    time_drain();
+    if (herr) return fail(LLG_ETIMEOUT, "a bounded device wait ran out in llg_forward");
+    float f = 0.f;
+    cudaEventElapsedTime(&f, ev0, ev1);
+    ms = f;
+    have_fwd = true;
+    for (int i = 0; i < n; ++i)
+      if (!std::isfinite(J[i])) return fail(LLG_ENONFINITE, "J is not finite for instance " + std::to_string(i));
+    return LLG_OK;
+  }
+
+  // reverse sweep over the accepted steps: per reverse index r, instance i
+  // reverses its step cnt_i - 1 - r (or idles with h = 0): recompute the six
+  // stages from its checkpoint, seed kappa_6 = h b_6 lambda, then adjoint
+  // stages 6..1 (eta_s kept for the lower stages, lambda += sum eta at 1)
+  llg_status adjoint_dp(void* dphi, void* dm0) {
+    cudaEventRecord(ev0, st);
+    long long Kmax = 0;
+    for (int i = 0; i < n; ++i) Kmax = std::max(Kmax, (long long)dp_cnt_h[i]);
+    const long long S = (long long)slot();
+    auto Yrec = [&](int s) { return dp_recY + (long long)(s - 1) * S; };   // Y_s, s = 2..6 (Y_1 = mrev)
+    auto Brec = [&](int s) { return dp_recB + (long long)(s - 1) * S; };
+    auto Ys = [&](int s) -> T* { return s == 1 ? dp_mrev : Yrec(s); };
+    for (long long r = 0; r < Kmax; ++r) {
+      launch_dp_reverse_state(n, dp_sched, dp_cnt, r, dp_hst, dp_slot, st);
+      launch_dp_gather<T>(dI, dRT, (int)rt.size(), dp_ck, S, dp_slot, dp_mrev, st);
+      nlaunch += 2;
+      fft_only(dp_mrev);
+      for (int s = 1; s <= 6; ++s) {
+        cols();
+        RowArgs<T> a = dp_args(s);
+        a.Yin = Ys(s);
+        a.m = dp_mrev;
+        a.Yout = s < 6 ? Yrec(s + 1) : dp_y5;
+        a.Bout = Brec(s);
+        rows(a, ROW_DP_STAGE);
+      }
+      int cur = 0;
+      {
+        AdjArgs<T> a = adj_args();
+        a.hst = dp_hst;
+        a.ebuf = dp_eta;
+        a.kstride = S;
+        a.stage = 6;
+        a.seed_only = 1;
+        a.dpb = (T)dp::b(6);
+        a.Yprev = Ys(6);
+        a.Bprev = Brec(6);
+        a.BbarOut = bb[cur];
+        adj_dp(a);
+      }
+      for (int s = 6; s >= 1; --s) {
+        cols();
+        AdjArgs<T> a = adj_args();
+        a.hst = dp_hst;
+        a.ebuf = dp_eta;
+        a.kstride = S;
+        a.stage = s;
+        a.Ys = Ys(s);
+        a.Bbar = bb[cur];
+        a.BbarOut = bb[1 - cur];
+        if (s > 1) {
+          a.Yprev = Ys(s - 1);
+          a.Bprev = Brec(s - 1);
+          a.dpb = (T)dp::b(s - 1);
+          for (int i = s; i <= 6; ++i) a.dpa[i] = (T)dp::a(i, s - 1);
+        }
+        adj_dp(a);
+        if (s > 1) cur ^= 1;
+      }
+    }
+    launch_grad_finish_tiles<T>(dI, dRT, (int)rt.size(), dpsi, psib, psic, static_cast<T*>(dphi), st);
+    ++nlaunch;
+    if (dm0) cudaMemcpyAsync(dm0, lam, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
+    cudaEventRecord(ev1, st);
+    int herr = 0;
+    cudaMemcpyAsync(&herr, errw, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "llg_adjoint");
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "llg_adjoint");
+    time_drain();
+    if (herr) return fail(LLG_ETIMEOUT, "a bounded device wait ran out in llg_adjoint");
+    float f = 0.f;
+    cudaEventElapsedTime(&f, ev0, ev1);
+    ms = f;
+    have_fwd = false;
+    return LLG_OK;
+  }
+
+  llg_status adaptive_steps(int inst, double* t, double* h, long long cap, long long* count) override {
+    if (!dp_mode || dp_cnt_h.empty()) return fail(LLG_ESTATE, "no adaptive forward pass to report");
+    if (inst < 0 || inst >= n || !count || cap < 0 || (cap > 0 && (!t || !h)))
+      return fail(LLG_EINVAL, "adaptive_steps: bad instance or buffers");
+    const long long K = dp_cnt_h[inst];
+    *count = K;
+    const long long k_n = std::min(K, cap);
+    if (k_n == 0) return LLG_OK;
+    std::vector<double> buf(2 * (size_t)n * k_n);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), dp_sched, sizeof(double) * buf.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "adaptive_steps");
+    for (long long k = 0; k < k_n; ++k) {
+      t[k] = buf[2 * (k * n + inst)];
+      h[k] = buf[2 * (k * n + inst) + 1];
+    }
+    return LLG_OK;
+  }
+
   llg_status forward(const void* phi_v, const void* m0_v, double* J, void* mT) override {
     if (!phi_v || !m0_v || !J) return fail(LLG_EINVAL, "phi, m0 and J must not be NULL");
+    if (dp_mode) return forward_dp(static_cast<const T*>(phi_v), m0_v, J, mT);
     const T* phi = static_cast<const T*>(phi_v);
     cudaEventRecord(ev0, st);
     material(phi);
@@ -1005,6 +1278,21 @@ struct Engine final : llg_ctx {
     a.wtab = wtab;
     return a;
   }
+  void adj_dp(const AdjArgs<T>& a0) {
+    AdjArgs<T> a = a0;
+    time_begin(2);
+    if (!rt2.empty()) {
+      a.tiles = dRT2;
+      launch_adj_dp<T>(a, (int)rt2.size(), smem_adj, st, false);
+      ++nlaunch;
+    }
+    if (!rt3.empty()) {
+      a.tiles = dRT3;
+      launch_adj_dp<T>(a, (int)rt3.size(), smem_adj, st, true);
+      ++nlaunch;
+    }
+    time_end(2);
+  }
   void adj(const AdjArgs<T>& a0) {
     AdjArgs<T> a = a0;
     time_begin(2);
@@ -1024,6 +1312,7 @@ struct Engine final : llg_ctx {
   llg_status adjoint(void* dphi, void* dm0) override {
     if (!have_fwd) return fail(LLG_ESTATE, "llg_adjoint needs a preceding llg_forward");
     if (!dphi) return fail(LLG_EINVAL, "dJdphi must not be NULL");
+    if (dp_mode) return adjoint_dp(dphi, dm0);
     cudaEventRecord(ev0, st);
     // The working state m (with the spectrum of its stage-1 input) is what
     // RESTORE loads, ADVANCE moves, SNAP saves and RECORD starts from.
@@ -1134,6 +1423,12 @@ llg_status llg_forward(llg_ctx* ctx, const void* phi_dev, const void* m0_dev, do
 llg_status llg_adjoint(llg_ctx* ctx, void* dJdphi_dev, void* dJdm0_dev) {
   if (!ctx) return LLG_EINVAL;
   return ctx->adjoint(dJdphi_dev, dJdm0_dev);
+}
+
+llg_status llg_adaptive_steps(llg_ctx* ctx, int inst, double* t_host, double* h_host, long long cap,
+                              long long* count) {
+  if (!ctx) return LLG_EINVAL;
+  return ctx->adaptive_steps(inst, t_host, h_host, cap, count);
 }
 
 llg_status levelset_step(llg_ctx* ctx, void* phi_dev, const void* grad_dev, const unsigned char* mask_dev,

@@ -25,11 +25,12 @@ LLG_OK, LLG_EINVAL, LLG_ENOMEM, LLG_ECUDA, LLG_ETIMEOUT, LLG_ENONFINITE, LLG_EST
 LLG_J_PORT, LLG_J_ENERGY_AREA, LLG_J_SPECTRAL, LLG_J_CURVE = 0, 1, 2, 3
 LLG_FP32, LLG_FP64 = 0, 1
 LLG_CKPT_STORE_ALL, LLG_CKPT_PERIODIC, LLG_CKPT_BINOMIAL = 0, 1, 2
+LLG_INT_RK4, LLG_INT_DOPRI5 = 0, 1
 
 EXPORTED = ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query",
             "llg_launch_count", "llg_kernel_time", "llg_last_error", "llg_destroy", "llg_schedule",
             "llg_padded_extents", "llg_abi_version", "llg_field_noalloc", "llg_rbf_workspace_bytes",
-            "llg_rbf_phi", "llg_rbf_grad", "llg_adam_step", "llg_fp64_fma_rate")
+            "llg_rbf_phi", "llg_rbf_grad", "llg_adam_step", "llg_fp64_fma_rate", "llg_adaptive_steps")
 
 
 class llg_rbf(ctypes.Structure):
@@ -57,7 +58,8 @@ class llg_problem(ctypes.Structure):
 
 class llg_options(ctypes.Structure):
     _fields_ = [("precision", c_int), ("ckpt", c_int), ("seg_len", c_int), ("use_graph", c_int),
-                ("rows_per_cta", c_int), ("cols_per_cta", c_int), ("time_kernels", c_int)]
+                ("rows_per_cta", c_int), ("cols_per_cta", c_int), ("time_kernels", c_int), ("integrator", c_int),
+                ("rtol", c_double), ("atol", c_double)]
 
 
 class LLGError(RuntimeError):
@@ -114,6 +116,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.llg_adam_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_ll, c_double, c_double, c_double,
                                   c_double, c_void_p]
     lib.llg_adam_step.restype = c_int
+    lib.llg_adaptive_steps.argtypes = [c_void_p, c_int, P(c_double), P(c_double), c_ll, P(c_ll)]
+    lib.llg_adaptive_steps.restype = c_int
     lib.llg_fp64_fma_rate.argtypes = [c_int, P(c_double), P(c_double), c_void_p]
     lib.llg_fp64_fma_rate.restype = c_int
     for f in ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query"):
@@ -177,11 +181,13 @@ def _check(lib, ctx, st):
 # ---- thin wrappers with the C names -------------------------------------
 
 def llg_create(problems: Sequence, precision=LLG_FP32, ckpt=LLG_CKPT_PERIODIC, seg_len=0,
-               stream=0, rows_per_cta=0, cols_per_cta=0, use_graph=0, time_kernels=0) -> int:
+               stream=0, rows_per_cta=0, cols_per_cta=0, use_graph=0, time_kernels=0,
+               integrator=LLG_INT_RK4, rtol=1e-6, atol=1e-9) -> int:
     lib = load()
     structs = [to_struct(p) for p in problems]          # hold the host arrays until create returns
     arr = (llg_problem * len(problems))(*structs)
-    opt = llg_options(precision, ckpt, seg_len, use_graph, rows_per_cta, cols_per_cta, time_kernels)
+    opt = llg_options(precision, ckpt, seg_len, use_graph, rows_per_cta, cols_per_cta, time_kernels, integrator,
+                      rtol, atol)
     ctx = c_void_p()
     st = lib.llg_create(arr, len(problems), ctypes.byref(opt), c_void_p(stream), ctypes.byref(ctx))
     if st != LLG_OK:
@@ -272,6 +278,19 @@ def llg_fp64_fma_rate(iters: int = 16384, stream: int = 0):
     return tf.value, ms.value
 
 
+def llg_adaptive_steps(ctx: int, inst: int):
+    """Accepted steps (t_k, h_k) of instance `inst` in the last adaptive
+    forward pass, as two numpy arrays."""
+    lib = load()
+    count = c_ll()
+    _check(lib, ctx, lib.llg_adaptive_steps(c_void_p(ctx), inst, None, None, 0, ctypes.byref(count)))
+    K = count.value
+    t = (c_double * max(1, K))()
+    h = (c_double * max(1, K))()
+    _check(lib, ctx, lib.llg_adaptive_steps(c_void_p(ctx), inst, t, h, K, ctypes.byref(count)))
+    return np.array(t[:K]), np.array(h[:K])
+
+
 def llg_query(ctx: int):
     lib = load()
     b = ctypes.c_size_t()
@@ -329,7 +348,8 @@ class Solver:
 
     def __init__(self, problems: Sequence, precision: str = "fp32", ckpt: str = "periodic",
                  seg_len: int = 0, stream=None, rows_per_cta: int = 0, cols_per_cta: int = 0,
-                 time_kernels: bool = False, use_graph: bool = True):
+                 time_kernels: bool = False, use_graph: bool = True, integrator: str = "rk4",
+                 rtol: float = 1e-6, atol: float = 1e-9):
         import torch
         self.torch = torch
         self.problems = list(problems)
@@ -337,8 +357,9 @@ class Solver:
         prec = LLG_FP32 if precision == "fp32" else LLG_FP64
         ck = {"periodic": LLG_CKPT_PERIODIC, "store_all": LLG_CKPT_STORE_ALL, "binomial": LLG_CKPT_BINOMIAL}[ckpt]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        integ = {"rk4": LLG_INT_RK4, "dopri5": LLG_INT_DOPRI5}[integrator]
         self.ctx = llg_create(self.problems, prec, ck, seg_len, self.stream.cuda_stream,
-                              rows_per_cta, cols_per_cta, int(use_graph), int(time_kernels))
+                              rows_per_cta, cols_per_cta, int(use_graph), int(time_kernels), integ, rtol, atol)
         self.nodes = [p.nx * p.ny * p.nz for p in self.problems]
         self.total = sum(self.nodes)
 
@@ -412,6 +433,10 @@ class Solver:
 
     def launch_count(self) -> int:
         return llg_launch_count(self.ctx)
+
+    def adaptive_steps(self, inst: int):
+        """(t_k, h_k) of the accepted steps of instance `inst` (dopri5)."""
+        return llg_adaptive_steps(self.ctx, inst)
 
     def kernel_time(self, family: int):
         return llg_kernel_time(self.ctx, family)
