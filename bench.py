@@ -157,6 +157,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank gets it): an all-reduce MAX of one
+    float64 on `device` ("cuda" under NCCL, "cpu" under gloo)."""
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(node_steps_per_rank, world, ms_max):
+    """Whole-job node-steps/s: every rank integrates its own replica of the
+    workload, so the job does world x node_steps in the slowest rank's time."""
+    return node_steps_per_rank * world / (ms_max / 1e3)
+
+
 def fft_flops(insts, family):
     """FP64 path: FFT flops of one launch of a kernel family over the batch,
     5 N log2 N per complex transform of length N (pointwise arithmetic not
@@ -382,11 +398,8 @@ def run_ours(args):
     fam1 = {f: sk.kernel_time(f) for f in (0, 1, 2)}
     ms_events = k0.elapsed_time(k1) / args.steps
     sk.close()
-    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = node_steps * world / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = job_throughput(node_steps, world, ms_max)
 
     # roofline of the dominant kernel family over the timed region
     hbm, peak_kind = measured_peaks()
