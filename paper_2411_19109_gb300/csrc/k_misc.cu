@@ -163,8 +163,9 @@ void launch_dp_control(const DevInst* inst, int n_inst, const double* eslots, do
 
 // Reverse step r of the adjoint sweep: each instance reverses its accepted
 // step k = cnt - 1 - r with the recorded (t_k, h_k), or idles (h = 0).
-__global__ void dp_reverse_state_kernel(int n_inst, const double* sched, const int* cnt, long long r, double* hst,
-                                        long long* slot) {
+__global__ void dp_reverse_state_kernel(int n_inst, const double* sched, const int* cnt, const long long* rptr,
+                                        double* hst, long long* slot) {
+  const long long r = *rptr;
   for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
     const long long k = (long long)cnt[i] - 1 - r;
     if (k >= 0) {
@@ -179,9 +180,9 @@ __global__ void dp_reverse_state_kernel(int n_inst, const double* sched, const i
   }
 }
 
-void launch_dp_reverse_state(int n_inst, const double* sched, const int* cnt, long long r, double* hst,
+void launch_dp_reverse_state(int n_inst, const double* sched, const int* cnt, const long long* rptr, double* hst,
                              long long* slot, cudaStream_t st) {
-  dp_reverse_state_kernel<<<1, 256, 0, st>>>(n_inst, sched, cnt, r, hst, slot);
+  dp_reverse_state_kernel<<<1, 256, 0, st>>>(n_inst, sched, cnt, rptr, hst, slot);
 }
 
 template <typename T>

@@ -168,7 +168,7 @@ void launch_dp_gather(const DevInst* inst, const RowTile* tiles, int ntiles, con
                       const long long* slot, T* out, cudaStream_t st);
 void launch_dp_control(const DevInst* inst, int n_inst, const double* eslots, double* hst, int* accept, int* cnt,
                        double* sched, long long max_steps, double T_end, int* overflow, cudaStream_t st);
-void launch_dp_reverse_state(int n_inst, const double* sched, const int* cnt, long long r, double* hst,
+void launch_dp_reverse_state(int n_inst, const double* sched, const int* cnt, const long long* rptr, double* hst,
                              long long* slot, cudaStream_t st);
 template <typename T>
 void set_smem_limits(size_t stage, size_t misc, size_t cols, size_t adj);

@@ -255,7 +255,8 @@ struct Engine final : llg_ctx {
   // that shape.  Value: the executable graph and the launches it holds.
   // ADVANCE_ADJ: recomputation during the reverse sweep (no objective terms).
   // The cache holds at most kMaxGraphs graphs; other shapes run directly.
-  enum SegKind { SEG_ADVANCE = 0, SEG_RECORD_FWD = 1, SEG_RECORD_ADJ = 2, SEG_REVERSE = 3, SEG_ADVANCE_ADJ = 4 };
+  enum SegKind { SEG_ADVANCE = 0, SEG_RECORD_FWD = 1, SEG_RECORD_ADJ = 2, SEG_REVERSE = 3, SEG_ADVANCE_ADJ = 4,
+                 SEG_DP_ATTEMPT = 5, SEG_DP_REVERSE = 6 };
   static constexpr size_t kMaxGraphs = 64;
   std::map<std::pair<int, long long>, std::pair<cudaGraphExec_t, long long>> graphs;
   cudaStream_t cap_st = nullptr;   // private stream the captures are recorded on
@@ -838,6 +839,14 @@ struct Engine final : llg_ctx {
   }
 
   void segment_body(int kind, long long len) {
+    if (kind == SEG_DP_ATTEMPT) {
+      for (long long l = 0; l < len; ++l) dp_attempt();
+      return;
+    }
+    if (kind == SEG_DP_REVERSE) {
+      dp_reverse_step();
+      return;
+    }
     if (kind == SEG_REVERSE) {
       reverse_segment(len);
       return;
@@ -1043,8 +1052,8 @@ struct Engine final : llg_ctx {
     std::vector<double> hh(4 * (size_t)n);
     int ovf = 0;
     bool done = N == 0;
-    for (long long att = 0; !done && att < max_att;) {
-      for (int k = 0; k < 4; ++k, ++att) dp_attempt();
+    for (long long att = 0; !done && att < max_att; att += 4) {
+      if (llg_status st2 = run_segment(SEG_DP_ATTEMPT, 4)) return st2;
       cudaMemcpyAsync(hh.data(), dp_hst, sizeof(double) * hh.size(), cudaMemcpyDeviceToHost, st);
       cudaMemcpyAsync(&ovf, dp_ovf, sizeof(int), cudaMemcpyDeviceToHost, st);
       cudaError_t e = cudaStreamSynchronize(st);
@@ -1093,6 +1102,60 @@ struct Engine final : llg_ctx {
     return LLG_OK;
   }
 
+  // one reverse step of the Dormand-Prince sweep (reverse index in *step_base)
+  void dp_reverse_step() {
+    const long long S = (long long)slot();
+    auto Yrec = [&](int s) { return dp_recY + (long long)(s - 1) * S; };   // Y_s, s = 2..6 (Y_1 = mrev)
+    auto Brec = [&](int s) { return dp_recB + (long long)(s - 1) * S; };
+    auto Ys = [&](int s) -> T* { return s == 1 ? dp_mrev : Yrec(s); };
+    launch_dp_reverse_state(n, dp_sched, dp_cnt, step_base, dp_hst, dp_slot, st);
+    launch_dp_gather<T>(dI, dRT, (int)rt.size(), dp_ck, S, dp_slot, dp_mrev, st);
+    nlaunch += 2;
+    fft_only(dp_mrev);
+    for (int s = 1; s <= 6; ++s) {
+      cols();
+      RowArgs<T> a = dp_args(s);
+      a.Yin = Ys(s);
+      a.m = dp_mrev;
+      a.Yout = s < 6 ? Yrec(s + 1) : dp_y5;
+      a.Bout = Brec(s);
+      rows(a, ROW_DP_STAGE);
+    }
+    int cur = 0;
+    {
+      AdjArgs<T> a = adj_args();
+      a.hst = dp_hst;
+      a.ebuf = dp_eta;
+      a.kstride = S;
+      a.stage = 6;
+      a.seed_only = 1;
+      a.dpb = (T)dp::b(6);
+      a.Yprev = Ys(6);
+      a.Bprev = Brec(6);
+      a.BbarOut = bb[cur];
+      adj_dp(a);
+    }
+    for (int s = 6; s >= 1; --s) {
+      cols();
+      AdjArgs<T> a = adj_args();
+      a.hst = dp_hst;
+      a.ebuf = dp_eta;
+      a.kstride = S;
+      a.stage = s;
+      a.Ys = Ys(s);
+      a.Bbar = bb[cur];
+      a.BbarOut = bb[1 - cur];
+      if (s > 1) {
+        a.Yprev = Ys(s - 1);
+        a.Bprev = Brec(s - 1);
+        a.dpb = (T)dp::b(s - 1);
+        for (int i = s; i <= 6; ++i) a.dpa[i] = (T)dp::a(i, s - 1);
+      }
+      adj_dp(a);
+      if (s > 1) cur ^= 1;
+    }
+  }
+
   // reverse sweep over the accepted steps: per reverse index r, instance i
   // reverses its step cnt_i - 1 - r (or idles with h = 0): recompute the six
   // stages from its checkpoint, seed kappa_6 = h b_6 lambda, then adjoint
@@ -1101,57 +1164,9 @@ struct Engine final : llg_ctx {
     cudaEventRecord(ev0, st);
     long long Kmax = 0;
     for (int i = 0; i < n; ++i) Kmax = std::max(Kmax, (long long)dp_cnt_h[i]);
-    const long long S = (long long)slot();
-    auto Yrec = [&](int s) { return dp_recY + (long long)(s - 1) * S; };   // Y_s, s = 2..6 (Y_1 = mrev)
-    auto Brec = [&](int s) { return dp_recB + (long long)(s - 1) * S; };
-    auto Ys = [&](int s) -> T* { return s == 1 ? dp_mrev : Yrec(s); };
     for (long long r = 0; r < Kmax; ++r) {
-      launch_dp_reverse_state(n, dp_sched, dp_cnt, r, dp_hst, dp_slot, st);
-      launch_dp_gather<T>(dI, dRT, (int)rt.size(), dp_ck, S, dp_slot, dp_mrev, st);
-      nlaunch += 2;
-      fft_only(dp_mrev);
-      for (int s = 1; s <= 6; ++s) {
-        cols();
-        RowArgs<T> a = dp_args(s);
-        a.Yin = Ys(s);
-        a.m = dp_mrev;
-        a.Yout = s < 6 ? Yrec(s + 1) : dp_y5;
-        a.Bout = Brec(s);
-        rows(a, ROW_DP_STAGE);
-      }
-      int cur = 0;
-      {
-        AdjArgs<T> a = adj_args();
-        a.hst = dp_hst;
-        a.ebuf = dp_eta;
-        a.kstride = S;
-        a.stage = 6;
-        a.seed_only = 1;
-        a.dpb = (T)dp::b(6);
-        a.Yprev = Ys(6);
-        a.Bprev = Brec(6);
-        a.BbarOut = bb[cur];
-        adj_dp(a);
-      }
-      for (int s = 6; s >= 1; --s) {
-        cols();
-        AdjArgs<T> a = adj_args();
-        a.hst = dp_hst;
-        a.ebuf = dp_eta;
-        a.kstride = S;
-        a.stage = s;
-        a.Ys = Ys(s);
-        a.Bbar = bb[cur];
-        a.BbarOut = bb[1 - cur];
-        if (s > 1) {
-          a.Yprev = Ys(s - 1);
-          a.Bprev = Brec(s - 1);
-          a.dpb = (T)dp::b(s - 1);
-          for (int i = s; i <= 6; ++i) a.dpa[i] = (T)dp::a(i, s - 1);
-        }
-        adj_dp(a);
-        if (s > 1) cur ^= 1;
-      }
+      set_step(r);
+      if (llg_status st2 = run_segment(SEG_DP_REVERSE, 1)) return st2;
     }
     launch_grad_finish_tiles<T>(dI, dRT, (int)rt.size(), dpsi, psib, psic, static_cast<T*>(dphi), st);
     ++nlaunch;
