@@ -663,7 +663,7 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
   // objective: the tile's sum of psi m_comp (channel 0) at every step
   const bool spectral_step = !DP && s == 4 && a.pslots != nullptr &&
                              ((I.objective == 2 && (n + 1) >= a.n_from) || I.objective == 3);
-  double psum[2] = {0.0, 0.0};
+  T psum[2] = {0, 0};   // per-thread partials in T (a thread adds a few nodes), tile sum in FP64
 #pragma unroll 1
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
     const long long n0 = zoff + (long long)y * nx + x;
@@ -776,11 +776,11 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
     }
     if (spectral_step) {
       if (I.objective == 3) {
-        psum[0] += (double)pi * (double)yn[I.comp];
+        psum[0] += pi * yn[I.comp];
       } else {
 #pragma unroll
         for (int b = 0; b < 2; ++b)
-          if (in_box(I.boxes[b], x, y)) psum[b] += (double)yn[I.comp];
+          if (in_box(I.boxes[b], x, y)) psum[b] += yn[I.comp];
       }
     }
   }
@@ -804,7 +804,7 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
       if (I.objective == 3 ? b != 0
                            : !(I.boxes[b][2] < y0 + nr && I.boxes[b][3] > y0 && I.boxes[b][0] < I.boxes[b][1]))
         continue;
-      const double tot = block_sum(psum[b], red);
+      const double tot = block_sum((double)psum[b], red);
       if (threadIdx.x == 0) a.pslots[2 * (I.slot_off + (long long)(n + 1) * I.ntile + tile.k) + b] = tot;
       __syncthreads();   // red is reused by the next box
     }
