@@ -150,3 +150,40 @@ def test_bench_fft_flop_model_and_reference_arm_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "node-steps/s"
     assert line["cpu_baseline"]["cores"] >= 1 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_cuda_dormand_prince_tableau_meets_the_order_conditions(tmp_path):
+    """The tableau the CUDA path compiles (csrc/dopri.cuh), printed by a host
+    program and checked against the order conditions of the 5(4) pair."""
+    import shutil
+    import subprocess
+    import numpy as np
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    src = tmp_path / "tab.cu"
+    src.write_text('#include <cstdio>\n#include "dopri.cuh"\nint main() {\n'
+                   '  for (int s = 1; s <= 7; ++s) std::printf("%.17g\\n", llg::dp::c(s));\n'
+                   '  for (int s = 1; s <= 7; ++s) for (int j = 1; j <= 7; ++j) std::printf("%.17g\\n", llg::dp::a(s, j));\n'
+                   '  for (int s = 1; s <= 7; ++s) std::printf("%.17g\\n", llg::dp::b(s));\n'
+                   '  for (int s = 1; s <= 7; ++s) std::printf("%.17g\\n", llg::dp::e(s));\n  return 0;\n}\n')
+    exe = tmp_path / "tab"
+    subprocess.run([nvcc, "-std=c++17", "-I", os.path.join(ROOT, "paper_2411_19109_gb300", "csrc"), str(src),
+                    "-o", str(exe)], check=True, capture_output=True, timeout=300)
+    v = np.array([float(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                    text=True).stdout.split()])
+    c, a, b, e = v[:7], v[7:56].reshape(7, 7), v[56:63], v[63:70]
+    bs = b - e
+    assert np.all(np.triu(a) == 0)                                  # explicit
+    np.testing.assert_allclose(a.sum(1), c, atol=1e-15)
+    np.testing.assert_array_equal(a[6], b)                          # first same as last
+    for w, order in ((b, 5), (bs, 4)):
+        assert w.sum() == pytest.approx(1.0, abs=1e-15)
+        for q in range(1, order):
+            assert w @ c ** q == pytest.approx(1.0 / (q + 1), abs=1e-14)
+        assert w @ a @ c == pytest.approx(1.0 / 6, abs=1e-14)
+        assert w @ a @ a @ c == pytest.approx(1.0 / 24, abs=1e-14)
+    assert b @ a @ c ** 3 == pytest.approx(1.0 / 20, abs=1e-14)
+    assert b @ (a @ c) ** 2 == pytest.approx(1.0 / 20, abs=1e-14)
+    assert b @ a @ a @ a @ c == pytest.approx(1.0 / 120, abs=1e-14)
+    assert e[6] == pytest.approx(-1.0 / 40, abs=1e-17) and np.abs(e).max() > 1e-3
