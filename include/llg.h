@@ -150,14 +150,15 @@ typedef struct {
                       size: err = sqrt(mean((psi e / (atol + rtol max(|psi
                       m|, |psi y5|)))^2)) over nodes and components, accept
                       if err <= 1, h <- h min(5, max(0.2, 0.9 err^-1/5)),
-                      the last step shortened to end at T.  At most nsteps
-                      accepted steps and 4 nsteps attempts per instance
+                      the last step shortened to end at T.  At most
+                      seg_len (0: nsteps) accepted steps, one checkpoint of
+                      m each, and 4 nsteps attempts per instance
                       (LLG_ETIMEOUT beyond).  The gradient is the exact
                       derivative over the accepted steps (their sizes held
                       fixed), from a store-all checkpoint of every accepted
                       step.  Needs the LLG_J_ENERGY_AREA objective and the
-                      sine drive (no drive table); ckpt and seg_len are
-                      ignored, use_graph replays captured attempts.          */
+                      sine drive (no drive table); ckpt is ignored,
+                      use_graph replays captured attempts.                   */
   double rtol, atol; /* LLG_INT_DOPRI5 tolerances                            */
 } llg_options;
 

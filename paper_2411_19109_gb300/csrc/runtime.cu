@@ -598,11 +598,12 @@ struct Engine final : llg_ctx {
     if (!ok) return fail(LLG_ENOMEM, "device allocation failed (" + std::to_string(bytes >> 20) + " MiB so far)");
     if (dp_mode) {
       const long long K7 = 7, R6 = 6;
-      dp_maxK = N;
-      const bool ok2 = alloc(&dp_k, S * K7) && alloc(&dp_y5, S) && alloc(&dp_ck, S * (N + 1)) &&
+      dp_maxK = opt.seg_len > 0 ? std::min<long long>(opt.seg_len, N) : N;   // checkpoint slots
+      const bool ok2 = alloc(&dp_k, S * K7) && alloc(&dp_y5, S) && alloc(&dp_ck, S * (dp_maxK + 1)) &&
                        alloc(&dp_recY, S * R6) && alloc(&dp_recB, S * R6) && alloc(&dp_eta, S * R6) &&
                        alloc(&dp_mrev, S) && alloc(&dp_e, rt.size()) && alloc(&dp_hst, 4 * (size_t)n) &&
-                       alloc(&dp_sched, 2 * (size_t)n * std::max(1LL, N)) && alloc(&dp_acc, n) && alloc(&dp_cnt, n) &&
+                       alloc(&dp_sched, 2 * (size_t)n * std::max(1LL, dp_maxK)) && alloc(&dp_acc, n) &&
+                       alloc(&dp_cnt, n) &&
                        alloc(&dp_ovf, 1) && alloc(&dp_slot, n);
       if (!ok2)
         return fail(LLG_ENOMEM, "device allocation failed for the adaptive integrator's store-all checkpoints (" +
@@ -1060,7 +1061,7 @@ struct Engine final : llg_ctx {
       if (e != cudaSuccess) return cuda_fail(e, "adaptive integrator");
       done = true;
       for (int i = 0; i < n; ++i) done &= hh[4 * i + 3] != 0.0;
-      if (ovf) return fail(LLG_ETIMEOUT, "adaptive integrator: more than nsteps accepted steps");
+      if (ovf) return fail(LLG_ETIMEOUT, "adaptive integrator: more accepted steps than checkpoint slots");
     }
     if (!done) return fail(LLG_ETIMEOUT, "adaptive integrator: no end of the interval within 4 nsteps attempts");
     dp_cnt_h.assign(n, 0);

@@ -104,3 +104,20 @@ def test_invalid_adaptive_setups_are_rejected():
             gpu_solver([type("I", (), {"problem": p})()], "fp32", integrator="dopri5", rtol=RTOL, atol=ATOL)
     with pytest.raises(LLGError):
         gpu_solver([ok], "fp32", integrator="dopri5", rtol=0.0, atol=ATOL)
+
+
+def test_checkpoint_slots_cap_the_accepted_steps():
+    from paper_2411_19109_gb300 import LLGError
+    inst = _case(12, 8, seed=56, N=40)
+    ref = _gpu([inst], "fp32")
+    K = len(ref["sched"][0][1])
+    assert K > 3
+    same = _gpu([inst], "fp32", seg_len=K)                 # exactly enough slots
+    assert same["J"][0] == ref["J"][0]
+    np.testing.assert_array_equal(same["dphi"][0], ref["dphi"][0])
+    s = gpu_solver([inst], "fp32", integrator="dopri5", rtol=RTOL, atol=ATOL, seg_len=K - 1)
+    try:
+        with pytest.raises(LLGError):
+            s.forward(s.pack_scalar([inst.phi]), s.pack_vector([inst.m0]))
+    finally:
+        s.close()
