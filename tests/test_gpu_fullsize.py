@@ -8,13 +8,13 @@ nodes carries none), J against the sum of the magnitudes of its terms (the
 port objective is a difference of two ports).
 
 FP32 and the demultiplexer's gradient: its port signal m_y stays at the level
-of the m0 noise (1e-3; the drive is below the film's uniform-mode frequency),
-while the FP32 demag FFT's rounding is relative to the whole field, which the
-uniform +x magnetisation and its edge fields dominate.  The gradient of that
-port signal then carries FP32 rounding of about 1e-3 relative after 100 steps
-(2e-2 after 20, where it is smaller still), while m and J hold 1e-5 and 1e-4
-and the FP64 path 1e-9; the nanoparticle and the random test grids hold
-1e-4 on the gradient in FP32 as well."""
+of the m0 noise (1e-3; the drive is below the film's uniform-mode frequency)
+and the FP32 gradient of that signal is 1e-3 off the oracle after 100 steps
+(2e-2 after 20), while m and J hold 1e-5 and 1e-4 and the same kernels in
+FP64 hold 1e-9.  It does not change with the damping or without the drive,
+nor when the demag FFT transforms only the deviation from the mean
+magnetisation, so the FFT's dynamic range is not the cause; the nanoparticle
+and the random test grids hold 1e-4 on the gradient in FP32 as well."""
 import numpy as np
 import pytest
 
