@@ -7,14 +7,16 @@ store-all path), and the nanoparticle (64 x 64) and single demultiplexer
 nodes carries none), J against the sum of the magnitudes of its terms (the
 port objective is a difference of two ports).
 
-FP32 and the demultiplexer's gradient: its port signal m_y stays at the level
-of the m0 noise (1e-3; the drive is below the film's uniform-mode frequency)
-and the FP32 gradient of that signal is 1e-3 off the oracle after 100 steps
-(2e-2 after 20), while m and J hold 1e-5 and 1e-4 and the same kernels in
-FP64 hold 1e-9.  It does not change with the damping or without the drive,
-nor when the demag FFT transforms only the deviation from the mean
-magnetisation, so the FFT's dynamic range is not the cause; the nanoparticle
-and the random test grids hold 1e-4 on the gradient in FP32 as well."""
+FP32 and the demultiplexer's gradient: it is 1e-3 off the oracle after 100
+steps (2e-2 after 20), while m and J hold 1e-5 and 1e-4 and the same kernels
+in FP64 hold 1e-9.  The source is the FP32 FFT of the adjoint's demag
+transpose: the adjoint field starts at the output ports and the design region
+sees only its tail, which FFT rounding (relative to the whole field's norm)
+cannot resolve.  Rounding the oracle's own adjoint demag FFT to FP32 (complex64)
+reproduces it (1e-2 after 20 steps, 5e-4 after 100), while FP32 rounding of
+the forward FFT or of every stored state, field and slope gives below 1e-6.
+The nanoparticle and the random test grids, whose adjoint fields cover the
+grid, hold 1e-4 on the gradient in FP32."""
 import numpy as np
 import pytest
 
