@@ -729,13 +729,16 @@ __device__ __forceinline__ void stage_body(const RowArgs<T>& a, const DevInst& I
         a.kbuf[(long long)(s - 1) * a.kstride + id] = k[c];
         if (s < 7) {
           T acc2 = a.dpa[s - 1] * k[c];
-          for (int j = 1; j < s; ++j)
-            if (a.dpa[j - 1] != (T)0) acc2 += a.dpa[j - 1] * a.kbuf[(long long)(j - 1) * a.kstride + id];
+          // fully unrolled: the slot loads of all earlier stages issue together
+#pragma unroll
+          for (int j = 1; j < 6; ++j)
+            if (j < s && a.dpa[j - 1] != (T)0) acc2 += a.dpa[j - 1] * a.kbuf[(long long)(j - 1) * a.kstride + id];
           const T yv = mn[c] + hdp * acc2;
           gYout[id] = yv;
           sEr[2 * c * GS + sl] = Ms * pi * yv;
         } else {
           T ec = a.dpe[6] * k[c];
+#pragma unroll
           for (int j = 1; j < 7; ++j)
             if (a.dpe[j - 1] != (T)0) ec += a.dpe[j - 1] * a.kbuf[(long long)(j - 1) * a.kstride + id];
           const double p = (double)pi;
