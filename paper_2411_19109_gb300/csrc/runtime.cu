@@ -260,11 +260,33 @@ struct Engine final : llg_ctx {
   static constexpr size_t kMaxGraphs = 64;
   std::map<std::pair<int, long long>, std::pair<cudaGraphExec_t, long long>> graphs;
   cudaStream_t cap_st = nullptr;   // private stream the captures are recorded on
+  // Two instance groups (even and odd index) whose RK4 segments run as two
+  // independent chains on two streams (two branches of each captured graph),
+  // so that one group's launches fill the other's last wave and kernels of
+  // different kinds share the SMs.  Each tile list has a partitioned device
+  // copy (group 0's tiles first); grp_sel selects the part the launch helpers
+  // take (-1: the whole list in its original order, which measured faster
+  // for single launches).
+  bool two_groups = false;
+  int grp_sel = -1;
+  size_t split_rt2 = 0, split_rt3 = 0, split_ct = 0, split_ct16 = 0, split_ct3 = 0;
+  RowTile *dRT2p = nullptr, *dRT3p = nullptr;
+  ColTile *dCTp = nullptr, *dCT16p = nullptr, *dCT3p = nullptr;
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // (offset, count) of the selected group in a tile list of size sz split at sp
+  std::pair<size_t, size_t> part(size_t sz, size_t sp) const {
+    if (grp_sel < 0) return {0, sz};
+    return grp_sel == 0 ? std::make_pair((size_t)0, sp) : std::make_pair(sp, sz - sp);
+  }
 
   ~Engine() override {
     if (st) cudaStreamSynchronize(st);
     for (auto& g : graphs) cudaGraphExecDestroy(g.second.first);
     if (cap_st) cudaStreamDestroy(cap_st);
+    if (st2) cudaStreamDestroy(st2);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
     for (void* p : allocs) cudaFree(p);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -582,6 +604,7 @@ struct Engine final : llg_ctx {
 
     const size_t S = slot();
     for (const RowTile& t : rt) (H[t.inst].nz > 1 ? rt3 : rt2).push_back(t);
+    two_groups = n >= 2 && !opt.time_kernels;
     bool ok = alloc(&dI, n) && alloc(&dRT, rt.size()) && alloc(&dRT2, std::max<size_t>(1, rt2.size())) &&
               alloc(&dRT3, std::max<size_t>(1, rt3.size())) && alloc(&dCT, std::max<size_t>(1, ct.size())) &&
               alloc(&dCT3, std::max<size_t>(1, ct3.size())) && alloc(&dCT16, std::max<size_t>(1, ct16.size())) && alloc(&psi, total_nodes) &&
@@ -596,6 +619,29 @@ struct Engine final : llg_ctx {
               alloc(&jterm, rt.size()) && alloc(&psitile, rt.size()) && alloc(&psimom, 2 * rt.size()) && alloc(&Jd, n) && alloc(&step_base, 1) &&
               alloc(&maxbits, 2 * n) && alloc(&rf, (size_t)n * 3 * (N + 1)) && alloc(&errw, 1);
     if (!ok) return fail(LLG_ENOMEM, "device allocation failed (" + std::to_string(bytes >> 20) + " MiB so far)");
+    if (two_groups) {
+      // partitioned copies of the tile lists: even instances first
+      auto even_r = [](const RowTile& t) { return t.inst % 2 == 0; };
+      auto even_c = [](const ColTile& t) { return t.inst % 2 == 0; };
+      std::vector<RowTile> p2 = rt2, p3 = rt3;
+      std::vector<ColTile> pc = ct, p16 = ct16, pc3 = ct3;
+      split_rt2 = std::stable_partition(p2.begin(), p2.end(), even_r) - p2.begin();
+      split_rt3 = std::stable_partition(p3.begin(), p3.end(), even_r) - p3.begin();
+      split_ct = std::stable_partition(pc.begin(), pc.end(), even_c) - pc.begin();
+      split_ct16 = std::stable_partition(p16.begin(), p16.end(), even_c) - p16.begin();
+      split_ct3 = std::stable_partition(pc3.begin(), pc3.end(), even_c) - pc3.begin();
+      const bool ok3 = alloc(&dRT2p, std::max<size_t>(1, p2.size())) && alloc(&dRT3p, std::max<size_t>(1, p3.size())) &&
+                       alloc(&dCTp, std::max<size_t>(1, pc.size())) && alloc(&dCT16p, std::max<size_t>(1, p16.size())) &&
+                       alloc(&dCT3p, std::max<size_t>(1, pc3.size()));
+      if (!ok3) return fail(LLG_ENOMEM, "device allocation failed (tile lists)");
+      cudaError_t e2 = cudaSuccess;
+      if (!p2.empty()) e2 = cudaMemcpy(dRT2p, p2.data(), sizeof(RowTile) * p2.size(), cudaMemcpyHostToDevice);
+      if (e2 == cudaSuccess && !p3.empty()) e2 = cudaMemcpy(dRT3p, p3.data(), sizeof(RowTile) * p3.size(), cudaMemcpyHostToDevice);
+      if (e2 == cudaSuccess && !pc.empty()) e2 = cudaMemcpy(dCTp, pc.data(), sizeof(ColTile) * pc.size(), cudaMemcpyHostToDevice);
+      if (e2 == cudaSuccess && !p16.empty()) e2 = cudaMemcpy(dCT16p, p16.data(), sizeof(ColTile) * p16.size(), cudaMemcpyHostToDevice);
+      if (e2 == cudaSuccess && !pc3.empty()) e2 = cudaMemcpy(dCT3p, pc3.data(), sizeof(ColTile) * pc3.size(), cudaMemcpyHostToDevice);
+      if (e2 != cudaSuccess) return cuda_fail(e2, "upload tile lists");
+    }
     if (dp_mode) {
       const long long K7 = 7, R6 = 6;
       dp_maxK = opt.seg_len > 0 ? std::min<long long>(opt.seg_len, N) : N;   // checkpoint slots
@@ -688,6 +734,12 @@ struct Engine final : llg_ctx {
     cudaFree(Gs);
     if (e != cudaSuccess) return cuda_fail(e, "demag tensor");
     set_smem_limits<T>(smem_rows, smem_misc, smem_cols, smem_adj);
+    if (two_groups) {
+      if ((e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "create the second stream");
+    }
     cudaMemsetAsync(wtab, 0, sizeof(double) * n * 2 * (N + 1), st);
     smem_cols3<T>(smem_c3);
     if constexpr (sizeof(T) == 4) smem_cols16<T>(smem_cols);
@@ -720,14 +772,15 @@ struct Engine final : llg_ctx {
     RowArgs<T> a = a0;
     const size_t sm = (mode == ROW_STAGE || mode == ROW_DP_STAGE) ? smem_rows : smem_misc;
     if (mode == ROW_STAGE) time_begin(0);
-    if (!rt2.empty()) {
-      a.tiles = dRT2;
-      launch_rows<T>(a, mode, (int)rt2.size(), sm, st, false);
+    const auto p2 = part(rt2.size(), split_rt2), p3 = part(rt3.size(), split_rt3);
+    if (p2.second) {
+      a.tiles = (grp_sel < 0 ? dRT2 : dRT2p) + p2.first;
+      launch_rows<T>(a, mode, (int)p2.second, sm, st, false);
       ++nlaunch;
     }
-    if (!rt3.empty()) {
-      a.tiles = dRT3;
-      launch_rows<T>(a, mode, (int)rt3.size(), sm, st, true);
+    if (p3.second) {
+      a.tiles = (grp_sel < 0 ? dRT3 : dRT3p) + p3.first;
+      launch_rows<T>(a, mode, (int)p3.second, sm, st, true);
       ++nlaunch;
     }
     if (mode == ROW_STAGE) time_end(0);
@@ -742,20 +795,22 @@ struct Engine final : llg_ctx {
     c.cols_max = TX;
     c.err = errw;
     time_begin(1);
-    if (!ct.empty()) {
-      launch_cols<T>(c, (int)ct.size(), smem_cols, st);
+    const auto pc = part(ct.size(), split_ct), p16 = part(ct16.size(), split_ct16), p3 = part(ct3.size(), split_ct3);
+    if (pc.second) {
+      c.tiles = (grp_sel < 0 ? dCT : dCTp) + pc.first;
+      launch_cols<T>(c, (int)pc.second, smem_cols, st);
       ++nlaunch;
     }
     if constexpr (sizeof(T) == 4) {
-      if (!ct16.empty()) {
-        c.tiles = dCT16;
-        launch_cols16<T>(c, (int)ct16.size(), smem_cols, st);
+      if (p16.second) {
+        c.tiles = (grp_sel < 0 ? dCT16 : dCT16p) + p16.first;
+        launch_cols16<T>(c, (int)p16.second, smem_cols, st);
         ++nlaunch;
       }
     }
-    if (!ct3.empty()) {
-      c.tiles = dCT3;
-      launch_cols3<T>(c, (int)ct3.size(), smem_c3, st);
+    if (p3.second) {
+      c.tiles = (grp_sel < 0 ? dCT3 : dCT3p) + p3.first;
+      launch_cols3<T>(c, (int)p3.second, smem_c3, st);
       ++nlaunch;
     }
     time_end(1);
@@ -839,7 +894,28 @@ struct Engine final : llg_ctx {
     }
   }
 
+  // RK4 segments with two instance groups: fork to the second stream, run
+  // each group's whole segment on its own stream, join
   void segment_body(int kind, long long len) {
+    if (!two_groups || kind == SEG_DP_ATTEMPT || kind == SEG_DP_REVERSE) {
+      segment_body_one(kind, len);
+      return;
+    }
+    cudaEventRecord(ev_fork, st);
+    cudaStreamWaitEvent(st2, ev_fork, 0);
+    const cudaStream_t s0 = st;
+    for (int g = 0; g < 2; ++g) {
+      grp_sel = g;
+      st = g == 0 ? s0 : st2;
+      segment_body_one(kind, len);
+    }
+    st = s0;
+    grp_sel = -1;
+    cudaEventRecord(ev_join, st2);
+    cudaStreamWaitEvent(st, ev_join, 0);
+  }
+
+  void segment_body_one(int kind, long long len) {
     if (kind == SEG_DP_ATTEMPT) {
       for (long long l = 0; l < len; ++l) dp_attempt();
       return;
@@ -1312,14 +1388,15 @@ struct Engine final : llg_ctx {
   void adj(const AdjArgs<T>& a0) {
     AdjArgs<T> a = a0;
     time_begin(2);
-    if (!rt2.empty()) {
-      a.tiles = dRT2;
-      launch_adj<T>(a, (int)rt2.size(), smem_adj, st, false);
+    const auto p2 = part(rt2.size(), split_rt2), p3 = part(rt3.size(), split_rt3);
+    if (p2.second) {
+      a.tiles = (grp_sel < 0 ? dRT2 : dRT2p) + p2.first;
+      launch_adj<T>(a, (int)p2.second, smem_adj, st, false);
       ++nlaunch;
     }
-    if (!rt3.empty()) {
-      a.tiles = dRT3;
-      launch_adj<T>(a, (int)rt3.size(), smem_adj, st, true);
+    if (p3.second) {
+      a.tiles = (grp_sel < 0 ? dRT3 : dRT3p) + p3.first;
+      launch_adj<T>(a, (int)p3.second, smem_adj, st, true);
       ++nlaunch;
     }
     time_end(2);
