@@ -264,3 +264,19 @@ def test_port_functional_closed_form():
     m[1] = 1.0      # m along y, no field: the oracle keeps it (demag is parallel? no: check J only)
     val = mod.port_term(m)
     assert val == pytest.approx(0.7 - 0.2, rel=1e-15)
+
+
+@pytest.mark.parametrize("power,n_from", [(1, 0), (2, 1), (2, 37)])
+def test_port_objective_on_a_precessing_macrospin(power, n_from):
+    """Running port sum over a Larmor macrospin (alpha = 0, B along z,
+    m0 = x): m_y(t_n) = sin(w n dt), so J = sum_{n >= n_from} (w_0 + w_1)
+    sin(w n dt)^p, with both boxes on the one node; the window start and the
+    exponent are both exercised."""
+    B, dt, N = 0.1, 1e-13, 120
+    p = W.Problem(nx=1, ny=1, nz=1, Ms=8e5, A=1.3e-11, alpha=0.0, B_bias=(0.0, 0.0, B), dt=dt, nsteps=N,
+                  objective=W.J_PORT, comp=1, power=power, boxes=((0, 1, 0, 1), (0, 1, 0, 1)),
+                  weights=(0.8, -0.3), n_from=n_from)
+    J, _, _ = llg.Model(p, np.ones((1, 1, 1))).forward(np.array([1.0, 0.0, 0.0]), keep=False)
+    n = np.arange(n_from, N + 1)
+    expect = 0.5 * (np.sin(G * B * n * dt) ** power).sum()
+    assert J == pytest.approx(expect, rel=1e-9)
