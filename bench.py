@@ -38,7 +38,10 @@ METRIC = "LLG fwd+adjoint node-steps/s, FP32 batched vs FP64 plain on GB300; % H
 UNIT = "node-steps/s"
 
 # Algorithmic bytes per node per launch (FP32), the data each kernel must move
-# at least once: see DESIGN.md, "Kernels and their rooflines".
+# at least once (stage: spectrum 24+24, Y 12, psi 4, m 12, accumulator 9+9, outputs 12,
+# recorded field 6; column: 24 read + 24 written; adjoint: spectrum 24+24 plus the
+# stage's Y, Bbar, psi, adjoint state, gradient sums and next-stage records, averaged
+# over the four stages of a step).
 BYTES_PER_NODE = {0: 112.0, 1: 48.0, 2: 185.0}
 FAMILY = {0: "rows_kernel<float,ROW_STAGE> (inverse row FFT + field + RK4 stage + forward row FFT)",
           1: "cols16_kernel<float> (column FFT with 16-element lanes, tensor product, inverse column FFT)",

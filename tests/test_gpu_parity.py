@@ -62,7 +62,7 @@ def test_forward_adjoint_parity_small(shape, objective, precision, tol_m, tol_g)
 # The unit vector m at air nodes (psi -> 0) carries no magnetisation and its
 # motion is ill-conditioned: in the oracle a 1e-9 perturbation of m0 grows to
 # 3e-2 at nodes with psi ~ 1e-16 within 1000 steps while the magnetisation
-# M/Ms = psi m moves by 2e-9.  Parity on m is therefore judged on psi m.
+# M/Ms = psi m moves by 2e-9.  Parity on m is therefore measured on psi m.
 # FP64: rounding-order differences (FMA on the GPU, none in the oracle) stay
 # far below 1e-8 on psi m.
 @pytest.mark.parametrize("precision,tol_m,tol_g", [("fp64", 1e-8, 1e-7), ("fp32", 1e-5, 1e-4)])
