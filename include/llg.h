@@ -72,8 +72,8 @@ enum { LLG_INT_RK4 = 0, LLG_INT_DOPRI5 = 1 };
 
 /* One instance.  SI units (m, A/m, J/m, J/m^3, T, Hz, s). */
 typedef struct {
-  int nx, ny, nz;            /* nodes; nx % 4 == 0, 4 <= nx <= 1024,
-                                1 <= ny <= 512, 1 <= nz <= 8 (1 = film)        */
+  int nx, ny, nz;            /* nodes; nx % 4 == 0, 4 <= nx <= 1024 (FP64:
+                                780), 1 <= ny <= 512, 1 <= nz <= 8 (1 = film)  */
   double dx, dy, dz;         /* node spacing = cell size                       */
   double Ms, A, Ku;          /* saturation magnetisation, exchange, anisotropy */
   double ku[3];              /* anisotropy axis (normalised by the library)    */
@@ -170,9 +170,11 @@ typedef struct llg_ctx llg_ctx;
  * Every instance must have the same nsteps, n_from and dt.
  * Returns LLG_EINVAL for unsupported sizes (nx % 4 != 0, nx outside [4, 1024],
  * ny outside [1, 512], nz outside [1, 8], or a row or column tile that does
- * not fit in shared memory: a 3D grid's column tile holds all nz layers of
- * one padded column, so nz * Py <= 4096 in FP32 and <= 2048 in FP64, Py the
- * padded y extent), and LLG_ENOMEM if the scratch does not fit. */
+ * not fit in shared memory: the adjoint's row tile stages 7 node arrays over
+ * 3 rows, so nx <= 780 in FP64 (any allowed nx in FP32); a 3D grid's column
+ * tile holds all nz layers of one padded column, so nz * Py <= 4096 in FP32
+ * and <= 2048 in FP64, Py the padded y extent), and LLG_ENOMEM if the scratch
+ * does not fit. */
 llg_status llg_create(const llg_problem* inst, int n_inst, const llg_options* opt,
                       void* cuda_stream, llg_ctx** out);
 

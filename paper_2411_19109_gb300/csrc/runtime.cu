@@ -472,8 +472,11 @@ struct Engine final : llg_ctx {
       smem_adj = std::max(smem_adj, adj_smem_bytes<T>(Lx, P[i].nx));
     }
     smem = std::max(std::max(smem_rows, smem_adj), std::max(std::max(smem_cols, smem_c3), smem_misc));
+    if (std::max(smem_rows, smem_adj) > 220 * 1024)
+      return fail(LLG_EINVAL, "a row tile does not fit in shared memory (nx too large for this precision: the "
+                              "adjoint stages 7 node arrays over 3 rows; FP64 takes nx <= 780)");
     if (smem > 220 * 1024)
-      return fail(LLG_EINVAL, "a row or column tile does not fit in shared memory (3D: nz * 2ny too large for "
+      return fail(LLG_EINVAL, "a column tile does not fit in shared memory (3D: nz * 2ny too large for "
                               "this precision)");
     (void)Lx_max;
     (void)Py_max;

@@ -79,3 +79,37 @@ def test_adaptive_integrator_needs_the_terminal_objective(lib, p):
     with pytest.raises(LLGError) as e:
         llg_create([p()], integrator=1, rtol=1e-5, atol=1e-8)
     assert e.value.status == LLG_EINVAL
+
+
+def _wide(nx, nz=1, ny=8):
+    return W.random_small(12, 8, 1, seed=1, nsteps=N).problem.replace(nx=nx, ny=ny, nz=nz)
+
+
+@pytest.mark.parametrize("nx", [784, 1024])
+def test_fp64_rows_wider_than_the_adjoint_tile_are_rejected(lib, nx):
+    """FP64 adjoint row tile: 3840 exchange slots x 16 B + 7 arrays x 3 rows x nx x 8 B
+    + the W_2048 table (32 KB) exceeds 220 KB once nx > 780."""
+    from paper_2411_19109_gb300.llg import LLG_EINVAL, LLGError, llg_create
+    with pytest.raises(LLGError) as e:
+        llg_create([_wide(nx)], precision=1)
+    assert e.value.status == LLG_EINVAL and "row tile" in str(e.value)
+
+
+@pytest.mark.parametrize("nx,precision", [(780, 1), (1024, 0)])
+def test_widest_supported_rows_pass_the_size_checks(lib, nx, precision):
+    """Accepted by every host check: what follows is device work, so without a
+    GPU the call fails later, with a status other than LLG_EINVAL."""
+    import torch
+    from paper_2411_19109_gb300.llg import LLG_EINVAL, LLGError, llg_create
+    if torch.cuda.is_available():
+        pytest.skip("would allocate on the device")
+    with pytest.raises(LLGError) as e:
+        llg_create([_wide(nx)], precision=precision)
+    assert e.value.status != LLG_EINVAL
+
+
+def test_fp64_3d_column_tile_limit_is_reported_as_a_column_tile(lib):
+    from paper_2411_19109_gb300.llg import LLG_EINVAL, LLGError, llg_create
+    with pytest.raises(LLGError) as e:
+        llg_create([_wide(16, nz=4, ny=512)], precision=1)
+    assert e.value.status == LLG_EINVAL and "column tile" in str(e.value)
