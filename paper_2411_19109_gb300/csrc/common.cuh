@@ -38,19 +38,19 @@ template <> struct Cplx<float> { using type = float2; };
 template <> struct Cplx<double> { using type = double2; };
 template <typename T> using cplx = typename Cplx<T>::type;
 
-template <typename C> __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
+template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
   C r; r.x = a; r.y = b; return r;
 }
-template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
-template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
-template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
   return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
-template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
+template <typename C> __host__ __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
 // multiply by -i (forward) or +i (inverse)
-template <typename C> __device__ __forceinline__ C mul_mi(C a) { return mk<C>(a.y, -a.x); }
-template <typename C> __device__ __forceinline__ C mul_pi(C a) { return mk<C>(-a.y, a.x); }
+template <typename C> __host__ __device__ __forceinline__ C mul_mi(C a) { return mk<C>(a.y, -a.x); }
+template <typename C> __host__ __device__ __forceinline__ C mul_pi(C a) { return mk<C>(-a.y, a.x); }
 
 // Block-wide sum of a double; result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* red) {

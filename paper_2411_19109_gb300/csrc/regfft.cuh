@@ -21,21 +21,21 @@ namespace llg {
 
 
 template <typename C, int DIR>
-__device__ __forceinline__ C rf_tw(const C* __restrict__ tw, int m, int stride) {
+__host__ __device__ __forceinline__ C rf_tw(const C* __restrict__ tw, int m, int stride) {
   C w = tw[m * stride];
   if (DIR > 0) w.y = -w.y;
   return w;
 }
 
 template <typename C, int DIR>
-__device__ __forceinline__ void rf_dft2(C& a, C& b) {
+__host__ __device__ __forceinline__ void rf_dft2(C& a, C& b) {
   const C s = cadd(a, b), d = csub(a, b);
   a = s;
   b = d;
 }
 
 template <typename C, int DIR>
-__device__ __forceinline__ void rf_dft4(C& x0, C& x1, C& x2, C& x3) {
+__host__ __device__ __forceinline__ void rf_dft4(C& x0, C& x1, C& x2, C& x3) {
   C a = cadd(x0, x2), b = csub(x0, x2);
   C c = cadd(x1, x3), d = csub(x1, x3);
   d = (DIR < 0) ? mul_mi(d) : mul_pi(d);
@@ -47,7 +47,7 @@ __device__ __forceinline__ void rf_dft4(C& x0, C& x1, C& x2, C& x3) {
 
 // 8-point DFT in place: x[k] <- sum_j x[j] W_8^{jk}
 template <typename C, int DIR>
-__device__ __forceinline__ void rf_dft8(C x[8]) {
+__host__ __device__ __forceinline__ void rf_dft8(C x[8]) {
   using R = decltype(C::x);
   const R h = (R)0.70710678118654752440;
   C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
@@ -79,7 +79,7 @@ __device__ __forceinline__ void rf_dft8(C x[8]) {
 // v[b + r*(8/RP)], r < RP.  Returns the outputs in the same slots; `dst`
 // receives the shared-memory index of each slot's output.
 template <typename C, int L, int RP, int DIR>
-__device__ __forceinline__ void rf_pass(C v[8], int t, int Ns, const C* __restrict__ tw, int tws, int dst[8]) {
+__host__ __device__ __forceinline__ void rf_pass(C v[8], int t, int Ns, const C* __restrict__ tw, int tws, int dst[8]) {
   constexpr int TT = L / 8;
   constexpr int NB = 8 / RP;
 #pragma unroll
@@ -221,7 +221,7 @@ __device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int
 
 // a * W_16^M with W_16 = exp(DIR * 2 pi i / 16) (DIR = -1 forward), M fixed.
 template <typename C, int DIR, int M>
-__device__ __forceinline__ C rf_w16(C a) {
+__host__ __device__ __forceinline__ C rf_w16(C a) {
   using R = decltype(C::x);
   constexpr int m = M & 15;
   const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173, h = (R)0.70710678118654752440;
@@ -247,7 +247,7 @@ __device__ __forceinline__ C rf_w16(C a) {
 // 16-point DFT in place as 4 x 4: x[k1 + 4 k2] = sum_n2 W16^{n2 k1} W4^{n2 k2}
 // sum_n1 W4^{n1 k1} x[4 n1 + n2].
 template <typename C, int DIR>
-__device__ __forceinline__ void rf_dft16(C x[16]) {
+__host__ __device__ __forceinline__ void rf_dft16(C x[16]) {
   C a[4][4];
 #pragma unroll
   for (int n2 = 0; n2 < 4; ++n2) {
@@ -275,7 +275,7 @@ __device__ __forceinline__ void rf_dft16(C x[16]) {
 // One Stockham pass of radix RP on the sixteen registers of thread t
 // (butterfly b: j = t + TT*b, inputs v[b + r*(16/RP)]).
 template <typename C, int L, int RP, int DIR>
-__device__ __forceinline__ void rf_pass16(C v[16], int t, int Ns, const C* __restrict__ tw, int tws,
+__host__ __device__ __forceinline__ void rf_pass16(C v[16], int t, int Ns, const C* __restrict__ tw, int tws,
                                           const C* __restrict__ tw4, int dst[16]) {
   constexpr int TT = L / 16;
   constexpr int NB = 16 / RP;
