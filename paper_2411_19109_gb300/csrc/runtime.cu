@@ -392,7 +392,6 @@ struct Engine final : llg_ctx {
     N = P[0].nsteps;
     n_from = P[0].n_from;
     dt = P[0].dt;
-    int Lx_max = 0, Py_max = 0;
     for (int i = 0; i < n; ++i) {
       const llg_problem& p = P[i];
       char buf[256];
@@ -442,10 +441,6 @@ struct Engine final : llg_ctx {
       if (p.objective == LLG_J_PORT && (p.comp < 0 || p.comp > 2 || (p.power != 1 && p.power != 2)))
         return fail(LLG_EINVAL, "port objective needs comp in 0..2 and power 1 or 2");
       if (p.absorb_nodes < 0) return fail(LLG_EINVAL, "absorb_nodes must be >= 0");
-      const int Px = std::max(16, next_pow2(2 * p.nx));
-      const int Py = std::max(8, next_pow2(2 * p.ny));
-      Lx_max = std::max(Lx_max, Px / 2);
-      Py_max = std::max(Py_max, Py);
     }
     if (opt.precision != LLG_FP32 && opt.precision != LLG_FP64)
       return fail(LLG_EINVAL, "precision must be LLG_FP32 or LLG_FP64");
@@ -478,8 +473,6 @@ struct Engine final : llg_ctx {
     if (smem > 220 * 1024)
       return fail(LLG_EINVAL, "a column tile does not fit in shared memory (3D: nz * 2ny too large for "
                               "this precision)");
-    (void)Lx_max;
-    (void)Py_max;
     // descriptors, shapes, tiles
     struct Shape { int nx, ny, nz; double dx, dy, dz; long long off; int Px, Py, Pz; };
     std::vector<Shape> shapes;
