@@ -24,7 +24,7 @@ Phi > 0 = magnetic (psi -> 1) and Phi < 0 = air.
 from __future__ import annotations
 
 import dataclasses
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 from typing import List, Optional, Tuple
 
 import numpy as np
