@@ -144,3 +144,45 @@ def test_uniform_cube_cell_field_is_parallel():
     M[:, 0, 0, 0] = [3e5, -2e5, 5e5]
     B = dm.demag_field_fft(M, 5e-9, 5e-9, 5e-9)
     np.testing.assert_allclose(B[:, 0, 0, 0], -dm.MU0 * M[:, 0, 0, 0] / 3, rtol=1e-13)
+
+
+@pytest.mark.parametrize("cells", [(16, 4, 1), (20, 3, 2)])
+def test_long_prism_average_equals_aharoni(cells):
+    """Prisms longer than the near/far switch radius: 6 % (16 x 4 x 1) and
+    11 % (20 x 3 x 2) of N_xx come from cell pairs the quadrature branch
+    evaluates, so the sum pins that branch to about 1e-9."""
+    nx, ny, nz = cells
+    dx, dy, dz = 3e-9, 4e-9, 2.5e-9
+    z, y, x = [a.ravel() for a in np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")]
+    hmax = max(dx, dy, dz)
+    tot = np.zeros(6)
+    far_xx = 0.0
+    for i in range(x.size):
+        ox, oy, oz = x[i] - x, y[i] - y, z[i] - z
+        t = dm.demag_tensor(ox, oy, oz, dx, dy, dz)
+        tot += t.sum(axis=1)
+        far = (ox * dx) ** 2 + (oy * dy) ** 2 + (oz * dz) ** 2 >= (dm.NEAR_RADIUS * hmax) ** 2
+        far_xx += t[0][far].sum()
+    tot /= x.size
+    a, b, c = nx * dx / 2, ny * dy / 2, nz * dz / 2
+    assert abs(far_xx / x.size) > 0.05 * abs(tot[0])        # the far branch carries weight here
+    assert tot[0] == pytest.approx(aharoni_factor(b, c, a), rel=1e-10)
+    assert tot[1] == pytest.approx(aharoni_factor(c, a, b), rel=1e-10)
+    assert tot[2] == pytest.approx(aharoni_factor(a, b, c), rel=1e-10)
+    np.testing.assert_allclose(tot[3:], 0.0, atol=1e-12)
+
+
+def test_far_branch_equals_closed_form_elementwise():
+    """Every component of the quadrature branch, off-diagonals included
+    (which the prism sums cancel), against Newell's closed form just beyond
+    the switch radius, where the closed form still holds ~1e-10 ((R/h)^6 eps
+    cancellation)."""
+    h = (5e-9, 4e-9, 3e-9)
+    hmax = max(h)
+    offs = np.array([(7, 2, 1), (6, -3, 2), (-5, 5, 3), (2, 7, -4), (8, 1, 0), (0, 8, 2), (-4, -6, 5)])
+    for o in offs:
+        X, Y, Z = [np.array(float(k) * s) for k, s in zip(o, h)]
+        assert X * X + Y * Y + Z * Z >= (dm.NEAR_RADIUS * hmax) ** 2
+        q = dm.demag_tensor(np.array(o[0]), np.array(o[1]), np.array(o[2]), *h)
+        c = np.array(dm.tensor_newell(X, Y, Z, *h))
+        assert np.abs(q - c).max() < 2e-9 * np.abs(c).max(), o
