@@ -3,19 +3,23 @@
 // file instead of memory obtained from the CUDA allocator.
 //
 // Who needs it: code that must not allocate device memory at the point
-// where it wants a field evaluation -- for example while a stream is being
-// captured into a CUDA graph (cudaMalloc may not be called during capture),
-// inside a host application or framework that owns all device memory through
-// its own allocator, or in a latency-critical loop where the implicit
-// synchronisation of cudaMalloc/cudaFree would stall other streams.  The
-// caller still provides phi, m and the output B.
+// where it wants a field evaluation -- a host application or framework that
+// owns all device memory through its own allocator and budget, or a
+// latency-critical loop where the implicit synchronisation of
+// cudaMalloc/cudaFree would stall other streams.  The caller still provides
+// phi, m and the output B.
 //
 // The scratch below (about 5.3 MB) is a static __device__ object: every GPU
 // that loads this library holds it until the process exits.  It bounds the
 // grid to NA_MAX_N x NA_MAX_N nodes.  In host code the array's name is only a
 // host-side stand-in; its device address is looked up with
-// cudaGetSymbolAddress once per device (on the first call made with that
-// device current) and carved into the buffers the kernels use.
+// cudaGetSymbolAddress on every call (a host-side lookup) and carved into the
+// buffers the kernels use.  The twiddle tables are uploaded once per device,
+// and again if the address changes (a new context after a device reset).
+// Each call's descriptor and work tiles reach the device as kernel
+// arguments of a set-up kernel, not as copies from host memory.  The demag
+// spectrum is rebuilt only when the grid or cell size differs from the
+// previous call's on that device.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -69,7 +73,15 @@ static __device__ __align__(256) unsigned char g_field_scratch[NA_BYTES];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-unsigned char* g_scratch_dev[kMaxDevices] = {};   // device address of g_field_scratch per device
+// per device: the array's device address the twiddles were uploaded to, and
+// the grid whose demag spectrum the array holds
+struct DeviceState {
+  unsigned char* base = nullptr;
+  bool tensor_valid = false;
+  int nx = 0, ny = 0;
+  double dx = 0, dy = 0, dz = 0;
+};
+DeviceState g_state[kMaxDevices];
 
 int pow2_at_least(int v) {
   int p = 1;
@@ -82,14 +94,10 @@ int log2_of(int v) {
   return l;
 }
 
-// Once per device, with that device current: resolve the array's device
-// address and fill the twiddle tables (which never change afterwards).
+// With the device current: resolve the array's device address; on the
+// first call for this address fill the twiddle tables (synchronously) and
+// forget any demag spectrum.  Caller holds g_setup_mutex.
 llg_status setup_device(int dev, unsigned char** base, const char** msg) {
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (g_scratch_dev[dev]) {
-    *base = g_scratch_dev[dev];
-    return LLG_OK;
-  }
   void* p = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&p, g_field_scratch);
   if (e != cudaSuccess || p == nullptr) {
@@ -97,6 +105,11 @@ llg_status setup_device(int dev, unsigned char** base, const char** msg) {
     return LLG_ECUDA;
   }
   unsigned char* b = static_cast<unsigned char*>(p);
+  if (g_state[dev].base == b) {
+    *base = b;
+    return LLG_OK;
+  }
+  g_state[dev] = DeviceState{};
   static float2 htw[kTwiddleN];
   static double2 htw64[kTwiddleN];
   for (int k = 0; k < kTwiddleN; ++k) {
@@ -109,10 +122,21 @@ llg_status setup_device(int dev, unsigned char** base, const char** msg) {
     if (msg) *msg = "llg_field_noalloc: uploading the twiddle tables failed";
     return LLG_ECUDA;
   }
-  g_scratch_dev[dev] = b;
+  g_state[dev].base = b;
   *base = b;
   return LLG_OK;
 }
+
+// Writes the call's descriptor and its row and column tiles into the
+// scratch; everything arrives as kernel arguments.
+__global__ void noalloc_setup_kernel(DevInst d, int rows, int tx, DevInst* dI, RowTile* dRT, ColTile* dCT) {
+  const int i = threadIdx.x;
+  if (i == 0) *dI = d;
+  const int nrt = (d.ny + rows - 1) / rows, nct = (d.Lx + tx - 1) / tx;
+  if (i < nrt) dRT[i] = RowTile{0, 0, i * rows, min(rows, d.ny - i * rows), i};
+  if (i < nct) dCT[i] = ColTile{0, i * tx, min(tx, d.Lx - i * tx), 0};
+}
+static_assert(NA_MAX_ROW_TILES <= 128 && NA_MAX_COL_TILES <= 128, "one set-up thread per tile");
 
 }  // namespace
 
@@ -144,9 +168,11 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
     if (err_msg) *err_msg = "llg_field_noalloc: no usable current device";
     return LLG_ECUDA;
   }
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
   unsigned char* base = nullptr;
   llg_status s = setup_device(dev, &base, err_msg);
   if (s != LLG_OK) return s;
+  DeviceState& ds = g_state[dev];
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
   // descriptor and work tiles of this call (same layout rules as llg_create)
@@ -180,15 +206,12 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   d.absorb_x = p.absorb_x;
   d.absorb_y = p.absorb_y;
   d.V = p.dx * p.dy * p.dz;
-  RowTile rt[NA_MAX_ROW_TILES];
-  ColTile ct[NA_MAX_COL_TILES];
-  int nrt = 0, nct = 0;
   const int rows = rows_per_tile(d.Lx);
-  for (int y0 = 0; y0 < p.ny; y0 += rows, ++nrt) rt[nrt] = {0, 0, y0, std::min(rows, p.ny - y0), nrt};
+  const int nrt = (p.ny + rows - 1) / rows;
   d.ntile = nrt;
   d.tile_off = 0;
   const int tx = std::max(1, std::min(1024 / Py, d.Lx));
-  for (int k0 = 0; k0 < d.Lx; k0 += tx) ct[nct++] = {0, k0, tx, 0};
+  const int nct = (d.Lx + tx - 1) / tx;
 
   DevInst* dI = reinterpret_cast<DevInst*>(base + OFF_INST);
   RowTile* dRT = reinterpret_cast<RowTile*>(base + OFF_RT);
@@ -203,17 +226,26 @@ extern "C" llg_status llg_field_noalloc(const llg_problem* prob, const void* phi
   const double2* tw64 = reinterpret_cast<const double2*>(base + OFF_TW64);
 
   fill_coef(d);
-  cudaError_t e = cudaMemcpyAsync(dI, &d, sizeof d, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dRT, rt, sizeof(RowTile) * nrt, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dCT, ct, sizeof(ColTile) * nct, cudaMemcpyHostToDevice, st);
-  // the demag spectrum of this grid, FP64 on the device (G is cleared inside)
-  if (e == cudaSuccess)
+  noalloc_setup_kernel<<<1, 128, 0, st>>>(d, rows, tx, dI, dRT, dCT);
+  cudaError_t e = cudaGetLastError();
+  // the demag spectrum of this grid, FP64 on the device (G is cleared
+  // inside), unless the array already holds it from the previous call
+  const bool same = ds.tensor_valid && ds.nx == p.nx && ds.ny == p.ny && ds.dx == p.dx && ds.dy == p.dy &&
+                    ds.dz == p.dz;
+  if (e == cudaSuccess && !same) {
+    ds.tensor_valid = false;
     e = build_tensor_spectrum<float>(tens, G, p.nx, p.ny, 1, Px, Py, 1, p.dx, p.dy, p.dz, tw64, st);
-  // psi from phi (the per-tile psi partials are not used by the field)
+    if (e == cudaSuccess) {
+      ds.tensor_valid = true;
+      ds.nx = p.nx; ds.ny = p.ny;
+      ds.dx = p.dx; ds.dy = p.dy; ds.dz = p.dz;
+    }
+  }
   if (e != cudaSuccess) {
-    if (err_msg) *err_msg = "llg_field_noalloc: set-up copies or tensor build failed";
+    if (err_msg) *err_msg = "llg_field_noalloc: set-up kernel or tensor build failed";
     return LLG_ECUDA;
   }
+  // psi from phi (the per-tile psi partials are not used by the field)
   launch_material_tiles<float>(dI, dRT, nrt, static_cast<const float*>(phi_dev), psi, dpsi, psitile, nullptr, st);
 
   RowArgs<float> a;

@@ -1,15 +1,18 @@
 """llg_field_noalloc, the allocation-free field evaluation, against llg_field.
 
-Some callers cannot allocate device memory where they evaluate a field (while
-a stream is captured into a CUDA graph, inside a framework that owns all
-device memory, in a loop where cudaMalloc's synchronisation would stall
-other streams).  llg_field_noalloc serves them from a fixed scratch array in
-the library; it must give the same field as the context-based llg_field.
+Some callers cannot allocate device memory where they evaluate a field (a
+framework that owns all device memory through its own allocator, a loop
+where cudaMalloc's synchronisation would stall other streams).
+llg_field_noalloc serves them from a fixed scratch array in the library; it
+must give the same field as the context-based llg_field.
 
-Two calls in a row with different grids and modes check that the second call
-does not depend on what the first left in the shared scratch.  This file is
-collected last (test_zz_*) so that a run stopping at its first failure has
-already run every other test.
+Calls in a row with different grids and modes check that a call does not
+depend on what the previous one left in the shared scratch, and a repeated
+grid that the spectrum kept from the previous call is still right.  Grids at
+the scratch's bound (128 x 128) and with 128-point columns (64 x 64) compare
+its 8-element column kernel with the 16-element one llg_field takes there.
+This file is collected last (test_zz_*) so that a run stopping at its first
+failure has already run every other test.
 """
 import numpy as np
 import pytest
@@ -56,6 +59,16 @@ def test_noalloc_field_matches_llg_field_twice():
     b = _noalloc_field(second, 0.0, True)
     assert rel_l2(b, _reference_field(second, 0.0, True)) < TOL
     assert np.isfinite(a).all() and np.isfinite(b).all()
+
+
+def test_noalloc_field_at_the_scratch_bound():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required")
+    for shape, t, demag_only in (((128, 128), 1.0e-11, False), ((64, 64), 0.0, True), ((64, 64), 3.0e-11, False),
+                                 ((128, 128), 0.0, True)):
+        inst = W.random_small(*shape, 1, seed=shape[0] + int(demag_only))
+        a = _noalloc_field(inst, t, demag_only)
+        assert rel_l2(a, _reference_field(inst, t, demag_only)) < TOL, shape
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
