@@ -69,6 +69,26 @@ enum { LLG_J_PORT = 0, LLG_J_ENERGY_AREA = 1, LLG_J_SPECTRAL = 2, LLG_J_CURVE = 
 enum { LLG_FP32 = 0, LLG_FP64 = 1 };
 enum { LLG_CKPT_STORE_ALL = 0, LLG_CKPT_PERIODIC = 1, LLG_CKPT_BINOMIAL = 2 };
 enum { LLG_INT_RK4 = 0, LLG_INT_DOPRI5 = 1 };
+enum { LLG_SPEC_WORKING = 0, LLG_SPEC_DFLOAT = 1 };
+enum { LLG_TUNE_DEFAULT = 0, LLG_TUNE_MEASURE = 1, LLG_TUNE_GIVEN = 2 };
+
+/* Launch configuration of the hot kernels: which compiled variant of a
+ * kernel family runs and how the batch is split over streams.  Only
+ * col_lanes changes results (a different FFT radix order in the FP32
+ * column pass, so FP32 rounding differs); the others are bit-identical.
+ * Fields that do not apply to a context (col_lanes in FP64, the
+ * double-float fields without LLG_SPEC_DFLOAT) are ignored. */
+typedef struct {
+  int col_lanes;   /* FP32 film column pass at 128-, 256- and 1024-point
+                      columns: 16 (16-element FFT lanes, 192-thread blocks,
+                      one shared-memory exchange fewer) or 8 (8-element
+                      lanes, 384-thread blocks)                           */
+  int col_blocks;  /* double-float column pass: the blocks per SM its
+                      register cap is compiled for, 2 (80 registers) or 1  */
+  int adj_blocks;  /* double-float adjoint stage kernel: 2 or 1           */
+  int groups;      /* RK4 segments as 2 independent chains (even and odd
+                      instances on two streams) or 1                      */
+} llg_launch;
 
 /* One instance.  SI units (m, A/m, J/m, J/m^3, T, Hz, s). */
 typedef struct {
@@ -140,8 +160,12 @@ typedef struct {
                       slots s; 0 = ceil(sqrt(nsteps)) for both               */
   int use_graph;   /* 1 = replay captured CUDA graphs of whole segments
                       (ignored while time_kernels = 1)                        */
-  int rows_per_cta;/* reserved (tile rows follow from the row FFT length)      */
-  int cols_per_cta;/* reserved (tile columns follow from the column FFT length) */
+  int tune;        /* launch configuration (llg_launch): LLG_TUNE_DEFAULT
+                      {16, 2, 2, 2}; LLG_TUNE_MEASURE: llg_create times each
+                      field's candidates on this batch (the kernel families
+                      they change, a few ms) and keeps the fastest, cached
+                      per device and batch shape for the process;
+                      LLG_TUNE_GIVEN: `launch` below as given             */
   int time_kernels;/* 1 = bracket every stage-kernel launch with CUDA events    */
   int integrator;  /* LLG_INT_RK4: fixed step dt for nsteps steps.
                       LLG_INT_DOPRI5: adaptive step size (Methods), the
@@ -160,13 +184,32 @@ typedef struct {
                       sine drive (no drive table); ckpt is ignored,
                       use_graph replays captured attempts.                   */
   double rtol, atol; /* LLG_INT_DOPRI5 tolerances                            */
+  int adj_spectral;  /* frequency domain of the adjoint's demag transpose
+                        (the row and column FFTs, the stored spectrum and the
+                        tensor spectrum it is multiplied by):
+                        LLG_SPEC_WORKING in the working precision;
+                        LLG_SPEC_DFLOAT (FP32 contexts, films, RK4) in
+                        double-float, hi + lo FP32 pairs (about 48 bits),
+                        while the node arrays stay FP32.  FP32 rounding of a
+                        Fourier coefficient perturbs the transform at every
+                        node by about 1e-7 of the whole field's norm, which
+                        drowns the adjoint field far from where the
+                        objective excites it (the design region between the
+                        demultiplexer's ports and its source); double-float
+                        brings that to about 1e-14.  The forward pass and
+                        the per-node arithmetic are unchanged.              */
+  llg_launch launch; /* LLG_TUNE_GIVEN: the configuration to use          */
 } llg_options;
 
 typedef struct llg_ctx llg_ctx;
 
-/* Validate `n_inst` problems, build the per-shape demag spectra (FP64 on the
- * device, stored in the working precision), pick tile shapes and allocate all
- * scratch.  `cuda_stream` is a cudaStream_t (NULL = default stream).
+/* Set up the problem of the Methods section for `n_inst` instances: the
+ * material map of Eq. 4, the effective field of Eq. 11 (exchange, anisotropy,
+ * Zeeman, demag) and the objective.  Validates the problems, builds the
+ * per-shape demag spectra (FP64 on the device, stored in the working
+ * precision, and in double-float for LLG_SPEC_DFLOAT), allocates all scratch
+ * and fixes the launch configuration (llg_options.tune; llg_launch_config
+ * reports it).  `cuda_stream` is a cudaStream_t (NULL = default stream).
  * Every instance must have the same nsteps, n_from and dt.
  * Returns LLG_EINVAL for unsupported sizes (nx % 4 != 0, nx outside [4, 1024],
  * ny outside [1, 512], nz outside [1, 8], or a row or column tile that does
@@ -178,7 +221,10 @@ typedef struct llg_ctx llg_ctx;
 llg_status llg_create(const llg_problem* inst, int n_inst, const llg_options* opt,
                       void* cuda_stream, llg_ctx** out);
 
-/* Forward pass: psi from phi, RK4 for nsteps from m0, J per instance.
+/* Forward pass (Eq. 4, then Eq. 11 integrated by RK4, and the objective:
+ * the port functional, Eq. 9's energy and size terms, Eq. 10's spectral
+ * sum or Eq. 8's magnetisation curve): psi from phi, nsteps from m0, J per
+ * instance.
  * J_host: [n_inst] doubles (required).  mT_dev: final m (nullable).
  * Keeps the checkpoints that llg_adjoint needs. */
 llg_status llg_forward(llg_ctx* ctx, const void* phi_dev, const void* m0_dev,
@@ -191,25 +237,41 @@ llg_status llg_forward(llg_ctx* ctx, const void* phi_dev, const void* m0_dev,
 llg_status llg_adaptive_steps(llg_ctx* ctx, int inst, double* t_host, double* h_host, long long cap,
                               long long* count);
 
-/* Reverse sweep after llg_forward on the same inputs: writes dJ/dPhi
- * (all nodes, unmasked) to dJdphi_dev and, if non-NULL, dJ/dm0 to dJdm0_dev.
- * LLG_ESTATE if no forward pass precedes it. */
-llg_status llg_adjoint(llg_ctx* ctx, void* dJdphi_dev, void* dJdm0_dev);
+/* Reverse sweep after llg_forward on the same inputs: the adjoint-state
+ * recursion (Eq. 6) and the parameter integral (Eq. 7) in their exact
+ * discrete form through the RK4 stages, then dJ/dPhi = a psi (1 - psi) dJ/dpsi
+ * (Eq. 4).  Writes dJ/dPhi (all nodes, unmasked) to dJdphi_dev and, if
+ * non-NULL, dJ/dm0 to dJdm0_dev.  dJ_dextra (nullable, n_inst host doubles):
+ * the cotangent of each instance's J under a combination made outside the
+ * library (e.g. Eq. 10 as the sum of the two frequency runs of a candidate,
+ * or an autograd graph above J); the outputs are then the gradients of
+ * sum_i dJ_dextra[i] J_i, instance by instance.  NULL means 1 for every
+ * instance.  LLG_ESTATE if no forward pass precedes it, LLG_EINVAL for a
+ * non-finite dJ_dextra. */
+llg_status llg_adjoint(llg_ctx* ctx, const double* dJ_dextra, void* dJdphi_dev, void* dJdm0_dev);
 
-/* Eq. 5 on the design mask, Phi <- Phi - lr grad, then Phi <- Phi / max|Phi|
+/* Level-set update (Eq. 5, and the renormalisation of the Results section's
+ * level-set method) on the design mask, Phi <- Phi - lr grad, then Phi <- Phi / max|Phi|
  * over the mask, per instance (an instance whose masked max is 0 is left
  * unscaled).  Nodes outside the mask are not touched. */
 llg_status levelset_step(llg_ctx* ctx, void* phi_dev, const void* grad_dev,
                          const unsigned char* mask_dev, double lr);
 
-/* Effective field B (tesla) of the magnetisation m_dev at time t for all
- * instances, psi taken from phi_dev; demag_only != 0 returns B_d alone.
+/* Effective field B (tesla) of Eq. 11 (Methods: exchange, anisotropy,
+ * Zeeman, demag) of the magnetisation m_dev at time t for all instances,
+ * psi taken from phi_dev (Eq. 4); demag_only != 0 returns B_d alone.
  * Layout of m_dev and B_dev as m0.  Diagnostic entry point for parity tests. */
 llg_status llg_field(llg_ctx* ctx, const void* phi_dev, const void* m_dev, double t,
                      int demag_only, void* B_dev);
 
+/* The launch configuration the context runs (llg_options.tune), and the
+ * host time (ms) llg_create spent timing candidates (0 if none). */
+llg_status llg_launch_config(llg_ctx* ctx, llg_launch* out, double* tune_ms);
+
 /* Bytes the context holds on the device, and the device time (ms) of the last
- * llg_forward / llg_adjoint call. */
+ * llg_forward / llg_adjoint call.  (This and the calls below up to
+ * llg_destroy are measurement and housekeeping; the paper has no
+ * counterpart.) */
 llg_status llg_query(llg_ctx* ctx, size_t* device_bytes, double* last_ms);
 
 /* Number of kernels the context has launched since llg_create. */
@@ -226,12 +288,13 @@ const char* llg_last_error(llg_ctx* ctx);
 void llg_destroy(llg_ctx* ctx);
 
 /* Effective field of one FP32 instance without any device allocation.
- * There is no counterpart in the paper: this entry point exists for callers
- * that must not allocate device memory where they need a field evaluation,
- * e.g. during CUDA stream capture (cudaMalloc is not allowed there), inside a
- * host framework that owns all device memory, or in a latency-critical loop
- * where cudaMalloc/cudaFree would synchronise other streams.
- * Same result as llg_field (same kernels) for a single instance, FP32 only.
+ * There is no counterpart in the paper.  It serves callers that cannot
+ * allocate device memory where they need a field evaluation: a host
+ * application or framework that owns all device memory through its own
+ * allocator and budget, or a latency-critical loop where cudaMalloc/cudaFree
+ * would synchronise the device and stall other streams.
+ * Same result as llg_field for a single instance, FP32 only (the 8-element
+ * column kernel at every column length).
  * prob: the instance (nsteps, objective fields are ignored); phi_dev [ny*nx],
  * m_dev [3][ny][nx] and B_dev [3][ny][nx] are caller-owned float device
  * buffers (m_dev and B_dev 16-byte aligned); cuda_stream is a cudaStream_t
@@ -240,12 +303,16 @@ void llg_destroy(llg_ctx* ctx);
  * by every GPU that loads the library until the process exits.  It limits the
  * grid to nz == 1, nx a multiple of 4 with 4 <= nx <= 128 and 1 <= ny <= 128;
  * larger grids return LLG_EINVAL.  No cudaMalloc, cudaFree or allocating
- * library call is made.  The first call on a device (with that device
+ * library call is made; the call's descriptor and work tiles reach the
+ * device as kernel arguments.  The first call on a device (with that device
  * current) looks up the array's device address and uploads constant tables,
- * synchronously: make that first call before any stream capture.  All calls
- * on a device share the array and leave their contents in it; calls that
- * overlap on the GPU (different streams, no ordering) race with each other.
- * On error *err_msg (if non-NULL) points to a static description. */
+ * synchronously: make that first call before any stream capture.  The demag
+ * spectrum (FP64 set-up kernels) is rebuilt only when the grid or cell size
+ * differs from the previous call's on that device.  All calls on a device
+ * share the array and leave their contents in it; calls that overlap on the
+ * GPU (different streams, no ordering) race with each other.  A device reset
+ * is not supported: the host-side record of what the array holds would be
+ * stale.  On error *err_msg (if non-NULL) points to a static description. */
 llg_status llg_field_noalloc(const llg_problem* prob, const void* phi_dev, const void* m_dev, double t,
                              int demag_only, void* B_dev, void* cuda_stream, const char** err_msg);
 

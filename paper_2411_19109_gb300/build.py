@@ -20,7 +20,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libllg_gb300.so")
 SOURCES = ("k_stage_f32.cu", "k_adj_f32.cu", "k_stage_f64.cu", "k_adj_f64.cu", "k_rowmisc_f32.cu",
            "k_rowmisc_f64.cu", "k_cols_f32.cu", "k_cols_f64.cu", "k_cols3_f32.cu", "k_cols3_f64.cu", "k_cols16_f32.cu",
-           "tensor.cu", "k_misc.cu", "runtime.cu", "noalloc.cu", "rbf.cu", "peak.cu", "k_dp_f32.cu", "k_dp_f64.cu")
+           "tensor.cu", "k_misc.cu", "runtime.cu", "noalloc.cu", "rbf.cu", "peak.cu", "k_dp_f32.cu", "k_dp_f64.cu",
+           "k_adj_df.cu", "k_cols_df.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

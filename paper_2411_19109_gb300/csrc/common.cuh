@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
+
 namespace llg {
 
 constexpr double kMu0 = 1.2566370614359173e-06;     // 4 pi 1e-7
@@ -36,6 +38,7 @@ __host__ __device__ constexpr int pz_of(int nz) {
 template <typename T> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };
 template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<dfloat> { using type = dcplx; };
 template <typename T> using cplx = typename Cplx<T>::type;
 
 template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
@@ -175,10 +178,11 @@ __host__ __device__ constexpr size_t stage_smem_bytes(int L, int nx) {
   return (size_t)kExch * sizeof(cplx<T>) + (size_t)4 * (rows_per_tile(L) + 2) * nx * sizeof(T) +
          (size_t)2 * L * sizeof(cplx<T>);
 }
-template <typename T>
+// S: the real type of the adjoint's frequency domain (T, or dfloat).
+template <typename T, typename S = T>
 __host__ __device__ constexpr size_t adj_smem_bytes(int L, int nx) {
-  return (size_t)kExch * sizeof(cplx<T>) + (size_t)7 * (rows_per_tile(L) + 2) * nx * sizeof(T) +
-         (size_t)2 * L * sizeof(cplx<T>);
+  return (size_t)kExch * sizeof(cplx<S>) + (size_t)7 * (rows_per_tile(L) + 2) * nx * sizeof(T) +
+         (size_t)2 * L * sizeof(cplx<S>);
 }
 
 

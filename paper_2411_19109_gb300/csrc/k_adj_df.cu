@@ -1,0 +1,9 @@
+// Explicit instantiations of the adjoint stage kernel with FP32 node arrays
+// and a double-float frequency domain (own translation unit so that it
+// compiles in parallel with the others).
+#include "kernels_impl.cuh"
+
+namespace llg {
+template void launch_adj<float, dfloat>(const AdjArgs<float, dfloat>&, int, size_t, cudaStream_t, bool, int);
+template void smem_adj<float, dfloat>(size_t);
+}  // namespace llg

@@ -3,6 +3,6 @@
 #include "kernels_impl.cuh"
 
 namespace llg {
-template void launch_adj<float>(const AdjArgs<float>&, int, size_t, cudaStream_t, bool);
+template void launch_adj<float>(const AdjArgs<float>&, int, size_t, cudaStream_t, bool, int);
 template void smem_adj<float>(size_t);
 }  // namespace llg

@@ -3,6 +3,6 @@
 #include "kernels_impl.cuh"
 
 namespace llg {
-template void launch_adj<double>(const AdjArgs<double>&, int, size_t, cudaStream_t, bool);
+template void launch_adj<double>(const AdjArgs<double>&, int, size_t, cudaStream_t, bool, int);
 template void smem_adj<double>(size_t);
 }  // namespace llg

@@ -84,12 +84,15 @@ __host__ __device__ constexpr size_t cols_smem_bytes(int Py) {
   return (size_t)(kExch + Py) * sizeof(cplx<T>) + (size_t)(1024 / Py + 1) * (Py / 2 + 1) * 4 * sizeof(T);
 }
 
-template <typename T>
+// S: the real type of the adjoint's frequency domain (spectrum, twiddles and
+// FFT arithmetic of the demag transpose): T itself, or dfloat for FP32 node
+// arrays with a double-float spectrum.
+template <typename T, typename S = T>
 struct AdjArgs {
   const DevInst* inst;
   const RowTile* tiles;
-  cplx<T>* spec;
-  const cplx<T>* tw;
+  cplx<S>* spec;
+  const cplx<S>* tw;
   const T* psi;
   const T* Ys;        // Y_s of this stage (halo)
   const T* Bbar;      // Bbar_s (halo)
@@ -121,8 +124,10 @@ struct AdjArgs {
 
 template <typename T>
 void launch_rows(const RowArgs<T>& a, int mode, int ntiles, size_t smem, cudaStream_t st, bool z3);
+// mb: the register-cap variant (blocks per SM it is compiled for; an
+// unknown value takes the type's default)
 template <typename T>
-void launch_cols(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+void launch_cols(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, int mb = 0);
 // film column pass with 16 register elements per lane (FP32, Py = 128, 256, 1024)
 template <typename T>
 void launch_cols16(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
@@ -148,15 +153,15 @@ __host__ __device__ constexpr size_t cols3_smem_bytes(int Py, int nz, int ncols)
   return ((size_t)3 * nz * ncols * (rf_padded_len(Py) + 1) + Py + 16) * sizeof(cplx<T>);
 }
 
-template <typename T>
-void launch_adj(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3);
+template <typename T, typename S = T>
+void launch_adj(const AdjArgs<T, S>& a, int ntiles, size_t smem, cudaStream_t st, bool z3, int mb = 0);
 template <typename T, int MODE>
 void launch_rows_mode(const RowArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3);
 template <typename T, int MODE>
 void smem_rows_mode(size_t smem);
 template <typename T>
 void smem_cols(size_t smem);
-template <typename T>
+template <typename T, typename S = T>
 void smem_adj(size_t smem);
 // Dormand-Prince adjoint stages, reverse-sweep gather, and step control
 template <typename T>
@@ -177,7 +182,8 @@ void launch_material_tiles(const DevInst* inst, const RowTile* tiles, int ntiles
                            T* dpsi, double* psitile, double* psimom, cudaStream_t st);
 template <typename T>
 void launch_grad_finish_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* dpsi,
-                              const T* psib, const T* psic, T* out, cudaStream_t st);
+                              const T* psib, const T* psic, const double* w, T* out, const T* lam, T* dm0,
+                              cudaStream_t st);
 template <typename T>
 void launch_levelset_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, T* phi, const T* grad,
                            const unsigned char* mask, double lr, unsigned int* maxbits, cudaStream_t st);

@@ -221,6 +221,11 @@ __device__ __forceinline__ void load_tensor_smem(const double* tab, int idx, dou
   const double2 b = reinterpret_cast<const double2*>(tab)[2 * idx + 1];
   n[0] = a.x; n[1] = a.y; n[2] = b.x; n[3] = b.y;
 }
+__device__ __forceinline__ void load_tensor_smem(const dfloat* tab, int idx, dfloat n[4]) {
+  const float4 a = reinterpret_cast<const float4*>(tab)[2 * idx];
+  const float4 b = reinterpret_cast<const float4*>(tab)[2 * idx + 1];
+  n[0] = dfloat(a.x, a.y); n[1] = dfloat(a.z, a.w); n[2] = dfloat(b.x, b.y); n[3] = dfloat(b.z, b.w);
+}
 __device__ __forceinline__ void load_tensor(const double* tab, long long idx, double n[4]) {
   const double2 a = __ldg(reinterpret_cast<const double2*>(tab) + 2 * idx);
   const double2 b = __ldg(reinterpret_cast<const double2*>(tab) + 2 * idx + 1);
@@ -328,8 +333,12 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kColThreads, sizeof(T) == 4 ? 3 : 1) cols_kernel(ColArgs<T> a) {
+// MB: the blocks per SM the kernel is compiled for (its register cap):
+// FP32 3; FP64 1; double-float 1 or 2 (launch-configuration candidates:
+// 32 registers of FFT values per lane make the register cap a trade
+// between occupancy and spills).
+template <typename T, int MB>
+__global__ void __launch_bounds__(kColThreads, MB) cols_kernel(ColArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ DevInst sI;
@@ -893,10 +902,17 @@ __global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? ((Z3 || MODE >= 
 // [W_{2L}^k, k < 2L].
 // ---------------------------------------------------------------------------
 
-template <typename T, int L, bool Z3, bool DP>
-__device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, const RowTile& tile,
+// Conversions between a node value (T) and the frequency domain's real
+// type (S): identity, or the double-float pair of an FP32 value and back.
+template <typename T> __device__ __forceinline__ T spec_to(T v) { return v; }
+template <typename T> __device__ __forceinline__ T spec_to(dfloat v) { return v.to_float(); }
+template <typename T> __device__ __forceinline__ T spec_to(double v) { return (T)v; }
+template <typename S, typename T> __device__ __forceinline__ S spec_from(T v) { return S(v); }
+
+template <typename T, typename S, int L, bool Z3, bool DP>
+__device__ __forceinline__ void adj_body(const AdjArgs<T, S>& a, const DevInst& I, const RowTile& tile,
                                          unsigned char* smem_raw, uint64_t* bars) {
-  using C = cplx<T>;
+  using C = cplx<S>;
   using G = RowGeom<L>;
   constexpr int RM = G::RM;
   constexpr int GS = group_stride(L);
@@ -916,7 +932,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   C* tw2 = reinterpret_cast<C*>(sP + (RM + 2) * nx);
   C* sE = sx + g.rl * 3 * GS;
   C* grp = sE + g.c * GS;
-  T* sEr = reinterpret_cast<T*>(sE);
+  S* sEr = reinterpret_cast<S*>(sE);
   C* row0 = a.spec + I.spec_off + ((long long)z * ny + y0) * 3 * L;
   const long long n = (a.step_base ? *a.step_base : 0) + a.local_step;
   const int s = a.stage;
@@ -976,7 +992,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
   if (!seed) {
     mbar_wait(&bars[0], 0, a.err);
     C v[8];
-    row_inverse_comp<T, L>(v, grp, active, grp, g.t, tw2);
+    row_inverse_comp<S, L>(v, grp, active, grp, g.t, tw2);
   }
   mbar_wait(&bars[1], 0, a.err);
   __syncthreads();
@@ -1067,7 +1083,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
       T D[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        D[c] = sEr[2 * c * GS + sl];
+        D[c] = spec_to<T>(sEr[2 * c * GS + sl]);
         gg[c] += Ms * pi * D[c];
       }
       qpsi += Ms * dot3(yi, D);
@@ -1142,40 +1158,42 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T>& a, const DevInst& I, 
       const long long id = off3 + c * nodes + n0;
       gbo[id] = bbar[c];
       ggp[id] = gl[c];
-      sEr[2 * c * GS + sl] = bbar[c];
+      sEr[2 * c * GS + sl] = spec_from<S>(bbar[c]);
     }
   }
   if (!emit) return;
   __syncthreads();
-  row_forward_comp<T, L>(grp, nx / 2, a.spec + I.spec_off + ((long long)z * ny + y) * 3 * L + g.c * L, active, g.t,
+  row_forward_comp<S, L>(grp, nx / 2, a.spec + I.spec_off + ((long long)z * ny + y) * 3 * L + g.c * L, active, g.t,
                          tw2);
 }
 
-template <typename T, bool Z3, bool DP>
-__device__ __forceinline__ void adj_dispatch(const AdjArgs<T>& a, const DevInst& I, const RowTile& tile,
+template <typename T, typename S, bool Z3, bool DP>
+__device__ __forceinline__ void adj_dispatch(const AdjArgs<T, S>& a, const DevInst& I, const RowTile& tile,
                                              unsigned char* smem_raw, uint64_t* bars) {
   switch (I.log2Lx) {
-    case 3: adj_body<T, 8, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 4: adj_body<T, 16, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 5: adj_body<T, 32, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 6: adj_body<T, 64, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 7: adj_body<T, 128, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 8: adj_body<T, 256, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 9: adj_body<T, 512, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 10: adj_body<T, 1024, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 3: adj_body<T, S, 8, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 4: adj_body<T, S, 16, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 5: adj_body<T, S, 32, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 6: adj_body<T, S, 64, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 7: adj_body<T, S, 128, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 8: adj_body<T, S, 256, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 9: adj_body<T, S, 512, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 10: adj_body<T, S, 1024, Z3, DP>(a, I, tile, smem_raw, bars); break;
     default: break;
   }
 }
 
-template <typename T, bool Z3>
-__global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? 2 : 1) adj_kernel(AdjArgs<T> a) {
+// MB: blocks per SM the adjoint stage kernel is compiled for: FP32 2;
+// FP64 1; FP32 with a double-float frequency domain 1 or 2 (candidates).
+template <typename T, typename S, bool Z3, int MB>
+__global__ void __launch_bounds__(kAdjThreads, MB) adj_kernel(AdjArgs<T, S> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ DevInst sI;
   __shared__ uint64_t bars[2];
   const RowTile tile = a.tiles[blockIdx.x];
   load_inst(sI, a.inst + tile.inst);
   __syncthreads();
-  adj_dispatch<T, Z3, false>(a, sI, tile, smem_raw, bars);
+  adj_dispatch<T, S, Z3, false>(a, sI, tile, smem_raw, bars);
 }
 
 // adjoint stage of a Dormand-Prince step (stages 6..1; the seed at stage 6)
@@ -1187,7 +1205,7 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? 2 : 1) adj_dp_ke
   const RowTile tile = a.tiles[blockIdx.x];
   load_inst(sI, a.inst + tile.inst);
   __syncthreads();
-  adj_dispatch<T, Z3, true>(a, sI, tile, smem_raw, bars);
+  adj_dispatch<T, T, Z3, true>(a, sI, tile, smem_raw, bars);
 }
 
 // ---------------------------------------------------------------------------
@@ -1224,17 +1242,26 @@ __global__ void material_kernel(const DevInst* inst, const RowTile* tiles, const
   }
 }
 
+// dJ/dPhi = a psi (1 - psi) (sum - compensation) of the Kahan pair, times the
+// instance's cotangent w (nullable: 1); with dm0 also dJ/dm0 = w lambda_0.
 template <typename T>
 __global__ void grad_finish_kernel(const DevInst* inst, const RowTile* tiles, const T* dpsi, const T* psib,
-                                   const T* psic, T* out) {
+                                   const T* psic, const double* w, T* out, const T* lam, T* dm0) {
   const RowTile tile = tiles[blockIdx.x];
   const DevInst& I = inst[tile.inst];
   const long long base = tile_base(I, tile);
   const int cnt = tile.nrows * I.nx;
+  const double wi = w ? w[tile.inst] : 1.0;
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
     const double g = ((double)psib[base + e] - (double)psic[base + e]) * (double)dpsi[base + e];
-    out[base + e] = (T)g;
+    out[base + e] = (T)(wi * g);
   }
+  if (!dm0) return;
+  for (int c = 0; c < 3; ++c)
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const long long id = 3 * I.node_off + (long long)c * I.nodes + (base - I.node_off) + e;
+      dm0[id] = w ? (T)(wi * (double)lam[id]) : lam[id];
+    }
 }
 
 __device__ __forceinline__ void atomic_max_abs(unsigned int* p, float v) {
@@ -1302,25 +1329,44 @@ void smem_rows_mode(size_t smem) {
   raise_smem_limit(reinterpret_cast<const void*>(rows_kernel<T, MODE, false>), &cur, smem);
   raise_smem_limit(reinterpret_cast<const void*>(rows_kernel<T, MODE, true>), &cur3, smem);
 }
+// Register-cap variants compiled per type: the first is the default.
+template <typename T> struct Variants { static constexpr int a = 1, b = 1; };
+template <> struct Variants<float> { static constexpr int a = 3, b = 3; };
+template <> struct Variants<dfloat> { static constexpr int a = 2, b = 1; };
+template <typename T, typename S> struct AdjVariants { static constexpr int a = 1, b = 1; };
+template <> struct AdjVariants<float, float> { static constexpr int a = 2, b = 2; };
+template <> struct AdjVariants<float, dfloat> { static constexpr int a = 2, b = 1; };
+
 template <typename T>
-void launch_cols(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st) {
-  cols_kernel<T><<<ntiles, kColThreads, smem, st>>>(a);
+void launch_cols(const ColArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, int mb) {
+  if (mb == Variants<T>::b) cols_kernel<T, Variants<T>::b><<<ntiles, kColThreads, smem, st>>>(a);
+  else cols_kernel<T, Variants<T>::a><<<ntiles, kColThreads, smem, st>>>(a);
 }
 template <typename T>
 void smem_cols(size_t smem) {
-  static size_t cur = 0;
-  raise_smem_limit(reinterpret_cast<const void*>(cols_kernel<T>), &cur, smem);
+  static size_t cur = 0, cur2 = 0;
+  raise_smem_limit(reinterpret_cast<const void*>(cols_kernel<T, Variants<T>::a>), &cur, smem);
+  raise_smem_limit(reinterpret_cast<const void*>(cols_kernel<T, Variants<T>::b>), &cur2, smem);
 }
-template <typename T>
-void launch_adj(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3) {
-  if (z3) adj_kernel<T, true><<<ntiles, kAdjThreads, smem, st>>>(a);
-  else adj_kernel<T, false><<<ntiles, kAdjThreads, smem, st>>>(a);
+template <typename T, typename S>
+void launch_adj(const AdjArgs<T, S>& a, int ntiles, size_t smem, cudaStream_t st, bool z3, int mb) {
+  constexpr int A = AdjVariants<T, S>::a, B = AdjVariants<T, S>::b;
+  if (mb == B && B != A) {
+    if (z3) adj_kernel<T, S, true, B><<<ntiles, kAdjThreads, smem, st>>>(a);
+    else adj_kernel<T, S, false, B><<<ntiles, kAdjThreads, smem, st>>>(a);
+  } else {
+    if (z3) adj_kernel<T, S, true, A><<<ntiles, kAdjThreads, smem, st>>>(a);
+    else adj_kernel<T, S, false, A><<<ntiles, kAdjThreads, smem, st>>>(a);
+  }
 }
-template <typename T>
+template <typename T, typename S>
 void smem_adj(size_t smem) {
-  static size_t cur = 0, cur3 = 0;
-  raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, false>), &cur, smem);
-  raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, true>), &cur3, smem);
+  constexpr int A = AdjVariants<T, S>::a, B = AdjVariants<T, S>::b;
+  static size_t cur[4] = {0, 0, 0, 0};
+  raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, S, false, A>), &cur[0], smem);
+  raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, S, true, A>), &cur[1], smem);
+  raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, S, false, B>), &cur[2], smem);
+  raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, S, true, B>), &cur[3], smem);
 }
 template <typename T>
 void launch_adj_dp(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3) {
@@ -1363,8 +1409,9 @@ void launch_material_tiles(const DevInst* inst, const RowTile* tiles, int ntiles
 }
 template <typename T>
 void launch_grad_finish_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* dpsi,
-                              const T* psib, const T* psic, T* out, cudaStream_t st) {
-  grad_finish_kernel<T><<<ntiles, 256, 0, st>>>(inst, tiles, dpsi, psib, psic, out);
+                              const T* psib, const T* psic, const double* w, T* out, const T* lam, T* dm0,
+                              cudaStream_t st) {
+  grad_finish_kernel<T><<<ntiles, 256, 0, st>>>(inst, tiles, dpsi, psib, psic, w, out, lam, dm0);
 }
 template <typename T>
 void launch_levelset_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, T* phi, const T* grad,

@@ -15,11 +15,14 @@
 // or binomial checkpointing with a fixed number of snapshot slots, which
 // trades more recomputation for memory independent of the segment length.
 #include <algorithm>
+#include <chrono>
 #include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -151,6 +154,11 @@ int next_pow2(int v) {
   while (p < v) p <<= 1;
   return p;
 }
+
+// Launch configurations chosen by timing (LLG_TUNE_MEASURE), per process,
+// keyed by device, precision, adjoint spectrum and the batch's grid shapes.
+std::mutex g_tune_mutex;
+std::map<std::string, llg_launch> g_tune_cache;
 int ilog2(int v) {
   int l = 0;
   while ((1 << l) < v) ++l;
@@ -163,7 +171,7 @@ struct llg_ctx {
   std::string err;
   virtual ~llg_ctx() {}
   virtual llg_status forward(const void* phi, const void* m0, double* J, void* mT) = 0;
-  virtual llg_status adjoint(void* dphi, void* dm0) = 0;
+  virtual llg_status adjoint(const double* wext, void* dphi, void* dm0) = 0;
   virtual llg_status adaptive_steps(int inst, double* t, double* h, long long cap, long long* count) = 0;
   virtual llg_status levelset(void* phi, const void* grad, const unsigned char* mask, double lr) = 0;
   virtual llg_status field(const void* phi, const void* m, double t, int demag_only, void* B) = 0;
@@ -171,6 +179,8 @@ struct llg_ctx {
   virtual double last_ms() const = 0;
   virtual long long launches() const = 0;
   virtual void kernel_time(int family, long long* count, double* ms) = 0;
+  llg_launch L{16, 2, 2, 2};   // the launch configuration in use
+  double tune_ms = 0.0;        // host time spent timing candidates at create
 };
 
 template <typename T>
@@ -209,6 +219,14 @@ struct Engine final : llg_ctx {
   T *psib = nullptr, *psic = nullptr;
   C *spec = nullptr, *tw = nullptr;
   double2* tw64 = nullptr;
+  // double-float frequency domain of the adjoint's demag transpose (FP32
+  // contexts with llg_options.adj_spectral = LLG_SPEC_DFLOAT): its own
+  // spectrum pool, twiddle table and tensor tables (hi + lo pairs of the
+  // FP64-built spectra)
+  bool adj_df = false;
+  dcplx *spec_df = nullptr, *tw_df = nullptr;
+  dfloat* tens_df = nullptr;
+  size_t smem_cols_df = 0, smem_adj_df = 0;
   // per-(step, row tile) objective partials, per-row-tile terminal and psi
   // partials, per-instance J
   double *slots = nullptr, *jterm = nullptr, *psitile = nullptr, *Jd = nullptr, *rf = nullptr;
@@ -241,6 +259,7 @@ struct Engine final : llg_ctx {
   long long total_slots = 0;
   long long* step_base = nullptr;
   unsigned int* maxbits = nullptr;
+  double* wext = nullptr;   // per-instance cotangents of J (llg_adjoint's dJ_dextra)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -447,6 +466,25 @@ struct Engine final : llg_ctx {
     if (opt.ckpt != LLG_CKPT_PERIODIC && opt.ckpt != LLG_CKPT_STORE_ALL && opt.ckpt != LLG_CKPT_BINOMIAL)
       return fail(LLG_EINVAL, "ckpt must be LLG_CKPT_PERIODIC, LLG_CKPT_STORE_ALL or LLG_CKPT_BINOMIAL");
     if (opt.seg_len < 0) return fail(LLG_EINVAL, "seg_len must be >= 0");
+    if (opt.adj_spectral != LLG_SPEC_WORKING && opt.adj_spectral != LLG_SPEC_DFLOAT)
+      return fail(LLG_EINVAL, "adj_spectral must be LLG_SPEC_WORKING or LLG_SPEC_DFLOAT");
+    adj_df = opt.adj_spectral == LLG_SPEC_DFLOAT;
+    if (opt.tune != LLG_TUNE_DEFAULT && opt.tune != LLG_TUNE_MEASURE && opt.tune != LLG_TUNE_GIVEN)
+      return fail(LLG_EINVAL, "tune must be LLG_TUNE_DEFAULT, LLG_TUNE_MEASURE or LLG_TUNE_GIVEN");
+    if (opt.tune == LLG_TUNE_GIVEN) {
+      const llg_launch& g = opt.launch;
+      if ((g.col_lanes != 8 && g.col_lanes != 16) || (g.col_blocks != 1 && g.col_blocks != 2) ||
+          (g.adj_blocks != 1 && g.adj_blocks != 2) || (g.groups != 1 && g.groups != 2))
+        return fail(LLG_EINVAL, "launch: col_lanes 8 or 16, col_blocks, adj_blocks and groups 1 or 2");
+      L = g;
+    }
+    if (adj_df) {
+      if (!std::is_same<T, float>::value)
+        return fail(LLG_EINVAL, "the double-float adjoint spectrum is an option of LLG_FP32 contexts");
+      if (dp_mode) return fail(LLG_EINVAL, "the double-float adjoint spectrum applies to the RK4 adjoint");
+      for (int i = 0; i < n_inst; ++i)
+        if (probs[i].nz != 1) return fail(LLG_EINVAL, "the double-float adjoint spectrum supports films (nz = 1)");
+    }
 
     // Tile shapes follow from the register FFTs: one component of a row FFT
     // of length Lx takes Lx/8 threads, so a 384-thread block covers 1024/Lx
@@ -465,7 +503,13 @@ struct Engine final : llg_ctx {
       smem_misc = std::max(smem_misc, (size_t)(kExch + 2 * Lx) * sizeof(C));
       smem_rows = std::max(smem_rows, stage_smem_bytes<T>(Lx, P[i].nx));
       smem_adj = std::max(smem_adj, adj_smem_bytes<T>(Lx, P[i].nx));
+      if (adj_df) {
+        smem_cols_df = std::max(smem_cols_df, cols_smem_bytes<dfloat>(Py));
+        smem_adj_df = std::max(smem_adj_df, adj_smem_bytes<float, dfloat>(Lx, P[i].nx));
+      }
     }
+    if (std::max(smem_cols_df, smem_adj_df) > 220 * 1024)
+      return fail(LLG_EINVAL, "a double-float adjoint tile does not fit in shared memory");
     smem = std::max(std::max(smem_rows, smem_adj), std::max(std::max(smem_cols, smem_c3), smem_misc));
     if (std::max(smem_rows, smem_adj) > 220 * 1024)
       return fail(LLG_EINVAL, "a row tile does not fit in shared memory (nx too large for this precision: the "
@@ -600,7 +644,9 @@ struct Engine final : llg_ctx {
 
     const size_t S = slot();
     for (const RowTile& t : rt) (H[t.inst].nz > 1 ? rt3 : rt2).push_back(t);
-    two_groups = n >= 2 && !opt.time_kernels;
+    // the partitioned tile lists exist for every batch of two or more, so
+    // that the number of chains can be chosen (or timed) after set-up
+    const bool can_split = n >= 2;
     bool ok = alloc(&dI, n) && alloc(&dRT, rt.size()) && alloc(&dRT2, std::max<size_t>(1, rt2.size())) &&
               alloc(&dRT3, std::max<size_t>(1, rt3.size())) && alloc(&dCT, std::max<size_t>(1, ct.size())) &&
               alloc(&dCT3, std::max<size_t>(1, ct3.size())) && alloc(&dCT16, std::max<size_t>(1, ct16.size())) && alloc(&psi, total_nodes) &&
@@ -613,9 +659,12 @@ struct Engine final : llg_ctx {
               alloc(&pslots, any_spec ? 2 * (size_t)total_slots : 2) && alloc(&Pd, (size_t)n * 2 * (N + 1)) &&
               alloc(&wtab, (size_t)n * 2 * (N + 1)) &&
               alloc(&jterm, rt.size()) && alloc(&psitile, rt.size()) && alloc(&psimom, 2 * rt.size()) && alloc(&Jd, n) && alloc(&step_base, 1) &&
-              alloc(&maxbits, 2 * n) && alloc(&rf, (size_t)n * 3 * (N + 1)) && alloc(&errw, 1);
+              alloc(&maxbits, 2 * n) && alloc(&rf, (size_t)n * 3 * (N + 1)) && alloc(&errw, 1) &&
+              alloc(&wext, n);
     if (!ok) return fail(LLG_ENOMEM, "device allocation failed (" + std::to_string(bytes >> 20) + " MiB so far)");
-    if (two_groups) {
+    if (adj_df && !(alloc(&spec_df, total_spec) && alloc(&tw_df, kTwiddleN) && alloc(&tens_df, total_tens)))
+      return fail(LLG_ENOMEM, "device allocation failed (double-float adjoint spectrum)");
+    if (can_split) {
       // partitioned copies of the tile lists: even instances first
       auto even_r = [](const RowTile& t) { return t.inst % 2 == 0; };
       auto even_c = [](const ColTile& t) { return t.inst % 2 == 0; };
@@ -692,6 +741,14 @@ struct Engine final : llg_ctx {
         return cuda_fail(e, "upload twiddles");
       if ((e = cudaMemcpyAsync(tw, hT.data(), sizeof(C) * kTwiddleN, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "upload twiddles");
+      std::vector<dcplx> hD(adj_df ? kTwiddleN : 0);
+      for (size_t k = 0; k < hD.size(); ++k) {
+        hD[k].x = dfloat(h64[k].x);
+        hD[k].y = dfloat(h64[k].y);
+      }
+      if (adj_df &&
+          (e = cudaMemcpyAsync(tw_df, hD.data(), sizeof(dcplx) * kTwiddleN, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "upload twiddles");
       if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "create");
     }
     {
@@ -721,6 +778,11 @@ struct Engine final : llg_ctx {
       e = build_tensor_spectrum<T>(tens + s.off, Gs, s.nx, s.ny, s.nz, s.Px, s.Py, s.Pz, s.dx, s.dy, s.dz, tw64,
                                    st);
       nlaunch += s.Pz > 1 ? 6 : 5;
+      if (e == cudaSuccess && adj_df) {
+        e = build_tensor_spectrum<dfloat>(tens_df + s.off, Gs, s.nx, s.ny, s.nz, s.Px, s.Py, s.Pz, s.dx, s.dy, s.dz,
+                                          tw64, st);
+        nlaunch += 5;
+      }
       if (e != cudaSuccess) {
         cudaFree(Gs);
         return cuda_fail(e, "demag tensor");
@@ -730,7 +792,7 @@ struct Engine final : llg_ctx {
     cudaFree(Gs);
     if (e != cudaSuccess) return cuda_fail(e, "demag tensor");
     set_smem_limits<T>(smem_rows, smem_misc, smem_cols, smem_adj);
-    if (two_groups) {
+    if (can_split) {
       if ((e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking)) != cudaSuccess ||
           (e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
           (e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming)) != cudaSuccess)
@@ -739,10 +801,109 @@ struct Engine final : llg_ctx {
     cudaMemsetAsync(wtab, 0, sizeof(double) * n * 2 * (N + 1), st);
     smem_cols3<T>(smem_c3);
     if constexpr (sizeof(T) == 4) smem_cols16<T>(smem_cols);
+    if constexpr (std::is_same<T, float>::value) {
+      if (adj_df) {
+        llg::smem_cols<dfloat>(smem_cols_df);
+        llg::smem_adj<float, dfloat>(smem_adj_df);
+      }
+    }
     cudaMemsetAsync(errw, 0, sizeof(int), st);
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "create");
+    if (opt.tune == LLG_TUNE_MEASURE)
+      if (llg_status ts = tune(shapes_key())) return ts;
+    two_groups = can_split && L.groups == 2 && !opt.time_kernels;
+    return LLG_OK;
+  }
+
+  // ------------------------------------------------------------ tuning
+  // Cache key: device, precision, adjoint spectrum, grid shapes with counts.
+  std::string shapes_key() const {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::map<std::vector<double>, int> cnt;
+    for (const llg_problem& p : P) ++cnt[{(double)p.nx, (double)p.ny, (double)p.nz, p.dx, p.dy, p.dz}];
+    std::string k = std::to_string(dev) + "/" + std::to_string(sizeof(T)) + "/" + std::to_string(adj_df ? 1 : 0);
+    char buf[160];
+    for (const auto& c : cnt) {
+      snprintf(buf, sizeof buf, "/%gx%gx%g:%g:%g:%g*%d", c.first[0], c.first[1], c.first[2], c.first[3], c.first[4],
+               c.first[5], c.second);
+      k += buf;
+    }
+    return k;
+  }
+  // median device time (ms) of `reps` runs of fn on the context stream
+  template <typename F>
+  double time_ms(F&& fn, int reps) {
+    std::vector<float> v;
+    fn();   // warm-up (and module load of the variant)
+    for (int r = 0; r < reps; ++r) {
+      cudaEventRecord(ev0, st);
+      fn();
+      cudaEventRecord(ev1, st);
+      cudaEventSynchronize(ev1);
+      float f = 0.f;
+      cudaEventElapsedTime(&f, ev0, ev1);
+      v.push_back(f);
+    }
+    std::sort(v.begin(), v.end());
+    return v[v.size() / 2];
+  }
+  // Coordinate search over the launch configuration on this batch: each
+  // field's alternative is timed on the launches it changes (kernel
+  // contents do not affect their speed; the buffers hold whatever set-up
+  // left) and kept if it is faster.  One recorded RK4 step and its
+  // reverse sweep serve as the workload of the chain split.
+  llg_status tune(const std::string& key) {
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        L = it->second;
+        return LLG_OK;
+      }
+    }
+    if (N < 1 || dp_mode || opt.time_kernels) return LLG_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    // defined contents for the timed launches (set-up left them unset)
+    for (T* b : {m, psi, dpsi, lam, G, gpart, bb[0], bb[1], psib, psic})
+      cudaMemsetAsync(b, 0, sizeof(T) * (b == psi || b == dpsi || b == psib || b == psic ? total_nodes : slot()), st);
+    const int reps = 5;
+    const bool two = n >= 2;
+    auto pick = [&](int* field, int alt, auto&& fn) {
+      const int cur = *field;
+      const double a = time_ms(fn, reps);
+      *field = alt;
+      const double b = time_ms(fn, reps);
+      if (!(b < 0.98 * a)) *field = cur;
+    };
+    set_step(0);
+    if (std::is_same<T, float>::value && !ct16.empty())
+      pick(&L.col_lanes, L.col_lanes == 16 ? 8 : 16, [&] { cols(); });
+    if (adj_df) {
+      pick(&L.col_blocks, L.col_blocks == 2 ? 1 : 2, [&] { cols_df(); });
+      cudaMemcpyAsync(recY_slot(0), m, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
+      step(0, true, false);
+      pick(&L.adj_blocks, L.adj_blocks == 2 ? 1 : 2, [&] { reverse_segment(1); });
+    }
+    if (two) {
+      two_groups = L.groups == 2;
+      const int alt = L.groups == 2 ? 1 : 2;
+      const double a = time_ms([&] { segment_body(SEG_RECORD_ADJ, 1); segment_body(SEG_REVERSE, 1); }, reps);
+      two_groups = alt == 2;
+      const double b = time_ms([&] { segment_body(SEG_RECORD_ADJ, 1); segment_body(SEG_REVERSE, 1); }, reps);
+      if (b < 0.98 * a) L.groups = alt;
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch configuration timing");
+    int herr = 0;
+    cudaMemcpy(&herr, errw, sizeof(int), cudaMemcpyDeviceToHost);
+    if (herr) return fail(LLG_ETIMEOUT, "a bounded device wait ran out while timing launch configurations");
+    tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = L;
     return LLG_OK;
   }
 
@@ -799,8 +960,10 @@ struct Engine final : llg_ctx {
     }
     if constexpr (sizeof(T) == 4) {
       if (p16.second) {
+        // the same tiles (1024/Py columns each) for either lane width
         c.tiles = (grp_sel < 0 ? dCT16 : dCT16p) + p16.first;
-        launch_cols16<T>(c, (int)p16.second, smem_cols, st);
+        if (L.col_lanes == 16) launch_cols16<T>(c, (int)p16.second, smem_cols, st);
+        else launch_cols<T>(c, (int)p16.second, smem_cols, st);
         ++nlaunch;
       }
     }
@@ -810,6 +973,33 @@ struct Engine final : llg_ctx {
       ++nlaunch;
     }
     time_end(1);
+  }
+  // column pass of the adjoint's double-float frequency domain: every film
+  // column tile (both film tile lists; the same columns per tile) through
+  // the 8-element column kernel instantiated for dfloat
+  void cols_df() {
+    if constexpr (std::is_same<T, float>::value) {
+      ColArgs<dfloat> c;
+      c.inst = dI;
+      c.spec = spec_df;
+      c.tw = tw_df;
+      c.tens = tens_df;
+      c.cols_max = TX;
+      c.err = errw;
+      time_begin(1);
+      const auto pc = part(ct.size(), split_ct), p16 = part(ct16.size(), split_ct16);
+      if (pc.second) {
+        c.tiles = (grp_sel < 0 ? dCT : dCTp) + pc.first;
+        launch_cols<dfloat>(c, (int)pc.second, smem_cols_df, st, L.col_blocks);
+        ++nlaunch;
+      }
+      if (p16.second) {
+        c.tiles = (grp_sel < 0 ? dCT16 : dCT16p) + p16.first;
+        launch_cols<dfloat>(c, (int)p16.second, smem_cols_df, st, L.col_blocks);
+        ++nlaunch;
+      }
+      time_end(1);
+    }
   }
   void set_step(long long v) {
     launch_set_step(step_base, v, st);
@@ -854,11 +1044,22 @@ struct Engine final : llg_ctx {
   }
 
   // one backward sweep over a recorded segment of len steps: seed with the
-  // stage-4 inputs of its last step, then the 4 len adjoint stages
+  // stage-4 inputs of its last step, then the 4 len adjoint stages; S is
+  // the real type of the demag transpose's frequency domain
   void reverse_segment(long long len) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (adj_df) {
+        reverse_segment_t<dfloat>(len);
+        return;
+      }
+    }
+    reverse_segment_t<T>(len);
+  }
+  template <typename S>
+  void reverse_segment_t(long long len) {
     int cur = 0;
     {
-      AdjArgs<T> a = adj_args();
+      AdjArgs<T, S> a = adj_args<S>();
       a.local_step = (int)(len - 1);
       a.stage = 4;
       a.seed_only = 1;
@@ -869,8 +1070,9 @@ struct Engine final : llg_ctx {
     }
     for (long long l = len - 1; l >= 0; --l) {
       for (int s = 4; s >= 1; --s) {
-        cols();
-        AdjArgs<T> a = adj_args();
+        if constexpr (std::is_same<S, T>::value) cols();
+        else cols_df();
+        AdjArgs<T, S> a = adj_args<S>();
         a.local_step = (int)l;
         a.stage = s;
         a.Ys = recY_slot(4 * l + s - 1);
@@ -1233,7 +1435,7 @@ struct Engine final : llg_ctx {
   // reverses its step cnt_i - 1 - r (or idles with h = 0): recompute the six
   // stages from its checkpoint, seed kappa_6 = h b_6 lambda, then adjoint
   // stages 6..1 (eta_s kept for the lower stages, lambda += sum eta at 1)
-  llg_status adjoint_dp(void* dphi, void* dm0) {
+  llg_status adjoint_dp(const double* dw, void* dphi, void* dm0) {
     cudaEventRecord(ev0, st);
     long long Kmax = 0;
     for (int i = 0; i < n; ++i) Kmax = std::max(Kmax, (long long)dp_cnt_h[i]);
@@ -1241,9 +1443,9 @@ struct Engine final : llg_ctx {
       set_step(r);
       if (llg_status st2 = run_segment(SEG_DP_REVERSE, 1)) return st2;
     }
-    launch_grad_finish_tiles<T>(dI, dRT, (int)rt.size(), dpsi, psib, psic, static_cast<T*>(dphi), st);
+    launch_grad_finish_tiles<T>(dI, dRT, (int)rt.size(), dpsi, psib, psic, dw, static_cast<T*>(dphi), lam,
+                                static_cast<T*>(dm0), st);
     ++nlaunch;
-    if (dm0) cudaMemcpyAsync(dm0, lam, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
     cudaEventRecord(ev1, st);
     int herr = 0;
     cudaMemcpyAsync(&herr, errw, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1345,13 +1547,19 @@ struct Engine final : llg_ctx {
   }
 
   // ------------------------------------------------------------ adjoint
-  AdjArgs<T> adj_args() {
-    AdjArgs<T> a;
+  template <typename S = T>
+  AdjArgs<T, S> adj_args() {
+    AdjArgs<T, S> a;
     std::memset(&a, 0, sizeof a);
     a.inst = dI;
     a.tiles = dRT;
-    a.spec = spec;
-    a.tw = tw;
+    if constexpr (std::is_same<S, T>::value) {
+      a.spec = spec;
+      a.tw = tw;
+    } else {
+      a.spec = spec_df;
+      a.tw = tw_df;
+    }
     a.psi = psi;
     a.gpart = gpart;
     a.lam = lam;
@@ -1381,27 +1589,44 @@ struct Engine final : llg_ctx {
     }
     time_end(2);
   }
-  void adj(const AdjArgs<T>& a0) {
-    AdjArgs<T> a = a0;
+  template <typename S>
+  void adj(const AdjArgs<T, S>& a0) {
+    AdjArgs<T, S> a = a0;
+    const size_t sm = std::is_same<S, T>::value ? smem_adj : smem_adj_df;
+    const int mb = std::is_same<S, T>::value ? 0 : L.adj_blocks;
     time_begin(2);
     const auto p2 = part(rt2.size(), split_rt2), p3 = part(rt3.size(), split_rt3);
     if (p2.second) {
       a.tiles = (grp_sel < 0 ? dRT2 : dRT2p) + p2.first;
-      launch_adj<T>(a, (int)p2.second, smem_adj, st, false);
+      launch_adj<T, S>(a, (int)p2.second, sm, st, false, mb);
       ++nlaunch;
     }
     if (p3.second) {
       a.tiles = (grp_sel < 0 ? dRT3 : dRT3p) + p3.first;
-      launch_adj<T>(a, (int)p3.second, smem_adj, st, true);
+      launch_adj<T, S>(a, (int)p3.second, sm, st, true, mb);
       ++nlaunch;
     }
     time_end(2);
   }
 
-  llg_status adjoint(void* dphi, void* dm0) override {
+  // the per-instance cotangents (nullptr: all 1) for grad_finish
+  llg_status upload_wext(const double* w, const double** dw) {
+    *dw = nullptr;
+    if (!w) return LLG_OK;
+    for (int i = 0; i < n; ++i)
+      if (!std::isfinite(w[i])) return fail(LLG_EINVAL, "dJ_dextra must be finite");
+    cudaError_t e = cudaMemcpyAsync(wext, w, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "upload dJ_dextra");
+    *dw = wext;
+    return LLG_OK;
+  }
+
+  llg_status adjoint(const double* w, void* dphi, void* dm0) override {
     if (!have_fwd) return fail(LLG_ESTATE, "llg_adjoint needs a preceding llg_forward");
     if (!dphi) return fail(LLG_EINVAL, "dJdphi must not be NULL");
-    if (dp_mode) return adjoint_dp(dphi, dm0);
+    const double* dw = nullptr;
+    if (llg_status s = upload_wext(w, &dw)) return s;
+    if (dp_mode) return adjoint_dp(dw, dphi, dm0);
     cudaEventRecord(ev0, st);
     // The working state m (with the spectrum of its stage-1 input) is what
     // RESTORE loads, ADVANCE moves, SNAP saves and RECORD starts from.
@@ -1423,9 +1648,9 @@ struct Engine final : llg_ctx {
         if (llg_status s = run_segment(SEG_REVERSE, ac.a - ac.b)) return s;
       }
     }
-    launch_grad_finish_tiles<T>(dI, dRT, (int)rt.size(), dpsi, psib, psic, static_cast<T*>(dphi), st);
+    launch_grad_finish_tiles<T>(dI, dRT, (int)rt.size(), dpsi, psib, psic, dw, static_cast<T*>(dphi), lam,
+                                static_cast<T*>(dm0), st);
     ++nlaunch;
-    if (dm0) cudaMemcpyAsync(dm0, lam, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
     cudaEventRecord(ev1, st);
     int herr = 0;
     cudaMemcpyAsync(&herr, errw, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1509,9 +1734,16 @@ llg_status llg_forward(llg_ctx* ctx, const void* phi_dev, const void* m0_dev, do
   return ctx->forward(phi_dev, m0_dev, J_host, mT_dev);
 }
 
-llg_status llg_adjoint(llg_ctx* ctx, void* dJdphi_dev, void* dJdm0_dev) {
+llg_status llg_adjoint(llg_ctx* ctx, const double* dJ_dextra, void* dJdphi_dev, void* dJdm0_dev) {
   if (!ctx) return LLG_EINVAL;
-  return ctx->adjoint(dJdphi_dev, dJdm0_dev);
+  return ctx->adjoint(dJ_dextra, dJdphi_dev, dJdm0_dev);
+}
+
+llg_status llg_launch_config(llg_ctx* ctx, llg_launch* out, double* tune_ms) {
+  if (!ctx || !out) return LLG_EINVAL;
+  *out = ctx->L;
+  if (tune_ms) *tune_ms = ctx->tune_ms;
+  return LLG_OK;
 }
 
 llg_status llg_adaptive_steps(llg_ctx* ctx, int inst, double* t_host, double* h_host, long long cap,
@@ -1586,6 +1818,6 @@ int llg_padded_extents(int nx, int ny, int* Px, int* Py) {
   return 0;
 }
 
-int llg_abi_version(void) { return 1; }
+int llg_abi_version(void) { return 2; }
 
 }  // extern "C"

@@ -218,6 +218,8 @@ template __global__ void tensor_pack_kernel<float>(const double2*, float*, int, 
 template __global__ void tensor_pack_kernel<double>(const double2*, double*, int, int);
 template __global__ void tensor_pack3_kernel<float>(const double2*, float*, int, int, int);
 template __global__ void tensor_pack3_kernel<double>(const double2*, double*, int, int, int);
+template __global__ void tensor_pack_kernel<dfloat>(const double2*, dfloat*, int, int);
+template __global__ void tensor_pack3_kernel<dfloat>(const double2*, dfloat*, int, int, int);
 
 // Elements of T in the packed spectrum table of one grid shape.
 long long tensor_table_len(int Px, int Py, int Pz) {
@@ -273,6 +275,8 @@ cudaError_t build_tensor_spectrum(T* table, double2* G, int nx, int ny, int nz, 
 template cudaError_t build_tensor_spectrum<float>(float*, double2*, int, int, int, int, int, int, double, double,
                                                   double, const double2*, cudaStream_t);
 template cudaError_t build_tensor_spectrum<double>(double*, double2*, int, int, int, int, int, int, double, double,
+                                                   double, const double2*, cudaStream_t);
+template cudaError_t build_tensor_spectrum<dfloat>(dfloat*, double2*, int, int, int, int, int, int, double, double,
                                                    double, const double2*, cudaStream_t);
 
 }  // namespace llg

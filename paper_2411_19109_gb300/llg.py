@@ -26,11 +26,14 @@ LLG_J_PORT, LLG_J_ENERGY_AREA, LLG_J_SPECTRAL, LLG_J_CURVE = 0, 1, 2, 3
 LLG_FP32, LLG_FP64 = 0, 1
 LLG_CKPT_STORE_ALL, LLG_CKPT_PERIODIC, LLG_CKPT_BINOMIAL = 0, 1, 2
 LLG_INT_RK4, LLG_INT_DOPRI5 = 0, 1
+LLG_SPEC_WORKING, LLG_SPEC_DFLOAT = 0, 1
+LLG_TUNE_DEFAULT, LLG_TUNE_MEASURE, LLG_TUNE_GIVEN = 0, 1, 2
 
 EXPORTED = ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query",
             "llg_launch_count", "llg_kernel_time", "llg_last_error", "llg_destroy", "llg_schedule",
             "llg_padded_extents", "llg_abi_version", "llg_field_noalloc", "llg_rbf_workspace_bytes",
-            "llg_rbf_phi", "llg_rbf_grad", "llg_adam_step", "llg_fp64_fma_rate", "llg_adaptive_steps")
+            "llg_rbf_phi", "llg_rbf_grad", "llg_adam_step", "llg_fp64_fma_rate", "llg_adaptive_steps",
+            "llg_launch_config")
 
 
 class llg_rbf(ctypes.Structure):
@@ -56,10 +59,17 @@ class llg_problem(ctypes.Structure):
                 ("centre_target", c_double * 2)]
 
 
+class llg_launch(ctypes.Structure):
+    _fields_ = [("col_lanes", c_int), ("col_blocks", c_int), ("adj_blocks", c_int), ("groups", c_int)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 class llg_options(ctypes.Structure):
     _fields_ = [("precision", c_int), ("ckpt", c_int), ("seg_len", c_int), ("use_graph", c_int),
-                ("rows_per_cta", c_int), ("cols_per_cta", c_int), ("time_kernels", c_int), ("integrator", c_int),
-                ("rtol", c_double), ("atol", c_double)]
+                ("tune", c_int), ("time_kernels", c_int), ("integrator", c_int),
+                ("rtol", c_double), ("atol", c_double), ("adj_spectral", c_int), ("launch", llg_launch)]
 
 
 class LLGError(RuntimeError):
@@ -88,7 +98,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     P = ctypes.POINTER
     lib.llg_create.argtypes = [P(llg_problem), c_int, P(llg_options), c_void_p, P(c_void_p)]
     lib.llg_forward.argtypes = [c_void_p, c_void_p, c_void_p, P(c_double), c_void_p]
-    lib.llg_adjoint.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.llg_adjoint.argtypes = [c_void_p, _PD, c_void_p, c_void_p]
+    lib.llg_launch_config.argtypes = [c_void_p, ctypes.POINTER(llg_launch), _PD]
+    lib.llg_launch_config.restype = c_int
     lib.levelset_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double]
     lib.llg_field.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_int, c_void_p]
     lib.llg_query.argtypes = [c_void_p, P(ctypes.c_size_t), P(c_double)]
@@ -181,13 +193,15 @@ def _check(lib, ctx, st):
 # ---- thin wrappers with the C names -------------------------------------
 
 def llg_create(problems: Sequence, precision=LLG_FP32, ckpt=LLG_CKPT_PERIODIC, seg_len=0,
-               stream=0, rows_per_cta=0, cols_per_cta=0, use_graph=0, time_kernels=0,
-               integrator=LLG_INT_RK4, rtol=1e-6, atol=1e-9) -> int:
+               stream=0, tune=LLG_TUNE_DEFAULT, use_graph=0, time_kernels=0,
+               integrator=LLG_INT_RK4, rtol=1e-6, atol=1e-9, adj_spectral=LLG_SPEC_WORKING,
+               launch=None) -> int:
     lib = load()
     structs = [to_struct(p) for p in problems]          # hold the host arrays until create returns
     arr = (llg_problem * len(problems))(*structs)
-    opt = llg_options(precision, ckpt, seg_len, use_graph, rows_per_cta, cols_per_cta, time_kernels, integrator,
-                      rtol, atol)
+    lc = llg_launch(**launch) if launch else llg_launch(16, 2, 2, 2)
+    opt = llg_options(precision, ckpt, seg_len, use_graph, tune, time_kernels, integrator,
+                      rtol, atol, adj_spectral, lc)
     ctx = c_void_p()
     st = lib.llg_create(arr, len(problems), ctypes.byref(opt), c_void_p(stream), ctypes.byref(ctx))
     if st != LLG_OK:
@@ -206,9 +220,20 @@ def llg_forward(ctx: int, phi_ptr: int, m0_ptr: int, n_inst: int, mT_ptr: int = 
     return np.array(J[:])
 
 
-def llg_adjoint(ctx: int, dphi_ptr: int, dm0_ptr: int = 0) -> None:
+def llg_adjoint(ctx: int, dphi_ptr: int, dm0_ptr: int = 0, dJ_dextra=None) -> None:
+    """dJ_dextra: optional per-instance cotangents of J (host sequence)."""
     lib = load()
-    _check(lib, ctx, lib.llg_adjoint(c_void_p(ctx), c_void_p(dphi_ptr), c_void_p(dm0_ptr or None)))
+    w = None if dJ_dextra is None else (c_double * len(dJ_dextra))(*[float(v) for v in dJ_dextra])
+    _check(lib, ctx, lib.llg_adjoint(c_void_p(ctx), w, c_void_p(dphi_ptr), c_void_p(dm0_ptr or None)))
+
+
+def llg_launch_config(ctx: int):
+    """(launch configuration as a dict, ms spent timing candidates at create)."""
+    lib = load()
+    out = llg_launch()
+    ms = c_double()
+    _check(lib, ctx, lib.llg_launch_config(c_void_p(ctx), ctypes.byref(out), ctypes.byref(ms)))
+    return out.as_dict(), ms.value
 
 
 def levelset_step(ctx: int, phi_ptr: int, grad_ptr: int, mask_ptr: int, lr: float) -> None:
@@ -347,9 +372,11 @@ class Solver:
     [sum 3 n_i] with each instance laid out [3][ny][nx])."""
 
     def __init__(self, problems: Sequence, precision: str = "fp32", ckpt: str = "periodic",
-                 seg_len: int = 0, stream=None, rows_per_cta: int = 0, cols_per_cta: int = 0,
+                 seg_len: int = 0, stream=None, tune: str = "default", launch=None,
                  time_kernels: bool = False, use_graph: bool = True, integrator: str = "rk4",
-                 rtol: float = 1e-6, atol: float = 1e-9):
+                 rtol: float = 1e-6, atol: float = 1e-9, adj_spectral: str = "working"):
+        """tune: "default", "measure" (time launch candidates at create) or
+        "given" (use `launch`, a dict of llg_launch fields)."""
         import torch
         self.torch = torch
         self.problems = list(problems)
@@ -358,8 +385,10 @@ class Solver:
         ck = {"periodic": LLG_CKPT_PERIODIC, "store_all": LLG_CKPT_STORE_ALL, "binomial": LLG_CKPT_BINOMIAL}[ckpt]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         integ = {"rk4": LLG_INT_RK4, "dopri5": LLG_INT_DOPRI5}[integrator]
+        spec = {"working": LLG_SPEC_WORKING, "dfloat": LLG_SPEC_DFLOAT}[adj_spectral]
+        tn = {"default": LLG_TUNE_DEFAULT, "measure": LLG_TUNE_MEASURE, "given": LLG_TUNE_GIVEN}[tune]
         self.ctx = llg_create(self.problems, prec, ck, seg_len, self.stream.cuda_stream,
-                              rows_per_cta, cols_per_cta, int(use_graph), int(time_kernels), integ, rtol, atol)
+                              tn, int(use_graph), int(time_kernels), integ, rtol, atol, spec, launch)
         self.nodes = [p.nx * p.ny * p.nz for p in self.problems]
         self.total = sum(self.nodes)
 
@@ -410,11 +439,15 @@ class Solver:
                         len(self.problems), mT.data_ptr() if mT is not None else 0)
         return J, mT
 
-    def adjoint(self, want_dm0: bool = False):
+    def adjoint(self, want_dm0: bool = False, dJ_dextra=None):
+        """dJ/dPhi (and dJ/dm0) of sum_i dJ_dextra[i] J_i (all ones if None)."""
         g = self.torch.empty(self.total, dtype=self.dtype, device="cuda")
         dm0 = self.torch.empty(3 * self.total, dtype=self.dtype, device="cuda") if want_dm0 else None
-        llg_adjoint(self.ctx, g.data_ptr(), dm0.data_ptr() if dm0 is not None else 0)
+        llg_adjoint(self.ctx, g.data_ptr(), dm0.data_ptr() if dm0 is not None else 0, dJ_dextra)
         return g, dm0
+
+    def launch_config(self):
+        return llg_launch_config(self.ctx)
 
     def levelset_step(self, phi, grad, mask, lr: float):
         if mask.dtype != self.torch.uint8 or not mask.is_cuda:
@@ -458,12 +491,9 @@ def _make_function():
 
         @staticmethod
         def backward(ctx, gJ):
-            solver = ctx.solver
-            g, dm0 = solver.adjoint(want_dm0=True)
-            w = gJ.to(g.dtype)
-            scale = torch.repeat_interleave(w, torch.as_tensor(ctx.counts, device=g.device))
-            scale3 = torch.repeat_interleave(w, torch.as_tensor([3 * c for c in ctx.counts], device=g.device))
-            return g * scale, dm0 * scale3, None
+            # the incoming cotangents of the instances' J seed the adjoint
+            g, dm0 = ctx.solver.adjoint(want_dm0=True, dJ_dextra=gJ.double().cpu().tolist())
+            return g, dm0, None
 
     return LLGFunction
 

@@ -6,6 +6,8 @@
 // them to those slots and reads back x[t + TT s].  It prints, per case, the
 // relative L2 error against a direct DFT in long double and whether every
 // pass scattered to a permutation of [0, L) (so no two lanes write one slot).
+// Precisions: FP32, FP64 and double-float (dcplx, the adjoint's frequency
+// domain option).
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -13,6 +15,11 @@
 #include "regfft.cuh"
 
 using namespace llg;
+
+// value of a real part as long double, for the comparison
+static long double to_ld(float v) { return v; }
+static long double to_ld(double v) { return v; }
+static long double to_ld(dfloat v) { return (long double)v.hi + (long double)v.lo; }
 
 static double lcg_unit(unsigned long long& s) {
   s = s * 6364136223846793005ULL + 1442695040888963407ULL;
@@ -67,8 +74,8 @@ static void run(const char* name, bool with_tw4) {
     const double a = lcg_unit(seed), b = lcg_unit(seed);
     v[(i % TT) * W + i / TT].x = (decltype(C::x))a;      // x[t + TT s] -> thread t, slot s
     v[(i % TT) * W + i / TT].y = (decltype(C::x))b;
-    xr[i] = (decltype(C::x))a;
-    xi[i] = (decltype(C::x))b;
+    xr[i] = to_ld(v[(i % TT) * W + i / TT].x);
+    xi[i] = to_ld(v[(i % TT) * W + i / TT].y);
   }
   std::vector<int> dst(L);
   bool perm = true;
@@ -115,7 +122,7 @@ static void run(const char* name, bool with_tw4) {
     int idx = -1;
     for (int i = 0; i < L; ++i)
       if (dst[i] == k) idx = i;                            // slot holding X[k]
-    const long double er = (long double)v[idx].x - sr, ei = (long double)v[idx].y - si;
+    const long double er = to_ld(v[idx].x) - sr, ei = to_ld(v[idx].y) - si;
     num += er * er + ei * ei;
     den += sr * sr + si * si;
   }
@@ -158,5 +165,7 @@ int main() {
   all_lengths<double2, 8>("f64");
   all_lengths<float2, 16>("f32");
   all_lengths<double2, 16>("f64");
+  all_lengths<dcplx, 8>("df");
+  all_lengths<dcplx, 16>("df");
   return 0;
 }

@@ -103,7 +103,8 @@ def test_binding_structs_have_the_c_layout(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = [("llg_problem", B.llg_problem), ("llg_options", B.llg_options), ("llg_rbf", B.llg_rbf)]
+    structs = [("llg_problem", B.llg_problem), ("llg_options", B.llg_options), ("llg_rbf", B.llg_rbf),
+               ("llg_launch", B.llg_launch)]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "llg.h"', "int main(void) {"]
     expect = []
     for cname, py in structs:

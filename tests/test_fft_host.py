@@ -5,7 +5,9 @@ and 16..2048 with 16, FP32 and FP64, forward and inverse, with and without the
 W^4k table.  Checked against a direct DFT in long double, and every pass must
 scatter its outputs to a permutation of the sequence (no two lanes write one
 shared-memory slot).  Covers lengths the GPU tests do not reach (rows of
-1024 and 2048 complex elements)."""
+1024 and 2048 complex elements).  The double-float precision (hi + lo FP32
+pairs, the adjoint's frequency-domain option) runs the same passes and must
+reach the few 2^-48 its arithmetic promises."""
 import os
 import shutil
 import subprocess
@@ -35,7 +37,7 @@ def cases(tmp_path_factory):
 
 def test_every_length_and_width_is_covered(cases):
     got = {(p, w, L, d) for p, w, L, d, *_ in cases}
-    for p in ("f32", "f64"):
+    for p in ("f32", "f64", "df"):
         for d in (-1, 1):
             for k in range(3, 12):
                 assert (p, 8, 2 ** k, d) in got
@@ -49,6 +51,7 @@ def test_every_pass_scatters_to_a_permutation(cases):
 
 def test_passes_compute_the_dft(cases):
     # FP32: a few ulp per pass (the twiddle powers are formed by products);
-    # FP64: rounding only
+    # FP64: rounding only; double-float: a few 2^-48 = 3.6e-15 per pass
+    bound = {"f32": 5e-7, "f64": 1e-15, "df": 2e-14}
     for prec, w, L, d, t4, err, _ in cases:
-        assert err < (5e-7 if prec == "f32" else 1e-15), (prec, w, L, d, t4, err)
+        assert err < bound[prec], (prec, w, L, d, t4, err)

@@ -45,13 +45,16 @@ def test_field_parity(shape, precision, tol):
         s.close()
 
 
-@pytest.mark.parametrize("precision,tol_m,tol_g", [("fp64", 1e-10, 1e-9), ("fp32", 1e-5, 1e-4)])
+# "fp32-df": FP32 with the double-float frequency domain in the adjoint
+@pytest.mark.parametrize("precision,tol_m,tol_g", [("fp64", 1e-10, 1e-9), ("fp32", 1e-5, 1e-4),
+                                                   ("fp32-df", 1e-5, 1e-4)])
 @pytest.mark.parametrize("shape,objective", [((12, 8), W.J_PORT), ((16, 12), W.J_ENERGY_AREA),
                                              ((8, 5), W.J_PORT), ((20, 3), W.J_ENERGY_AREA),
                                              ((8, 64), W.J_PORT)])
 def test_forward_adjoint_parity_small(shape, objective, precision, tol_m, tol_g):
     inst = W.random_small(*shape, 1, seed=3, nsteps=40, objective=objective)
-    g = gpu_run([inst], precision, want_dm0=True)
+    kw = {"adj_spectral": "dfloat"} if precision == "fp32-df" else {}
+    g = gpu_run([inst], precision[:4], want_dm0=True, **kw)
     o = oracle_run(inst)
     assert rel_l2(g["mT"][0], o["mT"]) < tol_m
     assert abs(g["J"][0] - o["J"]) <= tol_g * max(abs(o["J"]), 1e-30)
@@ -94,13 +97,14 @@ def test_batch_of_uneven_grids_matches_single_runs():
         np.testing.assert_array_equal(single["dphi"][0], b["dphi"][k])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32-df"])
 def test_schedules_give_identical_gradients(precision):
     inst = W.random_small(12, 8, 1, seed=5, nsteps=23)
-    ref = gpu_run([inst], precision, ckpt="store_all")
+    kw = {"adj_spectral": "dfloat"} if precision == "fp32-df" else {}
+    ref = gpu_run([inst], precision[:4], ckpt="store_all", **kw)
     for ckpt, seg in (("periodic", 0), ("periodic", 1), ("periodic", 4), ("periodic", 23), ("periodic", 40),
                       ("binomial", 0), ("binomial", 1), ("binomial", 2), ("binomial", 6)):
-        g = gpu_run([inst], precision, ckpt=ckpt, seg_len=seg, want_dm0=True)
+        g = gpu_run([inst], precision[:4], ckpt=ckpt, seg_len=seg, want_dm0=True, **kw)
         np.testing.assert_array_equal(g["dphi"][0], ref["dphi"][0])
         assert g["J"][0] == ref["J"][0]
 
