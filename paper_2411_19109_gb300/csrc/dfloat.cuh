@@ -1,23 +1,28 @@
 // Double-float ("double-word") arithmetic on the FP32 units.
 //
-// A dfloat is the unevaluated sum hi + lo of two FP32 numbers with
-// |lo| <= ulp(hi)/2: about 48 significant bits, at FP32 exponent range.  It
-// carries the frequency domain of the adjoint's demag transpose, where FP32
-// rounding (a relative error of a Fourier coefficient is a global error in
-// space) would swamp the small adjoint field far from its sources.  FP64 on
-// this GPU runs at 1/64 of the FP32 rate; a double-float add costs 11 FP32
-// operations and a product 8.
+// A dfloat is the unevaluated sum hi + lo of two FP32 numbers: about 48
+// significant bits, at FP32 exponent range.  It carries the frequency domain
+// of the adjoint's demag transpose, where FP32 rounding (a relative error of
+// a Fourier coefficient is a global error in space) would swamp the small
+// adjoint field far from its sources.  FP64 on this GPU runs at 1/64 of the
+// FP32 rate.
 //
-// The building blocks are the error-free transformations
+// The arithmetic is compensated rather than renormalised: hi evolves exactly
+// as the plain FP32 computation would, and lo carries the exact rounding
+// error of every operation on the hi parts forward, in FP32 (the scheme of
+// compensated summation and dot products, Ogita, Rump and Oishi, SIAM J. Sci.
+// Comput. 26(6), 2005, applied to every operation of the transform).  The
+// errors committed on the lo parts are of order 2^-24 |lo|, so hi + lo agrees
+// with the exact result to a small multiple of 2^-48 times the magnitudes
+// involved: a normwise bound, which is what an FFT needs (its own error
+// bound is normwise).  |lo| is not kept below ulp(hi)/2 -- under
+// cancellation hi may even be 0 -- which costs nothing here: the products
+// take lo times the other factor's hi in FP32 too.  A sum costs 8 FP32
+// operations, a product 5, a complex product 32.
+//
+// Error-free transformations used:
 //   TwoSum (Knuth, TAOCP vol. 2, 4.2.2): s + e = a + b exactly, any a, b;
-//   Fast2Sum (Dekker 1971): s + e = a + b exactly when exp(a) >= exp(b);
-//   TwoProd with a fused multiply-add: p + e = a * b exactly;
-// and the double-word algorithms analysed by Joldes, Muller and Popescu
-// (ACM TOMS 44(2), 2017): the "sloppy" sum (their Algorithm 4), whose error
-// is bounded in absolute terms by a small multiple of 2^-48 (|a| + |b|) but
-// not relative to the result under cancellation -- which is what an FFT
-// needs, its own error bound being normwise -- and the product with one FMA
-// per cross term (their Algorithm 11), relative error below 5 * 2^-48.
+//   TwoProd with a fused multiply-add: p + e = a * b exactly.
 //
 // Device code uses the _rn intrinsics, which the compiler never contracts
 // into FMAs or reassociates; host code (the host build of the FFT tests)
@@ -68,12 +73,6 @@ __host__ __device__ __forceinline__ float two_sum(float a, float b, float& e) {
   e = add(sub(a, sub(s, bb)), sub(b, bb));
   return s;
 }
-// s + e == a + b exactly when the exponent of a is at least that of b.
-__host__ __device__ __forceinline__ float fast_two_sum(float a, float b, float& e) {
-  const float s = add(a, b);
-  e = sub(b, sub(s, a));
-  return s;
-}
 // p + e == a * b exactly (barring underflow).
 __host__ __device__ __forceinline__ float two_prod(float a, float b, float& e) {
   const float p = mul(a, b);
@@ -92,32 +91,27 @@ struct dfloat {
   // rounds d to the nearest pair (compile-time constants, host-side tables;
   // on the device only in set-up kernels, since it takes FP64 operations)
   __host__ __device__ constexpr explicit dfloat(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
-  // nearest FP32 value of hi + lo
+  // FP32 value of hi + lo
   __host__ __device__ __forceinline__ float to_float() const { return dw::add(hi, lo); }
 };
 
 __host__ __device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
 
-// Sloppy double-word sum (Joldes, Muller, Popescu, Algorithm 4).
+// Compensated sum: hi = fl(a.hi + b.hi), lo = its error + a.lo + b.lo.
 __host__ __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
   float e;
   const float s = dw::two_sum(a.hi, b.hi, e);
-  const float t = dw::add(e, dw::add(a.lo, b.lo));
-  float l;
-  const float h = dw::fast_two_sum(s, t, l);
-  return dfloat(h, l);
+  return dfloat(s, dw::add(e, dw::add(a.lo, b.lo)));
 }
 __host__ __device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
 
-// Double-word product with FMA cross terms (Joldes, Muller, Popescu,
-// Algorithm 11; the lo * lo term is below the error bound and dropped).
+// Compensated product: hi = fl(a.hi b.hi), lo = its error + the cross
+// terms (the lo * lo term is of second order in the errors and dropped).
 __host__ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
   float e;
   const float p = dw::two_prod(a.hi, b.hi, e);
   const float t = dw::fma(a.lo, b.hi, dw::mul(a.hi, b.lo));
-  float l;
-  const float h = dw::fast_two_sum(p, dw::add(e, t), l);
-  return dfloat(h, l);
+  return dfloat(p, dw::add(e, t));
 }
 
 // Complex double-float.  16 bytes, loaded and stored as one float4.
@@ -126,10 +120,9 @@ struct __align__(16) dcplx {
 };
 
 // Complex product fused per component: re = a.x b.x - a.y b.y as TwoProd of
-// the high parts, one TwoSum of the two products, the four cross terms and
-// the two product errors added to its error, and one renormalisation -- 19
-// operations per component instead of two products and a sum (27); the
-// error stays below a few 2^-48 (|a.x b.x| + |a.y b.y|), normwise as above.
+// the high parts, one TwoSum of the two products, and the product errors
+// and the four cross terms added to its error -- 16 operations per
+// component instead of two products and a sum (18).
 __host__ __device__ __forceinline__ dfloat dot2_sub(dfloat a, dfloat b, dfloat c, dfloat d) {
   // a b - c d
   float e1, e2, es;
@@ -141,9 +134,7 @@ __host__ __device__ __forceinline__ dfloat dot2_sub(dfloat a, dfloat b, dfloat c
   t = dw::fma(a.lo, b.hi, t);
   t = dw::fma(-c.hi, d.lo, t);
   t = dw::fma(-c.lo, d.hi, t);
-  float l;
-  const float h = dw::fast_two_sum(s, dw::add(es, t), l);
-  return dfloat(h, l);
+  return dfloat(s, dw::add(es, t));
 }
 __host__ __device__ __forceinline__ dfloat dot2_add(dfloat a, dfloat b, dfloat c, dfloat d) {
   // a b + c d

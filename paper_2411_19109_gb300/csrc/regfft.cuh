@@ -129,6 +129,34 @@ __host__ __device__ __forceinline__ void rf_pass(C v[8], int t, int Ns, const C*
   }
 }
 
+// A radix-8 Stockham pass with the stage size Ns = 2^lns a run-time value
+// (shifts in place of the divisions by Ns), for the rolled pass loop of the
+// double-float transforms; same data movement as rf_pass<C, L, 8, DIR> at
+// Ns > 1.
+template <typename C, int L, int DIR>
+__host__ __device__ __forceinline__ void rf_pass8_rt(C v[8], int t, int lns, const C* __restrict__ tw, int tws,
+                                                     int dst[8]) {
+  constexpr int LOGL = (L == 8) ? 3 : (L == 16) ? 4 : (L == 32) ? 5 : (L == 64) ? 6 : (L == 128) ? 7
+                     : (L == 256) ? 8 : (L == 512) ? 9 : (L == 1024) ? 10 : 11;
+  const int k = t & ((1 << lns) - 1);
+  const int step = k << (LOGL - lns - 3);         // twiddle W_L^{r*step}
+  C x[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) x[r] = v[r];
+#pragma unroll
+  for (int r = 1; r < 8; ++r) x[r] = cmul(x[r], rf_tw<C, DIR>(tw, r * step, tws));
+  rf_dft8<C, DIR>(x);
+  const int base = ((t >> lns) << (lns + 3)) + k;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    v[r] = x[r];
+    dst[r] = base + (r << lns);
+  }
+}
+
+template <typename C> struct RolledPasses { static constexpr bool value = false; };
+template <> struct RolledPasses<dcplx> { static constexpr bool value = true; };
+
 // Synchronisation of the threads that exchange one sequence: the whole block,
 // one warp (the group lies inside it), or a named barrier over `n` threads.
 struct GroupSync {
@@ -180,6 +208,31 @@ __device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int
   constexpr int R0 = (M % 3 == 1) ? 2 : (M % 3 == 2) ? 4 : 8;
   constexpr int NPASS = (M % 3 == 0) ? M / 3 : M / 3 + 1;
   int dst[8];
+  if constexpr (RolledPasses<C>::value) {
+    // double-float: the first pass, then one copy of the radix-8 pass code
+    // in a rolled loop (a double-float butterfly is ~10x the code of an FP32
+    // one, and the unrolled passes overflowed the instruction cache)
+#pragma unroll
+    for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, R0, DIR>(v[c], t, 1, tw, tws, dst);
+    int lns = R0 == 2 ? 1 : (R0 == 4 ? 2 : 3);
+#pragma unroll 1
+    for (int p = 1; p < NPASS; ++p) {
+#pragma unroll
+      for (int c = 0; c < NCOMP; ++c)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) sm[(c * sstride + row_pad(L, dst[s])) * estride] = v[c][s];
+      sync();
+#pragma unroll
+      for (int c = 0; c < NCOMP; ++c)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) v[c][s] = sm[(c * sstride + row_pad(L, t + TT * s)) * estride];
+      sync();
+#pragma unroll
+      for (int c = 0; c < NCOMP; ++c) rf_pass8_rt<C, L, DIR>(v[c], t, lns, tw, tws, dst);
+      lns += 3;
+    }
+    return;
+  }
   int Ns = 1;
 #pragma unroll
   for (int p = 0; p < NPASS; ++p) {
