@@ -280,8 +280,9 @@ long long llg_launch_count(llg_ctx* ctx);
 /* Device time of one kernel family since llg_create, summed over CUDA-event
  * pairs recorded around each launch on the context's stream (needs
  * llg_options.time_kernels = 1; otherwise both outputs are 0).
- * family: 0 = forward row/stage kernel, 1 = column (demag) kernel,
- *         2 = adjoint stage kernel. */
+ * family: 0 = forward row/stage kernel, 1 = column (demag) kernel in the
+ *         working precision, 2 = adjoint stage kernel, 3 = column kernel of
+ *         the adjoint's double-float frequency domain. */
 llg_status llg_kernel_time(llg_ctx* ctx, int family, long long* launches, double* total_ms);
 
 const char* llg_last_error(llg_ctx* ctx);

@@ -325,7 +325,7 @@ struct Engine final : llg_ctx {
     long long count = 0;
     double ms = 0.0;
   };
-  Timer timers[3];
+  Timer timers[4];
   void time_begin(int fam) {
     if (!opt.time_kernels) return;
     Timer& tm = timers[fam];
@@ -357,7 +357,7 @@ struct Engine final : llg_ctx {
     }
   }
   void kernel_time(int family, long long* count, double* ms) override {
-    if (family < 0 || family > 2) {
+    if (family < 0 || family > 3) {
       if (count) *count = 0;
       if (ms) *ms = 0.0;
       return;
@@ -986,7 +986,7 @@ struct Engine final : llg_ctx {
       c.tens = tens_df;
       c.cols_max = TX;
       c.err = errw;
-      time_begin(1);
+      time_begin(3);
       const auto pc = part(ct.size(), split_ct), p16 = part(ct16.size(), split_ct16);
       if (pc.second) {
         c.tiles = (grp_sel < 0 ? dCT : dCTp) + pc.first;
@@ -998,7 +998,7 @@ struct Engine final : llg_ctx {
         launch_cols<dfloat>(c, (int)p16.second, smem_cols_df, st, L.col_blocks);
         ++nlaunch;
       }
-      time_end(1);
+      time_end(3);
     }
   }
   void set_step(long long v) {
@@ -1774,7 +1774,7 @@ llg_status llg_query(llg_ctx* ctx, size_t* device_bytes, double* last_ms) {
 long long llg_launch_count(llg_ctx* ctx) { return ctx ? ctx->launches() : 0; }
 
 llg_status llg_kernel_time(llg_ctx* ctx, int family, long long* launches, double* total_ms) {
-  if (!ctx || family < 0 || family > 2) return LLG_EINVAL;
+  if (!ctx || family < 0 || family > 3) return LLG_EINVAL;
   ctx->kernel_time(family, launches, total_ms);
   return LLG_OK;
 }

@@ -329,7 +329,8 @@ def llg_launch_count(ctx: int) -> int:
 
 
 def llg_kernel_time(ctx: int, family: int):
-    """(launches, total_ms) of a kernel family: 0 row stage, 1 column, 2 adjoint."""
+    """(launches, total_ms) of a kernel family: 0 row stage, 1 column, 2 adjoint,
+    3 column pass of the double-float adjoint spectrum."""
     lib = load()
     n = c_ll()
     ms = c_double()
