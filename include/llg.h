@@ -71,6 +71,7 @@ enum { LLG_CKPT_STORE_ALL = 0, LLG_CKPT_PERIODIC = 1, LLG_CKPT_BINOMIAL = 2 };
 enum { LLG_INT_RK4 = 0, LLG_INT_DOPRI5 = 1 };
 enum { LLG_SPEC_WORKING = 0, LLG_SPEC_DFLOAT = 1 };
 enum { LLG_TUNE_DEFAULT = 0, LLG_TUNE_MEASURE = 1, LLG_TUNE_GIVEN = 2 };
+enum { LLG_RECORD_STAGES = 0, LLG_RECORD_STATES = 1 };
 
 /* Launch configuration of the hot kernels: which compiled variant of a
  * kernel family runs and how the batch is split over streams.  Only
@@ -199,6 +200,14 @@ typedef struct {
                         brings that to about 1e-14.  The forward pass and
                         the per-node arithmetic are unchanged.              */
   llg_launch launch; /* LLG_TUNE_GIVEN: the configuration to use          */
+  int record;        /* what a checkpoint segment keeps for the reverse
+                        sweep (RK4): LLG_RECORD_STAGES every step's four
+                        stage inputs and fields (8 arrays of 3 x nodes per
+                        step), recorded once; LLG_RECORD_STATES only m per
+                        step (one array per step), each reverse step
+                        recomputing its four stages first (one more forward
+                        step per step: less memory, more time).  Results are
+                        bit-identical.                                      */
 } llg_options;
 
 typedef struct llg_ctx llg_ctx;

@@ -392,6 +392,23 @@ struct Engine final : llg_ctx {
   size_t slot() const { return (size_t)3 * total_nodes; }
   T* recY_slot(long long i) { return recY + (size_t)i * slot(); }
   T* recB_slot(long long i) { return recB + (size_t)i * slot(); }
+  // The segment record.  LLG_RECORD_STAGES: every step's four stage inputs
+  // Y_s (Y_1 = m_l) and fields B_s, recorded once by the RECORD segment.
+  // LLG_RECORD_STATES: only m_l per step; each reverse step recomputes its
+  // stages into one of two step records (parity of l), because adjoint
+  // stage 1 of step l already needs stage 4 of step l - 1.
+  bool rec_states = false;
+  T* mtmp = nullptr;          // states: m_{l+1} of a recomputed step (not kept)
+  C* spec2 = nullptr;         // states: the recomputation's own spectrum pool
+  T* Mrec(long long l) { return rec_states ? recY_slot(l) : recY_slot(4 * l); }
+  T* Yrec(long long l, int s) {
+    if (!rec_states) return recY_slot(4 * l + s - 1);
+    return s == 1 ? Mrec(l) : recB_slot(7 * (l & 1) + s - 2);
+  }
+  T* Brec(long long l, int s) {
+    if (!rec_states) return recB_slot(4 * l + s - 1);
+    return recB_slot(7 * (l & 1) + 3 + s - 1);
+  }
 
   // ---------------------------------------------------------------- create
   llg_status create(const llg_problem* probs, int n_inst, const llg_options* o, cudaStream_t stream) {
@@ -469,6 +486,9 @@ struct Engine final : llg_ctx {
     if (opt.adj_spectral != LLG_SPEC_WORKING && opt.adj_spectral != LLG_SPEC_DFLOAT)
       return fail(LLG_EINVAL, "adj_spectral must be LLG_SPEC_WORKING or LLG_SPEC_DFLOAT");
     adj_df = opt.adj_spectral == LLG_SPEC_DFLOAT;
+    if (opt.record != LLG_RECORD_STAGES && opt.record != LLG_RECORD_STATES)
+      return fail(LLG_EINVAL, "record must be LLG_RECORD_STAGES or LLG_RECORD_STATES");
+    rec_states = opt.record == LLG_RECORD_STATES && !dp_mode;
     if (opt.tune != LLG_TUNE_DEFAULT && opt.tune != LLG_TUNE_MEASURE && opt.tune != LLG_TUNE_GIVEN)
       return fail(LLG_EINVAL, "tune must be LLG_TUNE_DEFAULT, LLG_TUNE_MEASURE or LLG_TUNE_GIVEN");
     if (opt.tune == LLG_TUNE_GIVEN) {
@@ -652,8 +672,8 @@ struct Engine final : llg_ctx {
               alloc(&dCT3, std::max<size_t>(1, ct3.size())) && alloc(&dCT16, std::max<size_t>(1, ct16.size())) && alloc(&psi, total_nodes) &&
               alloc(&dpsi, total_nodes) && alloc(&m, S) && alloc(&Ya, S) && alloc(&Yb, S) && alloc(&acc, S) &&
               alloc(&tens, total_tens) && alloc(&spec, total_spec) && alloc(&tw, kTwiddleN) &&
-              alloc(&tw64, kTwiddleN) && alloc(&recY, S * (4 * rec_steps + 1)) &&
-              alloc(&recB, S * std::max(1LL, 4 * rec_steps)) && alloc(&ckpt, S * std::max(1LL, nckpt)) &&
+              alloc(&tw64, kTwiddleN) && alloc(&recY, S * (rec_states ? rec_steps + 1 : 4 * rec_steps + 1)) &&
+              alloc(&recB, S * (rec_states ? 14 : std::max(1LL, 4 * rec_steps))) && alloc(&ckpt, S * std::max(1LL, nckpt)) &&
               alloc(&lam, S) && alloc(&G, S) && alloc(&gpart, S) && alloc(&bb[0], S) && alloc(&bb[1], S) &&
               alloc(&psib, total_nodes) && alloc(&psic, total_nodes) && alloc(&slots, (size_t)total_slots) &&
               alloc(&pslots, any_spec ? 2 * (size_t)total_slots : 2) && alloc(&Pd, (size_t)n * 2 * (N + 1)) &&
@@ -664,6 +684,8 @@ struct Engine final : llg_ctx {
     if (!ok) return fail(LLG_ENOMEM, "device allocation failed (" + std::to_string(bytes >> 20) + " MiB so far)");
     if (adj_df && !(alloc(&spec_df, total_spec) && alloc(&tw_df, kTwiddleN) && alloc(&tens_df, total_tens)))
       return fail(LLG_ENOMEM, "device allocation failed (double-float adjoint spectrum)");
+    if (rec_states && !(alloc(&mtmp, S) && alloc(&spec2, total_spec)))
+      return fail(LLG_ENOMEM, "device allocation failed (step records)");
     if (can_split) {
       // partitioned copies of the tile lists: even instances first
       auto even_r = [](const RowTile& t) { return t.inst % 2 == 0; };
@@ -942,11 +964,11 @@ struct Engine final : llg_ctx {
     }
     if (mode == ROW_STAGE) time_end(0);
   }
-  void cols() {
+  void cols(C* sp = nullptr) {
     ColArgs<T> c;
     c.inst = dI;
     c.tiles = dCT;
-    c.spec = spec;
+    c.spec = sp ? sp : spec;
     c.tw = tw;
     c.tens = tens;
     c.cols_max = TX;
@@ -1005,9 +1027,10 @@ struct Engine final : llg_ctx {
     launch_set_step(step_base, v, st);
     ++nlaunch;
   }
-  void fft_only(const T* Y) {
+  void fft_only(const T* Y, C* sp = nullptr) {
     RowArgs<T> a = row_args();
     a.Yin = Y;
+    if (sp) a.spec = sp;
     rows(a, ROW_FFT_ONLY);
   }
   void material(const T* phi) {
@@ -1027,18 +1050,46 @@ struct Engine final : llg_ctx {
       a.acc = acc;
       a.slots = objective ? slots : nullptr;
       a.pslots = objective && any_spec ? pslots : nullptr;
-      if (record) {
-        a.m = recY_slot(4LL * l);
-        a.Yin = recY_slot(4LL * l + s - 1);
-        a.Bout = recB_slot(4LL * l + s - 1);
-        if (s < 4) a.Yout = recY_slot(4LL * l + s);
-        else a.mout = recY_slot(4LL * (l + 1));
+      if (record && !rec_states) {
+        a.m = Mrec(l);
+        a.Yin = Yrec(l, s);
+        a.Bout = Brec(l, s);
+        if (s < 4) a.Yout = Yrec(l, s + 1);
+        else a.mout = Mrec(l + 1);
+      } else if (record) {
+        // states only: the stages run on the ping-pong buffers, m_{l+1}
+        // goes to the next state slot
+        a.m = Mrec(l);
+        a.Yin = (s == 1) ? Mrec(l) : (s == 3 ? Yb : Ya);
+        if (s < 4) a.Yout = (s == 2) ? Yb : Ya;
+        else a.mout = Mrec(l + 1);
       } else {
         a.m = m;
         a.Yin = (s == 1) ? m : (s == 3 ? Yb : Ya);
         if (s < 4) a.Yout = (s == 2) ? Yb : Ya;
         else a.mout = m;
       }
+      rows(a, ROW_STAGE);
+    }
+  }
+
+  // LLG_RECORD_STATES: recompute step l's stage inputs and fields from m_l
+  // into its step record, on the recomputation's own spectrum pool (the
+  // adjoint's holds a transform in flight); no objective terms
+  void recompute_step(long long l) {
+    fft_only(Mrec(l), spec2);
+    for (int s = 1; s <= 4; ++s) {
+      cols(spec2);
+      RowArgs<T> a = row_args();
+      a.spec = spec2;
+      a.local_step = (int)l;
+      a.stage = s;
+      a.acc = acc;
+      a.m = Mrec(l);
+      a.Yin = Yrec(l, s);
+      a.Bout = Brec(l, s);
+      if (s < 4) a.Yout = Yrec(l, s + 1);
+      else a.mout = mtmp;
       rows(a, ROW_STAGE);
     }
   }
@@ -1058,32 +1109,35 @@ struct Engine final : llg_ctx {
   template <typename S>
   void reverse_segment_t(long long len) {
     int cur = 0;
+    if (rec_states) recompute_step(len - 1);
     {
       AdjArgs<T, S> a = adj_args<S>();
       a.local_step = (int)(len - 1);
       a.stage = 4;
       a.seed_only = 1;
-      a.Yprev = recY_slot(4 * (len - 1) + 3);
-      a.Bprev = recB_slot(4 * (len - 1) + 3);
+      a.Yprev = Yrec(len - 1, 4);
+      a.Bprev = Brec(len - 1, 4);
       a.BbarOut = bb[cur];
       adj(a);
     }
     for (long long l = len - 1; l >= 0; --l) {
       for (int s = 4; s >= 1; --s) {
+        // stage 1 of step l seeds step l - 1 from its stage-4 record
+        if (rec_states && s == 1 && l > 0) recompute_step(l - 1);
         if constexpr (std::is_same<S, T>::value) cols();
         else cols_df();
         AdjArgs<T, S> a = adj_args<S>();
         a.local_step = (int)l;
         a.stage = s;
-        a.Ys = recY_slot(4 * l + s - 1);
+        a.Ys = Yrec(l, s);
         a.Bbar = bb[cur];
         a.BbarOut = bb[1 - cur];
         if (s > 1) {
-          a.Yprev = recY_slot(4 * l + s - 2);
-          a.Bprev = recB_slot(4 * l + s - 2);
+          a.Yprev = Yrec(l, s - 1);
+          a.Bprev = Brec(l, s - 1);
         } else if (l > 0) {
-          a.Yprev = recY_slot(4 * (l - 1) + 3);
-          a.Bprev = recB_slot(4 * (l - 1) + 3);
+          a.Yprev = Yrec(l - 1, 4);
+          a.Bprev = Brec(l - 1, 4);
           a.seed_next = 1;
         }
         adj(a);
@@ -1503,7 +1557,7 @@ struct Engine final : llg_ctx {
         cudaMemcpyAsync(recY_slot(0), m, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
         set_step(ac.a);
         if (llg_status s = run_segment(SEG_RECORD_FWD, ac.b - ac.a)) return s;
-        cur = recY_slot(4 * (ac.b - ac.a));
+        cur = Mrec(ac.b - ac.a);
       }
     }
     mN_ptr = cur;

@@ -28,6 +28,7 @@ LLG_CKPT_STORE_ALL, LLG_CKPT_PERIODIC, LLG_CKPT_BINOMIAL = 0, 1, 2
 LLG_INT_RK4, LLG_INT_DOPRI5 = 0, 1
 LLG_SPEC_WORKING, LLG_SPEC_DFLOAT = 0, 1
 LLG_TUNE_DEFAULT, LLG_TUNE_MEASURE, LLG_TUNE_GIVEN = 0, 1, 2
+LLG_RECORD_STAGES, LLG_RECORD_STATES = 0, 1
 
 EXPORTED = ("llg_create", "llg_forward", "llg_adjoint", "levelset_step", "llg_field", "llg_query",
             "llg_launch_count", "llg_kernel_time", "llg_last_error", "llg_destroy", "llg_schedule",
@@ -69,7 +70,8 @@ class llg_launch(ctypes.Structure):
 class llg_options(ctypes.Structure):
     _fields_ = [("precision", c_int), ("ckpt", c_int), ("seg_len", c_int), ("use_graph", c_int),
                 ("tune", c_int), ("time_kernels", c_int), ("integrator", c_int),
-                ("rtol", c_double), ("atol", c_double), ("adj_spectral", c_int), ("launch", llg_launch)]
+                ("rtol", c_double), ("atol", c_double), ("adj_spectral", c_int), ("launch", llg_launch),
+                ("record", c_int)]
 
 
 class LLGError(RuntimeError):
@@ -195,13 +197,13 @@ def _check(lib, ctx, st):
 def llg_create(problems: Sequence, precision=LLG_FP32, ckpt=LLG_CKPT_PERIODIC, seg_len=0,
                stream=0, tune=LLG_TUNE_DEFAULT, use_graph=0, time_kernels=0,
                integrator=LLG_INT_RK4, rtol=1e-6, atol=1e-9, adj_spectral=LLG_SPEC_WORKING,
-               launch=None) -> int:
+               launch=None, record=LLG_RECORD_STAGES) -> int:
     lib = load()
     structs = [to_struct(p) for p in problems]          # hold the host arrays until create returns
     arr = (llg_problem * len(problems))(*structs)
     lc = llg_launch(**launch) if launch else llg_launch(16, 2, 2, 2)
     opt = llg_options(precision, ckpt, seg_len, use_graph, tune, time_kernels, integrator,
-                      rtol, atol, adj_spectral, lc)
+                      rtol, atol, adj_spectral, lc, record)
     ctx = c_void_p()
     st = lib.llg_create(arr, len(problems), ctypes.byref(opt), c_void_p(stream), ctypes.byref(ctx))
     if st != LLG_OK:
@@ -375,7 +377,7 @@ class Solver:
     def __init__(self, problems: Sequence, precision: str = "fp32", ckpt: str = "periodic",
                  seg_len: int = 0, stream=None, tune: str = "default", launch=None,
                  time_kernels: bool = False, use_graph: bool = True, integrator: str = "rk4",
-                 rtol: float = 1e-6, atol: float = 1e-9, adj_spectral: str = "working"):
+                 rtol: float = 1e-6, atol: float = 1e-9, adj_spectral: str = "working", record: str = "stages"):
         """tune: "default", "measure" (time launch candidates at create) or
         "given" (use `launch`, a dict of llg_launch fields)."""
         import torch
@@ -389,7 +391,8 @@ class Solver:
         spec = {"working": LLG_SPEC_WORKING, "dfloat": LLG_SPEC_DFLOAT}[adj_spectral]
         tn = {"default": LLG_TUNE_DEFAULT, "measure": LLG_TUNE_MEASURE, "given": LLG_TUNE_GIVEN}[tune]
         self.ctx = llg_create(self.problems, prec, ck, seg_len, self.stream.cuda_stream,
-                              tn, int(use_graph), int(time_kernels), integ, rtol, atol, spec, launch)
+                              tn, int(use_graph), int(time_kernels), integ, rtol, atol, spec, launch,
+                              {"stages": LLG_RECORD_STAGES, "states": LLG_RECORD_STATES}[record])
         self.nodes = [p.nx * p.ny * p.nz for p in self.problems]
         self.total = sum(self.nodes)
 

@@ -223,3 +223,57 @@ def test_batch_with_both_column_kernels_matches_single_runs():
         np.testing.assert_array_equal(single["dphi"][0], b["dphi"][k])
         np.testing.assert_array_equal(single["mT"][0], b["mT"][k])
         assert single["J"][0] == b["J"][k]
+
+
+# The widest rows llg_create accepts: nx = 1024 in FP32 (row FFT length 1024,
+# one row per tile, 128-lane FFT groups on named barriers) and nx = 780 in
+# FP64 (the adjoint's row tile at its shared-memory limit; the same FFT
+# length), plus the double-float adjoint spectrum at nx = 1024.
+@pytest.mark.parametrize("precision,nx,tol", [("fp32", 1024, 2e-6), ("fp64", 780, 1e-11), ("fp32", 780, 2e-6)])
+def test_widest_rows_field(precision, nx, tol):
+    from oracle import llg
+    inst = W.random_small(nx, 3, 1, seed=nx)
+    s = gpu_solver([inst], precision)
+    try:
+        phi = s.pack_scalar([inst.phi])
+        m = s.pack_vector([inst.m0])
+        model = llg.Model(inst.problem, inst.phi)
+        B = s.unpack_vector(s.field(phi, m, 2.0e-11))[0].double().cpu().numpy()
+        assert rel_l2(B, model.field(inst.m0, 2.0e-11)) < tol
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("precision,nx,tol_m,tol_g", [("fp32", 1024, 1e-5, 1e-4), ("fp32-df", 1024, 1e-5, 1e-4),
+                                                      ("fp64", 780, 1e-10, 1e-9)])
+def test_widest_rows_forward_adjoint(precision, nx, tol_m, tol_g):
+    inst = W.random_small(nx, 2, 1, seed=nx + 1, nsteps=12)
+    kw = {"adj_spectral": "dfloat"} if precision == "fp32-df" else {}
+    g = gpu_run([inst], precision[:4], want_dm0=True, **kw)
+    o = oracle_run(inst)
+    assert rel_l2(g["mT"][0], o["mT"]) < tol_m
+    assert abs(g["J"][0] - o["J"]) <= tol_g * max(abs(o["J"]), 1e-30)
+    assert rel_l2(g["dphi"][0], o["dphi"]) < tol_g
+    assert rel_l2(g["dm0"][0], o["dm0"]) < tol_g
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32-df"])
+def test_state_records_match_stage_records(precision):
+    """LLG_RECORD_STATES (m per step; each reverse step recomputes its
+    stages) gives bit-identical J and gradients to LLG_RECORD_STAGES in
+    every schedule, batched over two uneven grids with two instance-group
+    chains and graph replays, and holds less memory on a long segment."""
+    insts = [W.random_small(12, 8, 1, seed=5, nsteps=23), W.random_small(16, 5, 1, seed=6, nsteps=23,
+                                                                           objective=W.J_ENERGY_AREA)]
+    kw = {"adj_spectral": "dfloat"} if precision == "fp32-df" else {}
+    for ckpt, seg in (("periodic", 0), ("periodic", 23), ("binomial", 2), ("store_all", 0)):
+        ref = gpu_run(insts, precision[:4], ckpt=ckpt, seg_len=seg, want_dm0=True, **kw)
+        for graphs in (True, False):
+            g = gpu_run(insts, precision[:4], ckpt=ckpt, seg_len=seg, want_dm0=True, record="states",
+                        use_graph=graphs, **kw)
+            np.testing.assert_array_equal(g["J"], ref["J"])
+            for k in range(len(insts)):
+                np.testing.assert_array_equal(g["dphi"][k], ref["dphi"][k])
+                np.testing.assert_array_equal(g["dm0"][k], ref["dm0"][k])
+        if ckpt == "periodic" and seg == 23:
+            assert g["bytes"] < ref["bytes"]
