@@ -641,6 +641,7 @@ def run_ours(args):
         s64.close()
         del p64, q64
         line["workloads"] = other_workloads(stream)
+        line["record_modes"] = record_modes(stream)
         # CPU baseline: the oracle on this host's cores (all cores, and one)
         pool = OraclePool()
         pool.sample(10)                   # starts the workers
@@ -660,6 +661,54 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def record_modes(stream):
+    """Memory against time of the two segment records: every stage (the
+    default) or only m per step with each reverse step recomputing its
+    stages.  Device bytes at the full configurations (contexts created,
+    not run) and forward+adjoint throughput on batch64 at 1000 RK4 steps."""
+    from paper_2411_19109_gb300 import Solver
+    out = {}
+    for rec in ("stages", "states"):
+        r = {}
+        sv = Solver([i.problem for i in W.batch64(nsteps=10000)], precision="fp32", ckpt="periodic",
+                    adj_spectral="dfloat", record=rec, stream=stream)
+        r["batch64_10000_device_bytes"] = int(sv.query()[0])
+        sv.close()
+        sv = Solver([W.thick512(nsteps=50000).problem], precision="fp32", ckpt="periodic", record=rec, stream=stream)
+        r["thick512_50000_device_bytes"] = int(sv.query()[0])
+        sv.close()
+        insts = W.batch64(nsteps=1000)
+        t = time_workload_rec(insts, 1000, rec, stream)
+        r["batch64_1000_forward_adjoint"] = t
+        out[rec] = r
+    out["unit"] = UNIT
+    return out
+
+
+def time_workload_rec(insts, nsteps, rec, stream):
+    import torch
+    from paper_2411_19109_gb300 import Solver
+    nodes = sum(i.problem.nx * i.problem.ny * i.problem.nz for i in insts)
+    s = Solver([i.problem for i in insts], precision="fp32", ckpt="periodic", use_graph=True, stream=stream,
+               adj_spectral="dfloat", tune="measure", record=rec)
+    try:
+        phi = s.pack_scalar([i.phi for i in insts])
+        m0 = s.pack_vector([i.m0 for i in insts])
+        s.forward(phi, m0)
+        s.adjoint()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.forward(phi, m0)
+        s.adjoint()
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        return nodes * nsteps / (e0.elapsed_time(e1) / 1e3)
+    finally:
+        s.close()
 
 
 def other_workloads(stream):
