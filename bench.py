@@ -321,11 +321,13 @@ def _df_fft_ops(L):
 
 def df_ops_per_launch(insts, family):
     """FP32 operations of one whole-batch launch of a double-float kernel:
-    family 2 (adjoint stage: inverse and forward row FFTs of length Px/2 per
-    row and component, with the packed-real unpack (80 per point) and pack
-    (90)), family 3 (column pass: forward and inverse FFT of length Py per
-    column kx < Px/2 and component, and the tensor product, about 27 per
-    point).  Node-phase arithmetic is not counted."""
+    family 2 (fused adjoint stage: inverse and forward row FFTs of length
+    Px/2 per row and component, with the packed-real unpack (80 per point)
+    and pack (90)), family 4 (one row transform of the split adjoint stage,
+    inverse or forward: half of that), family 3 (column pass: forward and
+    inverse FFT of length Py per column kx < Px/2 and component, and the
+    tensor product, about 27 per point).  Node-phase arithmetic is not
+    counted."""
     tot = 0.0
     for i in insts:
         p = i.problem
@@ -334,6 +336,8 @@ def df_ops_per_launch(insts, family):
         Lx = Px // 2
         if family == 2:
             tot += p.ny * p.nz * 3 * (2 * _df_fft_ops(Lx) + Lx * (80 + 90))
+        elif family == 4:
+            tot += p.ny * p.nz * 3 * (_df_fft_ops(Lx) + Lx * 85)
         else:
             tot += Lx * 3 * (2 * _df_fft_ops(Py) + Py * 27)
     return tot
@@ -344,36 +348,57 @@ def df_ops_per_launch(insts, family):
 # outputs 12, recorded field 6); FP32 column pass (24 read + 24 written);
 # adjoint stage (spectrum read and written, the stage's Y, Bbar, psi, adjoint
 # state, gradient sums and next-stage records: 137 + the spectrum 48 in FP32,
-# 96 in double-float); double-float column pass (48 read + 48 written).
-BYTES_PER_NODE = {0: 112.0, 1: 48.0, 2: 233.0, 3: 96.0}
+# 96 in double-float); double-float column pass (48 read + 48 written); the
+# split adjoint stage's FP32 node phase (137 + the demag transpose 12) and
+# one of its double-float row transforms (spectrum 48 + nodes 12).
+BYTES_PER_NODE = {0: 112.0, 1: 48.0, 2: 233.0, 3: 96.0, 4: 60.0}
 BYTES_PER_NODE_FP32_ADJ = 185.0
+BYTES_PER_NODE_SPLIT_ADJ = 149.0
 FAMILY = {0: "rows_kernel<float,ROW_STAGE> (inverse row FFT + field + RK4 stage + forward row FFT)",
           1: "cols16_kernel<float> (column FFT with 16-element lanes, tensor product, inverse column FFT)",
           2: "adj_kernel<float,dfloat> (adjoint stage: double-float row FFTs, demag/exchange transposes, dJ/dpsi)",
-          3: "cols_kernel<dfloat> (column pass of the adjoint's double-float frequency domain)"}
+          3: "cols_kernel<dfloat> (column pass of the adjoint's double-float frequency domain)",
+          4: "spec_rows_kernel<float,dfloat> (double-float row transforms of the split adjoint stage)"}
+SPLIT_ADJ_NAME = "adj_split_kernel<float> (split adjoint stage: FP32 node phase, demag/exchange transposes, dJ/dpsi)"
 FP32_LANES_PER_SM, SMS = 128, 152
 
 
-def kernel_families(sk, step_fn, insts, nodes, spec):
+def family_kind(f, spec, split):
+    """How a timing family is measured: ("df", bytes/node) for double-float
+    kernels (FP32-arithmetic roofline), ("hbm", bytes/node) otherwise."""
+    if f == 2:
+        if spec != "dfloat":
+            return "hbm", BYTES_PER_NODE_FP32_ADJ, "adj_kernel<float> (adjoint stage)"
+        if split:
+            return "hbm", BYTES_PER_NODE_SPLIT_ADJ, SPLIT_ADJ_NAME
+        return "df", BYTES_PER_NODE[2], FAMILY[2]
+    if f in (3, 4):
+        return "df", BYTES_PER_NODE[f], FAMILY[f]
+    return "hbm", BYTES_PER_NODE[f], FAMILY[f]
+
+
+def kernel_families(sk, step_fn, insts, nodes, spec, split):
     """Per-family launches and average device time over one step of a
     context that brackets every stage-kernel launch with CUDA events."""
-    f0 = {f: sk.kernel_time(f) for f in (0, 1, 2, 3)}
+    fams = (0, 1, 2, 3, 4)
+    f0 = {f: sk.kernel_time(f) for f in fams}
     step_fn(sk)
     import torch
     torch.cuda.synchronize()
-    f1 = {f: sk.kernel_time(f) for f in (0, 1, 2, 3)}
+    f1 = {f: sk.kernel_time(f) for f in fams}
     kern = {}
-    for f in (0, 1, 2, 3):
+    for f in fams:
         n = f1[f][0] - f0[f][0]
         t = f1[f][1] - f0[f][1]
         if n <= 0:
             continue
         avg_ms = t / n
-        bpn = BYTES_PER_NODE[f] if (f != 2 or spec == "dfloat") else BYTES_PER_NODE_FP32_ADJ
+        kind, bpn, name = family_kind(f, spec, split)
         bytes_launch = bpn * nodes
-        kern[f] = {"launches": n, "total_ms": t, "avg_us": 1e3 * avg_ms, "bytes_per_launch": bytes_launch,
+        kern[f] = {"kernel": name, "kind": kind, "bytes_per_node": bpn, "launches": n, "total_ms": t,
+                   "avg_us": 1e3 * avg_ms, "bytes_per_launch": bytes_launch,
                    "achieved_gbs": bytes_launch / (avg_ms / 1e3) / 1e9}
-        if spec == "dfloat" and f in (2, 3):
+        if kind == "df":
             ops = df_ops_per_launch(insts, f)
             kern[f]["fp32_ops_per_launch"] = ops
             kern[f]["achieved_tops"] = ops / (avg_ms / 1e3) / 1e12
@@ -386,8 +411,8 @@ def kernel_families(sk, step_fn, insts, nodes, spec):
 def roofline_of(kern, spec, hbm, peak_kind, sm_mhz, nodes, timing_note):
     dom = max(kern, key=lambda f: kern[f]["total_ms"])
     k = kern[dom]
-    name = FAMILY[dom] if not (dom == 2 and spec != "dfloat") else "adj_kernel<float> (adjoint stage)"
-    if spec == "dfloat" and dom in (2, 3):
+    name = k["kernel"]
+    if k["kind"] == "df":
         # double-float kernels: bound by FP32 arithmetic (the compensated
         # operations), against the FP32 lanes x clock of the device
         peak = SMS * FP32_LANES_PER_SM * (sm_mhz or 2070.0) * 1e6 / 1e12
@@ -397,10 +422,10 @@ def roofline_of(kern, spec, hbm, peak_kind, sm_mhz, nodes, timing_note):
                                "add/multiply/FMA per lane per clock (FP32 operations, an FMA counted once)",
                 "ops_per_launch": k["fp32_ops_per_launch"],
                 "ops": "FP32 operations of the double-float FFTs (and pack/unpack, tensor product) per launch",
-                "hbm_model": {"bytes_per_node": BYTES_PER_NODE[dom], "achieved_gbs": k["achieved_gbs"],
+                "hbm_model": {"bytes_per_node": k["bytes_per_node"], "achieved_gbs": k["achieved_gbs"],
                               "frac": k["achieved_gbs"] / hbm},
                 "kernel_timing": timing_note}
-    bpn = BYTES_PER_NODE[dom] if not (dom == 2 and spec != "dfloat") else BYTES_PER_NODE_FP32_ADJ
+    bpn = k["bytes_per_node"]
     return {"bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
             "frac": k["achieved_gbs"] / hbm, "traffic": ncu_traffic(dom) if spec != "dfloat" else None,
             "kernel": name, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
@@ -535,7 +560,7 @@ def run_ours(args):
     # times, so the timed region above runs graphs and this pass does not)
     sk = Solver([i.problem for i in insts], precision="fp32", ckpt="periodic", time_kernels=True,
                 use_graph=False, stream=stream, adj_spectral=SPEC, tune="given", launch=launch)
-    kern = kernel_families(sk, lambda sv: step(lr, sv), insts, nodes, SPEC)
+    kern = kernel_families(sk, lambda sv: step(lr, sv), insts, nodes, SPEC, bool(launch.get("adj_split")))
     sk.close()
     hbm, peak_kind = measured_peaks()
     roofline = roofline_of(kern, SPEC, hbm, peak_kind, csum.get("sm_mhz"), nodes,
@@ -563,7 +588,8 @@ def run_ours(args):
                              "note": "the forward pass of each timed step (periodic checkpoints, objective)"},
             "roofline": roofline, "gpu_launches": launches,
             "clocks": csum,
-            "kernels": {FAMILY[f].split(" ")[0]: v for f, v in kern.items()},
+            "kernels": {v["kernel"].split(" ")[0]: {kk: vv for kk, vv in v.items() if kk != "kernel"}
+                        for v in kern.values()},
             "peak_mem_bytes": int(mem_bytes)}
 
     if rank == 0 and not args.no_extras:

@@ -89,6 +89,11 @@ typedef struct {
   int adj_blocks;  /* double-float adjoint stage kernel: 2 or 1           */
   int groups;      /* RK4 segments as 2 independent chains (even and odd
                       instances on two streams) or 1                      */
+  int adj_split;   /* double-float adjoint stage: 1 = three launches (the
+                      inverse row transform to a field buffer, the FP32
+                      node phase at 2 blocks per SM, the forward row
+                      transform), 0 = one fused kernel (its FFT registers
+                      allow one block per SM)                             */
 } llg_launch;
 
 /* One instance.  SI units (m, A/m, J/m, J/m^3, T, Hz, s). */
@@ -162,7 +167,7 @@ typedef struct {
   int use_graph;   /* 1 = replay captured CUDA graphs of whole segments
                       (ignored while time_kernels = 1)                        */
   int tune;        /* launch configuration (llg_launch): LLG_TUNE_DEFAULT
-                      {16, 2, 2, 2}; LLG_TUNE_MEASURE: llg_create times each
+                      {16, 2, 2, 2, 1}; LLG_TUNE_MEASURE: llg_create times each
                       field's candidates on this batch (the kernel families
                       they change, a few ms) and keeps the fastest, cached
                       per device and batch shape for the process;
@@ -291,7 +296,9 @@ long long llg_launch_count(llg_ctx* ctx);
  * llg_options.time_kernels = 1; otherwise both outputs are 0).
  * family: 0 = forward row/stage kernel, 1 = column (demag) kernel in the
  *         working precision, 2 = adjoint stage kernel, 3 = column kernel of
- *         the adjoint's double-float frequency domain. */
+ *         the adjoint's double-float frequency domain, 4 = row transforms
+ *         of that domain (split adjoint stage; family 2 is then its FP32
+ *         node phase). */
 llg_status llg_kernel_time(llg_ctx* ctx, int family, long long* launches, double* total_ms);
 
 const char* llg_last_error(llg_ctx* ctx);

@@ -104,6 +104,8 @@ struct AdjArgs {
   const T* Yprev;     // Y and B of the next stage to be reversed
   const T* Bprev;
   T* BbarOut;
+  const T* Dext;      // split adjoint stage: the demag transpose N * Bbar_s
+                      // at the nodes, from its own row-transform launch
   const long long* step_base;
   int* err;
   int local_step;
@@ -155,6 +157,41 @@ __host__ __device__ constexpr size_t cols3_smem_bytes(int Py, int nz, int ncols)
 
 template <typename T, typename S = T>
 void launch_adj(const AdjArgs<T, S>& a, int ntiles, size_t smem, cudaStream_t st, bool z3, int mb = 0);
+
+// Split adjoint stage (films): the node phase of adj_kernel with the demag
+// transpose read from a.Dext and without the row transforms, whose own
+// launches (spec_rows) run them in the frequency domain's type.
+template <typename T>
+void launch_adj_split(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+template <typename T>
+void smem_adj_split(size_t smem);
+template <typename T>
+__host__ __device__ constexpr size_t adj_split_smem_bytes(int L, int nx) {
+  return (size_t)7 * (rows_per_tile(L) + 2) * nx * sizeof(T);
+}
+
+// Row transforms of a frequency domain of real type S for node arrays of
+// type T, one row tile per block: DIR = +1 the inverse transform of the
+// tile's spectrum rows to the field at the nodes (out), DIR = -1 the forward
+// transform of the nodes' values (src) to the spectrum rows.
+template <typename T, typename S>
+struct SpecRowArgs {
+  const DevInst* inst;
+  const RowTile* tiles;
+  cplx<S>* spec;
+  const cplx<S>* tw;
+  T* out;             // DIR = +1: [3][nodes] per instance (pooled like m)
+  const T* src;       // DIR = -1: [3][nodes]
+  int* err;
+};
+template <typename T, typename S>
+void launch_spec_rows(const SpecRowArgs<T, S>& a, int dir, int ntiles, size_t smem, cudaStream_t st);
+template <typename T, typename S>
+void smem_spec_rows(size_t smem);
+template <typename S>
+__host__ __device__ constexpr size_t spec_rows_smem_bytes(int L) {
+  return (size_t)(kExch + 2 * L) * sizeof(cplx<S>);
+}
 template <typename T, int MODE>
 void launch_rows_mode(const RowArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3);
 template <typename T, int MODE>

@@ -909,7 +909,10 @@ template <typename T> __device__ __forceinline__ T spec_to(dfloat v) { return v.
 template <typename T> __device__ __forceinline__ T spec_to(double v) { return (T)v; }
 template <typename S, typename T> __device__ __forceinline__ S spec_from(T v) { return S(v); }
 
-template <typename T, typename S, int L, bool Z3, bool DP>
+// SPLIT: the node phase alone -- the demag transpose comes from a.Dext and
+// no row transform runs here (its own launches do them); shared memory then
+// holds only the staged halo rows.
+template <typename T, typename S, int L, bool Z3, bool DP, bool SPLIT = false>
 __device__ __forceinline__ void adj_body(const AdjArgs<T, S>& a, const DevInst& I, const RowTile& tile,
                                          unsigned char* smem_raw, uint64_t* bars) {
   using C = cplx<S>;
@@ -926,14 +929,14 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T, S>& a, const DevInst& 
   const long long nodes = I.nodes, layer = I.layer;
   const long long zoff = (long long)z * layer;   // first node of the tile's layer
   C* sx = reinterpret_cast<C*>(smem_raw);
-  T* sYs = reinterpret_cast<T*>(sx + kExch);
+  T* sYs = SPLIT ? reinterpret_cast<T*>(smem_raw) : reinterpret_cast<T*>(sx + kExch);
   T* sBb = sYs + 3 * (RM + 2) * nx;
   T* sP = sBb + 3 * (RM + 2) * nx;
   C* tw2 = reinterpret_cast<C*>(sP + (RM + 2) * nx);
   C* sE = sx + g.rl * 3 * GS;
   C* grp = sE + g.c * GS;
   S* sEr = reinterpret_cast<S*>(sE);
-  C* row0 = a.spec + I.spec_off + ((long long)z * ny + y0) * 3 * L;
+  C* row0 = SPLIT ? nullptr : a.spec + I.spec_off + ((long long)z * ny + y0) * 3 * L;
   const long long n = (a.step_base ? *a.step_base : 0) + a.local_step;
   const int s = a.stage;
   const long long off3 = 3 * I.node_off;
@@ -970,15 +973,17 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T, S>& a, const DevInst& 
     mbar_init(&bars[1], 1);
     mbar_fence_init();
   }
-  load_twiddles(tw2, a.tw, 2 * L);
+  if (!SPLIT) load_twiddles(tw2, a.tw, 2 * L);
   __syncthreads();
   if (tid == 0) {
     unsigned bytes = 0;
     if (!seed) {
-      const unsigned rowb = (unsigned)(L * sizeof(C));
-      mbar_arrive_expect(&bars[0], nr * 3 * rowb);
-      for (int r = 0; r < nr; ++r)
-        for (int c = 0; c < 3; ++c) bulk_load(sx + (r * 3 + c) * GS, row0 + (r * 3 + c) * L, rowb, &bars[0]);
+      if (!SPLIT) {
+        const unsigned rowb = (unsigned)(L * sizeof(C));
+        mbar_arrive_expect(&bars[0], nr * 3 * rowb);
+        for (int r = 0; r < nr; ++r)
+          for (int c = 0; c < 3; ++c) bulk_load(sx + (r * 3 + c) * GS, row0 + (r * 3 + c) * L, rowb, &bars[0]);
+      }
       const unsigned hb = (unsigned)((yhi - ylo) * nx * sizeof(T));
       bytes += 7 * hb;
     }
@@ -989,7 +994,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T, S>& a, const DevInst& 
       stage_halo(sP, RM, a.psi + I.node_off + zoff, nodes, 1, nx, y0, ylo, yhi, &bars[1]);
     }
   }
-  if (!seed) {
+  if (!seed && !SPLIT) {
     mbar_wait(&bars[0], 0, a.err);
     C v[8];
     row_inverse_comp<S, L>(v, grp, active, grp, g.t, tw2);
@@ -1005,7 +1010,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T, S>& a, const DevInst& 
     const int sl = node_slot<T, L>(x);
     // every pointwise value of this node first, so that the load latencies
     // overlap (these arrays are disjoint from the ones this loop writes)
-    T lam[3], gg[3], gsum[3], yp[3], bp[3];
+    T lam[3], gg[3], gsum[3], yp[3], bp[3], dx[3];
     T qs = 0, qc = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -1014,6 +1019,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T, S>& a, const DevInst& 
       if (!seed) {
         gg[c] = ggp[id];
         gsum[c] = (!DP && s < 4) ? gG[id] : (T)0;
+        if (SPLIT) dx[c] = a.Dext[id];
       }
       if (emit) {
         yp[c] = gYp[id];
@@ -1083,7 +1089,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T, S>& a, const DevInst& 
       T D[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        D[c] = spec_to<T>(sEr[2 * c * GS + sl]);
+        D[c] = SPLIT ? dx[c] : spec_to<T>(sEr[2 * c * GS + sl]);
         gg[c] += Ms * pi * D[c];
       }
       qpsi += Ms * dot3(yi, D);
@@ -1158,27 +1164,27 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T, S>& a, const DevInst& 
       const long long id = off3 + c * nodes + n0;
       gbo[id] = bbar[c];
       ggp[id] = gl[c];
-      sEr[2 * c * GS + sl] = spec_from<S>(bbar[c]);
+      if (!SPLIT) sEr[2 * c * GS + sl] = spec_from<S>(bbar[c]);
     }
   }
-  if (!emit) return;
+  if (!emit || SPLIT) return;
   __syncthreads();
   row_forward_comp<S, L>(grp, nx / 2, a.spec + I.spec_off + ((long long)z * ny + y) * 3 * L + g.c * L, active, g.t,
                          tw2);
 }
 
-template <typename T, typename S, bool Z3, bool DP>
+template <typename T, typename S, bool Z3, bool DP, bool SPLIT = false>
 __device__ __forceinline__ void adj_dispatch(const AdjArgs<T, S>& a, const DevInst& I, const RowTile& tile,
                                              unsigned char* smem_raw, uint64_t* bars) {
   switch (I.log2Lx) {
-    case 3: adj_body<T, S, 8, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 4: adj_body<T, S, 16, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 5: adj_body<T, S, 32, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 6: adj_body<T, S, 64, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 7: adj_body<T, S, 128, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 8: adj_body<T, S, 256, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 9: adj_body<T, S, 512, Z3, DP>(a, I, tile, smem_raw, bars); break;
-    case 10: adj_body<T, S, 1024, Z3, DP>(a, I, tile, smem_raw, bars); break;
+    case 3: adj_body<T, S, 8, Z3, DP, SPLIT>(a, I, tile, smem_raw, bars); break;
+    case 4: adj_body<T, S, 16, Z3, DP, SPLIT>(a, I, tile, smem_raw, bars); break;
+    case 5: adj_body<T, S, 32, Z3, DP, SPLIT>(a, I, tile, smem_raw, bars); break;
+    case 6: adj_body<T, S, 64, Z3, DP, SPLIT>(a, I, tile, smem_raw, bars); break;
+    case 7: adj_body<T, S, 128, Z3, DP, SPLIT>(a, I, tile, smem_raw, bars); break;
+    case 8: adj_body<T, S, 256, Z3, DP, SPLIT>(a, I, tile, smem_raw, bars); break;
+    case 9: adj_body<T, S, 512, Z3, DP, SPLIT>(a, I, tile, smem_raw, bars); break;
+    case 10: adj_body<T, S, 1024, Z3, DP, SPLIT>(a, I, tile, smem_raw, bars); break;
     default: break;
   }
 }
@@ -1194,6 +1200,107 @@ __global__ void __launch_bounds__(kAdjThreads, MB) adj_kernel(AdjArgs<T, S> a) {
   load_inst(sI, a.inst + tile.inst);
   __syncthreads();
   adj_dispatch<T, S, Z3, false>(a, sI, tile, smem_raw, bars);
+}
+
+// node phase of a film adjoint stage whose row transforms run as their own
+// launches (2 blocks per SM: shared memory holds only the halo rows)
+template <typename T>
+__global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? 2 : 1) adj_split_kernel(AdjArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ DevInst sI;
+  __shared__ uint64_t bars[2];
+  const RowTile tile = a.tiles[blockIdx.x];
+  load_inst(sI, a.inst + tile.inst);
+  __syncthreads();
+  adj_dispatch<T, T, false, false, true>(a, sI, tile, smem_raw, bars);
+}
+
+// ---------------------------------------------------------------------------
+// row transforms of a frequency domain as launches of their own (used with
+// the split adjoint stage): one row tile per block, the same thread layout
+// as the row-family kernels.  DIR = +1: bulk copy of the tile's spectrum
+// rows, inverse row FFT, the field at the nodes to `out`; DIR = -1: the
+// nodes' values from `src`, forward row FFT, packed rows to the spectrum.
+// Shared memory: exchange scratch (kExch complex of S) and W_{2L}.
+// ---------------------------------------------------------------------------
+
+template <typename T, typename S, int L, int DIR>
+__device__ __forceinline__ void spec_rows_body(const SpecRowArgs<T, S>& a, const DevInst& I, const RowTile& tile,
+                                               unsigned char* smem_raw, uint64_t* bar) {
+  using C = cplx<S>;
+  using G = RowGeom<L>;
+  constexpr int GS = group_stride(L);
+  const G g(threadIdx.x);
+  const int nr = tile.nrows;
+  const bool active = g.rl < nr;
+  const int nx = I.nx, ny = I.ny, y0 = tile.y0;
+  const int y = y0 + (active ? g.rl : 0);
+  const long long nodes = I.nodes;
+  const long long zoff = (long long)tile.z * I.layer;
+  C* sx = reinterpret_cast<C*>(smem_raw);
+  C* tw2 = sx + kExch;
+  C* sE = sx + g.rl * 3 * GS;
+  C* grp = sE + g.c * GS;
+  S* sEr = reinterpret_cast<S*>(sE);
+  C* row0 = a.spec + I.spec_off + ((long long)tile.z * ny + y0) * 3 * L;
+  const long long off3 = 3 * I.node_off;
+  if (DIR > 0 && threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  load_twiddles(tw2, a.tw, 2 * L);
+  __syncthreads();
+  if (DIR > 0) {
+    if (threadIdx.x == 0) {
+      const unsigned rowb = (unsigned)(L * sizeof(C));
+      mbar_arrive_expect(bar, nr * 3 * rowb);
+      for (int r = 0; r < nr; ++r)
+        for (int c = 0; c < 3; ++c) bulk_load(sx + (r * 3 + c) * GS, row0 + (r * 3 + c) * L, rowb, bar);
+    }
+    mbar_wait(bar, 0, a.err);
+    C v[8];
+    row_inverse_comp<S, L>(v, grp, active, grp, g.t, tw2);
+    __syncthreads();
+#pragma unroll 1
+    for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
+      const long long n0 = zoff + (long long)y * nx + x;
+      const int sl = node_slot<T, L>(x);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a.out[off3 + c * nodes + n0] = spec_to<T>(sEr[2 * c * GS + sl]);
+    }
+  } else {
+#pragma unroll 1
+    for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
+      const long long n0 = zoff + (long long)y * nx + x;
+      const int sl = node_slot<T, L>(x);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sEr[2 * c * GS + sl] = spec_from<S>(a.src[off3 + c * nodes + n0]);
+    }
+    __syncthreads();
+    row_forward_comp<S, L>(grp, nx / 2, a.spec + I.spec_off + ((long long)tile.z * ny + y) * 3 * L + g.c * L,
+                           active, g.t, tw2);
+  }
+}
+
+template <typename T, typename S, int DIR>
+__global__ void __launch_bounds__(kRowThreads, 2) spec_rows_kernel(SpecRowArgs<T, S> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ DevInst sI;
+  __shared__ uint64_t bar;
+  const RowTile tile = a.tiles[blockIdx.x];
+  load_inst(sI, a.inst + tile.inst);
+  __syncthreads();
+  switch (sI.log2Lx) {
+    case 3: spec_rows_body<T, S, 8, DIR>(a, sI, tile, smem_raw, &bar); break;
+    case 4: spec_rows_body<T, S, 16, DIR>(a, sI, tile, smem_raw, &bar); break;
+    case 5: spec_rows_body<T, S, 32, DIR>(a, sI, tile, smem_raw, &bar); break;
+    case 6: spec_rows_body<T, S, 64, DIR>(a, sI, tile, smem_raw, &bar); break;
+    case 7: spec_rows_body<T, S, 128, DIR>(a, sI, tile, smem_raw, &bar); break;
+    case 8: spec_rows_body<T, S, 256, DIR>(a, sI, tile, smem_raw, &bar); break;
+    case 9: spec_rows_body<T, S, 512, DIR>(a, sI, tile, smem_raw, &bar); break;
+    case 10: spec_rows_body<T, S, 1024, DIR>(a, sI, tile, smem_raw, &bar); break;
+    default: break;
+  }
 }
 
 // adjoint stage of a Dormand-Prince step (stages 6..1; the seed at stage 6)
@@ -1367,6 +1474,26 @@ void smem_adj(size_t smem) {
   raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, S, true, A>), &cur[1], smem);
   raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, S, false, B>), &cur[2], smem);
   raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, S, true, B>), &cur[3], smem);
+}
+template <typename T>
+void launch_adj_split(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st) {
+  adj_split_kernel<T><<<ntiles, kAdjThreads, smem, st>>>(a);
+}
+template <typename T>
+void smem_adj_split(size_t smem) {
+  static size_t cur = 0;
+  raise_smem_limit(reinterpret_cast<const void*>(adj_split_kernel<T>), &cur, smem);
+}
+template <typename T, typename S>
+void launch_spec_rows(const SpecRowArgs<T, S>& a, int dir, int ntiles, size_t smem, cudaStream_t st) {
+  if (dir > 0) spec_rows_kernel<T, S, 1><<<ntiles, kRowThreads, smem, st>>>(a);
+  else spec_rows_kernel<T, S, -1><<<ntiles, kRowThreads, smem, st>>>(a);
+}
+template <typename T, typename S>
+void smem_spec_rows(size_t smem) {
+  static size_t cur = 0, cur2 = 0;
+  raise_smem_limit(reinterpret_cast<const void*>(spec_rows_kernel<T, S, 1>), &cur, smem);
+  raise_smem_limit(reinterpret_cast<const void*>(spec_rows_kernel<T, S, -1>), &cur2, smem);
 }
 template <typename T>
 void launch_adj_dp(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3) {

@@ -179,7 +179,7 @@ struct llg_ctx {
   virtual double last_ms() const = 0;
   virtual long long launches() const = 0;
   virtual void kernel_time(int family, long long* count, double* ms) = 0;
-  llg_launch L{16, 2, 2, 2};   // the launch configuration in use
+  llg_launch L{16, 2, 2, 2, 1};   // the launch configuration in use
   double tune_ms = 0.0;        // host time spent timing candidates at create
 };
 
@@ -227,6 +227,11 @@ struct Engine final : llg_ctx {
   dcplx *spec_df = nullptr, *tw_df = nullptr;
   dfloat* tens_df = nullptr;
   size_t smem_cols_df = 0, smem_adj_df = 0;
+  // split double-float adjoint stage (llg_launch.adj_split): the node
+  // phase's FP32 kernel and the double-float row transforms, which pass the
+  // demag transpose through Dbuf (3 x nodes)
+  T* Dbuf = nullptr;
+  size_t smem_split = 0, smem_rows_df = 0;
   // per-(step, row tile) objective partials, per-row-tile terminal and psi
   // partials, per-instance J
   double *slots = nullptr, *jterm = nullptr, *psitile = nullptr, *Jd = nullptr, *rf = nullptr;
@@ -325,7 +330,7 @@ struct Engine final : llg_ctx {
     long long count = 0;
     double ms = 0.0;
   };
-  Timer timers[4];
+  Timer timers[5];
   void time_begin(int fam) {
     if (!opt.time_kernels) return;
     Timer& tm = timers[fam];
@@ -357,7 +362,7 @@ struct Engine final : llg_ctx {
     }
   }
   void kernel_time(int family, long long* count, double* ms) override {
-    if (family < 0 || family > 3) {
+    if (family < 0 || family > 4) {
       if (count) *count = 0;
       if (ms) *ms = 0.0;
       return;
@@ -494,8 +499,10 @@ struct Engine final : llg_ctx {
     if (opt.tune == LLG_TUNE_GIVEN) {
       const llg_launch& g = opt.launch;
       if ((g.col_lanes != 8 && g.col_lanes != 16) || (g.col_blocks != 1 && g.col_blocks != 2) ||
-          (g.adj_blocks != 1 && g.adj_blocks != 2) || (g.groups != 1 && g.groups != 2))
-        return fail(LLG_EINVAL, "launch: col_lanes 8 or 16, col_blocks, adj_blocks and groups 1 or 2");
+          (g.adj_blocks != 1 && g.adj_blocks != 2) || (g.groups != 1 && g.groups != 2) ||
+          (g.adj_split != 0 && g.adj_split != 1))
+        return fail(LLG_EINVAL, "launch: col_lanes 8 or 16, col_blocks, adj_blocks and groups 1 or 2, "
+                                "adj_split 0 or 1");
       L = g;
     }
     if (adj_df) {
@@ -526,6 +533,8 @@ struct Engine final : llg_ctx {
       if (adj_df) {
         smem_cols_df = std::max(smem_cols_df, cols_smem_bytes<dfloat>(Py));
         smem_adj_df = std::max(smem_adj_df, adj_smem_bytes<float, dfloat>(Lx, P[i].nx));
+        smem_split = std::max(smem_split, adj_split_smem_bytes<T>(Lx, P[i].nx));
+        smem_rows_df = std::max(smem_rows_df, spec_rows_smem_bytes<dfloat>(Lx));
       }
     }
     if (std::max(smem_cols_df, smem_adj_df) > 220 * 1024)
@@ -682,7 +691,8 @@ struct Engine final : llg_ctx {
               alloc(&maxbits, 2 * n) && alloc(&rf, (size_t)n * 3 * (N + 1)) && alloc(&errw, 1) &&
               alloc(&wext, n);
     if (!ok) return fail(LLG_ENOMEM, "device allocation failed (" + std::to_string(bytes >> 20) + " MiB so far)");
-    if (adj_df && !(alloc(&spec_df, total_spec) && alloc(&tw_df, kTwiddleN) && alloc(&tens_df, total_tens)))
+    if (adj_df && !(alloc(&spec_df, total_spec) && alloc(&tw_df, kTwiddleN) && alloc(&tens_df, total_tens) &&
+                    alloc(&Dbuf, slot())))
       return fail(LLG_ENOMEM, "device allocation failed (double-float adjoint spectrum)");
     if (rec_states && !(alloc(&mtmp, S) && alloc(&spec2, total_spec)))
       return fail(LLG_ENOMEM, "device allocation failed (step records)");
@@ -827,6 +837,8 @@ struct Engine final : llg_ctx {
       if (adj_df) {
         llg::smem_cols<dfloat>(smem_cols_df);
         llg::smem_adj<float, dfloat>(smem_adj_df);
+        llg::smem_adj_split<float>(smem_split);
+        llg::smem_spec_rows<float, dfloat>(smem_rows_df);
       }
     }
     cudaMemsetAsync(errw, 0, sizeof(int), st);
@@ -907,7 +919,8 @@ struct Engine final : llg_ctx {
       pick(&L.col_blocks, L.col_blocks == 2 ? 1 : 2, [&] { cols_df(); });
       cudaMemcpyAsync(recY_slot(0), m, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
       step(0, true, false);
-      pick(&L.adj_blocks, L.adj_blocks == 2 ? 1 : 2, [&] { reverse_segment(1); });
+      pick(&L.adj_split, L.adj_split ? 0 : 1, [&] { reverse_segment(1); });
+      if (!L.adj_split) pick(&L.adj_blocks, L.adj_blocks == 2 ? 1 : 2, [&] { reverse_segment(1); });
     }
     if (two) {
       two_groups = L.groups == 2;
@@ -1643,8 +1656,58 @@ struct Engine final : llg_ctx {
     }
     time_end(2);
   }
+  // double-float row transforms of the split adjoint stage (dir +1: spec_df
+  // -> Dbuf, dir -1: src -> spec_df)
+  void spec_rows_df(int dir, const T* src) {
+    if constexpr (std::is_same<T, float>::value) {
+      SpecRowArgs<float, dfloat> r;
+      r.inst = dI;
+      r.spec = spec_df;
+      r.tw = tw_df;
+      r.out = Dbuf;
+      r.src = src;
+      r.err = errw;
+      time_begin(4);
+      const auto p2 = part(rt2.size(), split_rt2);
+      if (p2.second) {
+        r.tiles = (grp_sel < 0 ? dRT2 : dRT2p) + p2.first;
+        launch_spec_rows<float, dfloat>(r, dir, (int)p2.second, smem_rows_df, st);
+        ++nlaunch;
+      }
+      time_end(4);
+    }
+  }
+
   template <typename S>
   void adj(const AdjArgs<T, S>& a0) {
+    if constexpr (!std::is_same<S, T>::value) {
+      if (L.adj_split) {
+        // inverse row transform of N * Bbar_s to Dbuf, the FP32 node phase,
+        // then the forward row transform of the next Bbar
+        AdjArgs<T> b = adj_args<T>();
+        b.local_step = a0.local_step;
+        b.stage = a0.stage;
+        b.seed_only = a0.seed_only;
+        b.seed_next = a0.seed_next;
+        b.Ys = a0.Ys;
+        b.Bbar = a0.Bbar;
+        b.BbarOut = a0.BbarOut;
+        b.Yprev = a0.Yprev;
+        b.Bprev = a0.Bprev;
+        b.Dext = Dbuf;
+        if (!b.seed_only) spec_rows_df(1, nullptr);
+        time_begin(2);
+        const auto p2 = part(rt2.size(), split_rt2);
+        if (p2.second) {
+          b.tiles = (grp_sel < 0 ? dRT2 : dRT2p) + p2.first;
+          launch_adj_split<T>(b, (int)p2.second, smem_split, st);
+          ++nlaunch;
+        }
+        time_end(2);
+        if (b.seed_only || b.stage > 1 || b.seed_next) spec_rows_df(-1, b.BbarOut);
+        return;
+      }
+    }
     AdjArgs<T, S> a = a0;
     const size_t sm = std::is_same<S, T>::value ? smem_adj : smem_adj_df;
     const int mb = std::is_same<S, T>::value ? 0 : L.adj_blocks;
@@ -1828,7 +1891,7 @@ llg_status llg_query(llg_ctx* ctx, size_t* device_bytes, double* last_ms) {
 long long llg_launch_count(llg_ctx* ctx) { return ctx ? ctx->launches() : 0; }
 
 llg_status llg_kernel_time(llg_ctx* ctx, int family, long long* launches, double* total_ms) {
-  if (!ctx || family < 0 || family > 3) return LLG_EINVAL;
+  if (!ctx || family < 0 || family > 4) return LLG_EINVAL;
   ctx->kernel_time(family, launches, total_ms);
   return LLG_OK;
 }

@@ -61,7 +61,8 @@ class llg_problem(ctypes.Structure):
 
 
 class llg_launch(ctypes.Structure):
-    _fields_ = [("col_lanes", c_int), ("col_blocks", c_int), ("adj_blocks", c_int), ("groups", c_int)]
+    _fields_ = [("col_lanes", c_int), ("col_blocks", c_int), ("adj_blocks", c_int), ("groups", c_int),
+                ("adj_split", c_int)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -201,7 +202,7 @@ def llg_create(problems: Sequence, precision=LLG_FP32, ckpt=LLG_CKPT_PERIODIC, s
     lib = load()
     structs = [to_struct(p) for p in problems]          # hold the host arrays until create returns
     arr = (llg_problem * len(problems))(*structs)
-    lc = llg_launch(**launch) if launch else llg_launch(16, 2, 2, 2)
+    lc = llg_launch(**launch) if launch else llg_launch(16, 2, 2, 2, 1)
     opt = llg_options(precision, ckpt, seg_len, use_graph, tune, time_kernels, integrator,
                       rtol, atol, adj_spectral, lc, record)
     ctx = c_void_p()
@@ -332,7 +333,8 @@ def llg_launch_count(ctx: int) -> int:
 
 def llg_kernel_time(ctx: int, family: int):
     """(launches, total_ms) of a kernel family: 0 row stage, 1 column, 2 adjoint,
-    3 column pass of the double-float adjoint spectrum."""
+    3 column pass of the double-float adjoint spectrum, 4 its row transforms
+    (split adjoint stage)."""
     lib = load()
     n = c_ll()
     ms = c_double()

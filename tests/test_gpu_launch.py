@@ -2,8 +2,9 @@
 the C ABI.
 
 * Every launch-configuration candidate (llg_launch: register-cap variants of
-  the double-float column and adjoint kernels, one or two instance-group
-  chains) gives bit-identical J and gradients to the default; the FP32
+  the double-float column and adjoint kernels, the fused or split
+  double-float adjoint stage, one or two instance-group chains) gives
+  bit-identical J and gradients to the default; the FP32
   column pass with 8- instead of 16-element FFT lanes (a different radix
   order) meets the oracle bars.  The configuration the timing search picks
   (LLG_TUNE_MEASURE) meets them too, and a second context of the same batch
@@ -40,15 +41,15 @@ def _batch():
             W.random_small(8, 100, 1, seed=44, nsteps=12)]
 
 
-DEFAULT = {"col_lanes": 16, "col_blocks": 2, "adj_blocks": 2, "groups": 2}
+DEFAULT = {"col_lanes": 16, "col_blocks": 2, "adj_blocks": 2, "groups": 2, "adj_split": 1}
 
 
 @pytest.mark.parametrize("precision,spec", [("fp32", "dfloat"), ("fp32", "working"), ("fp64", "working")])
 def test_launch_candidates_are_bit_identical(precision, spec):
     insts = _batch()
     ref = gpu_run(insts, precision, adj_spectral=spec, tune="given", launch=DEFAULT, want_dm0=True)
-    for field, alt in (("col_blocks", 1), ("adj_blocks", 1), ("groups", 1)):
-        cfg = dict(DEFAULT, **{field: alt})
+    for alt in ({"col_blocks": 1}, {"adj_split": 0}, {"adj_split": 0, "adj_blocks": 1}, {"groups": 1}):
+        cfg = dict(DEFAULT, **alt)
         g = gpu_run(insts, precision, adj_spectral=spec, tune="given", launch=cfg, want_dm0=True)
         np.testing.assert_array_equal(g["J"], ref["J"])
         for k in range(len(insts)):
@@ -72,7 +73,7 @@ def test_measured_configuration_meets_the_oracle_and_is_cached():
     try:
         cfg, ms = s.launch_config()
         assert cfg["col_lanes"] in (8, 16) and cfg["col_blocks"] in (1, 2)
-        assert cfg["adj_blocks"] in (1, 2) and cfg["groups"] in (1, 2)
+        assert cfg["adj_blocks"] in (1, 2) and cfg["groups"] in (1, 2) and cfg["adj_split"] in (0, 1)
     finally:
         s.close()
     s2 = gpu_solver(insts, "fp32", adj_spectral="dfloat", tune="measure")
