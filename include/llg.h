@@ -86,7 +86,10 @@ typedef struct {
                       lanes, 384-thread blocks)                           */
   int col_blocks;  /* double-float column pass: the blocks per SM its
                       register cap is compiled for, 2 (80 registers) or 1  */
-  int adj_blocks;  /* double-float adjoint stage kernel: 2 or 1           */
+  int adj_blocks;  /* double-float adjoint stage: blocks per SM the fused
+                      kernel (1 or 2) or the split stage's FP32 node phase
+                      (2, or 3 with a 56-register cap and spills; 1 acts
+                      as 2) is compiled for                               */
   int groups;      /* RK4 segments as 2 independent chains (even and odd
                       instances on two streams) or 1                      */
   int adj_split;   /* double-float adjoint stage: 1 = three launches (the

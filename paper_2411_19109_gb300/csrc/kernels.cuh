@@ -162,7 +162,7 @@ void launch_adj(const AdjArgs<T, S>& a, int ntiles, size_t smem, cudaStream_t st
 // transpose read from a.Dext and without the row transforms, whose own
 // launches (spec_rows) run them in the frequency domain's type.
 template <typename T>
-void launch_adj_split(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st);
+void launch_adj_split(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, int mb);
 template <typename T>
 void smem_adj_split(size_t smem);
 template <typename T>

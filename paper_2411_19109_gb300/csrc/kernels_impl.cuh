@@ -221,10 +221,20 @@ __device__ __forceinline__ void load_tensor_smem(const double* tab, int idx, dou
   const double2 b = reinterpret_cast<const double2*>(tab)[2 * idx + 1];
   n[0] = a.x; n[1] = a.y; n[2] = b.x; n[3] = b.y;
 }
-__device__ __forceinline__ void load_tensor_smem(const dfloat* tab, int idx, dfloat n[4]) {
-  const float4 a = reinterpret_cast<const float4*>(tab)[2 * idx];
-  const float4 b = reinterpret_cast<const float4*>(tab)[2 * idx + 1];
-  n[0] = dfloat(a.x, a.y); n[1] = dfloat(a.z, a.w); n[2] = dfloat(b.x, b.y); n[3] = dfloat(b.z, b.w);
+// Record ky of column slot col of a tile's tensor records (nky per column).
+// Double-float film tables are planar per column -- the nky hi records
+// (xx, yy, zz, xy) then the nky lo records, 16 bytes each -- so that
+// consecutive lanes' 16-byte loads meet distinct bank groups (interleaved
+// 32-byte records gave every load a 2-way conflict).
+template <typename T>
+__device__ __forceinline__ void load_tensor_col(const T* tab, int col, int nky, int ky, T n[4]) {
+  load_tensor_smem(tab, col * nky + ky, n);
+}
+template <>
+__device__ __forceinline__ void load_tensor_col<dfloat>(const dfloat* tab, int col, int nky, int ky, dfloat n[4]) {
+  const float4* q = reinterpret_cast<const float4*>(tab) + 2 * col * nky;
+  const float4 h = q[ky], l = q[nky + ky];
+  n[0] = dfloat(h.x, l.x); n[1] = dfloat(h.y, l.y); n[2] = dfloat(h.z, l.z); n[3] = dfloat(h.w, l.w);
 }
 __device__ __forceinline__ void load_tensor(const double* tab, long long idx, double n[4]) {
   const double2 a = __ldg(reinterpret_cast<const double2*>(tab) + 2 * idx);
@@ -297,7 +307,7 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
     const int kyf = lo ? ky : L - ky;
     if (kx != 0) {
       T n[4];
-      load_tensor_smem(stab, cl * nky + kyf, n);
+      load_tensor_col(stab, cl, nky, kyf, n);
       const T nxy = lo ? n[3] : -n[3];
       if (c == 2) {
         v[s] = cscale(v[s], n[2]);
@@ -310,8 +320,8 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
       // packed DC (kx = 0) and Nyquist (kx = Px/2) columns: separate them by
       // Hermitian symmetry in ky, apply each its own (diagonal) tensor
       T nd[4], nq[4];
-      load_tensor_smem(stab, kyf, nd);
-      load_tensor_smem(stab, NC * nky + kyf, nq);
+      load_tensor_col(stab, 0, nky, kyf, nd);
+      load_tensor_col(stab, NC, nky, kyf, nq);
       const int km = (L - ky) & (L - 1);
       const T p = (T)0.5 * (nd[c] + nq[c]), q = (T)0.5 * (nd[c] - nq[c]);
       const C vb = cconj(grp[rf_pad(km)]);
@@ -1203,9 +1213,10 @@ __global__ void __launch_bounds__(kAdjThreads, MB) adj_kernel(AdjArgs<T, S> a) {
 }
 
 // node phase of a film adjoint stage whose row transforms run as their own
-// launches (2 blocks per SM: shared memory holds only the halo rows)
-template <typename T>
-__global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? 2 : 1) adj_split_kernel(AdjArgs<T> a) {
+// launches (shared memory holds only the halo rows); MB: 2 or 3 blocks per
+// SM (80 or 56 registers, the latter with spills: a launch candidate)
+template <typename T, int MB>
+__global__ void __launch_bounds__(kAdjThreads, MB) adj_split_kernel(AdjArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ DevInst sI;
   __shared__ uint64_t bars[2];
@@ -1476,13 +1487,15 @@ void smem_adj(size_t smem) {
   raise_smem_limit(reinterpret_cast<const void*>(adj_kernel<T, S, true, B>), &cur[3], smem);
 }
 template <typename T>
-void launch_adj_split(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st) {
-  adj_split_kernel<T><<<ntiles, kAdjThreads, smem, st>>>(a);
+void launch_adj_split(const AdjArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, int mb) {
+  if (mb == 3) adj_split_kernel<T, 3><<<ntiles, kAdjThreads, smem, st>>>(a);
+  else adj_split_kernel<T, 2><<<ntiles, kAdjThreads, smem, st>>>(a);
 }
 template <typename T>
 void smem_adj_split(size_t smem) {
-  static size_t cur = 0;
-  raise_smem_limit(reinterpret_cast<const void*>(adj_split_kernel<T>), &cur, smem);
+  static size_t cur = 0, cur3 = 0;
+  raise_smem_limit(reinterpret_cast<const void*>(adj_split_kernel<T, 2>), &cur, smem);
+  raise_smem_limit(reinterpret_cast<const void*>(adj_split_kernel<T, 3>), &cur3, smem);
 }
 template <typename T, typename S>
 void launch_spec_rows(const SpecRowArgs<T, S>& a, int dir, int ntiles, size_t smem, cudaStream_t st) {

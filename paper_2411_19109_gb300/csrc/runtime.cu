@@ -499,9 +499,9 @@ struct Engine final : llg_ctx {
     if (opt.tune == LLG_TUNE_GIVEN) {
       const llg_launch& g = opt.launch;
       if ((g.col_lanes != 8 && g.col_lanes != 16) || (g.col_blocks != 1 && g.col_blocks != 2) ||
-          (g.adj_blocks != 1 && g.adj_blocks != 2) || (g.groups != 1 && g.groups != 2) ||
+          (g.adj_blocks < 1 || g.adj_blocks > 3) || (g.groups != 1 && g.groups != 2) ||
           (g.adj_split != 0 && g.adj_split != 1))
-        return fail(LLG_EINVAL, "launch: col_lanes 8 or 16, col_blocks, adj_blocks and groups 1 or 2, "
+        return fail(LLG_EINVAL, "launch: col_lanes 8 or 16, col_blocks and groups 1 or 2, adj_blocks 1 to 3, "
                                 "adj_split 0 or 1");
       L = g;
     }
@@ -920,7 +920,10 @@ struct Engine final : llg_ctx {
       cudaMemcpyAsync(recY_slot(0), m, sizeof(T) * slot(), cudaMemcpyDeviceToDevice, st);
       step(0, true, false);
       pick(&L.adj_split, L.adj_split ? 0 : 1, [&] { reverse_segment(1); });
-      if (!L.adj_split) pick(&L.adj_blocks, L.adj_blocks == 2 ? 1 : 2, [&] { reverse_segment(1); });
+      // the split node phase compiles for 2 or 3 blocks per SM, the fused
+      // stage for 1 or 2
+      if (L.adj_split) pick(&L.adj_blocks, L.adj_blocks == 3 ? 2 : 3, [&] { reverse_segment(1); });
+      else pick(&L.adj_blocks, L.adj_blocks == 2 ? 1 : 2, [&] { reverse_segment(1); });
     }
     if (two) {
       two_groups = L.groups == 2;
@@ -1700,7 +1703,7 @@ struct Engine final : llg_ctx {
         const auto p2 = part(rt2.size(), split_rt2);
         if (p2.second) {
           b.tiles = (grp_sel < 0 ? dRT2 : dRT2p) + p2.first;
-          launch_adj_split<T>(b, (int)p2.second, smem_split, st);
+          launch_adj_split<T>(b, (int)p2.second, smem_split, st, L.adj_blocks);
           ++nlaunch;
         }
         time_end(2);

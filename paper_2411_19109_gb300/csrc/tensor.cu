@@ -179,6 +179,21 @@ __global__ void fft_lines_kernel(double2* data, int log2L, int nlines, long long
 // Packed table [kx 0..Px/2][ky 0..Py/2][4] of -mu0/(Px Py) * Re(G^).  The xy
 // component is odd in both coordinates, so it vanishes exactly on the kx = 0,
 // kx = Px/2, ky = 0 and ky = Py/2 lines; those entries are set to zero.
+// Record (kx, ky) lives at table[(kx nky + ky) 4 + c]; a double-float
+// table stores each column kx planar, its nky hi records (4 floats each)
+// then its nky lo records, in the same 8 floats per record of space.
+template <typename T>
+__device__ __forceinline__ void tensor_put(T* table, int kx, int ky, int nky, int c, double v) {
+  table[((long long)kx * nky + ky) * 4 + c] = (T)v;
+}
+template <>
+__device__ __forceinline__ void tensor_put<dfloat>(dfloat* table, int kx, int ky, int nky, int c, double v) {
+  const dfloat d(v);
+  float* col = reinterpret_cast<float*>(table) + (long long)kx * nky * 8;
+  col[ky * 4 + c] = d.hi;
+  col[(nky + ky) * 4 + c] = d.lo;
+}
+
 template <typename T>
 __global__ void tensor_pack_kernel(const double2* G, T* table, int Px, int Py) {
   const int nkx = Px / 2 + 1, nky = Py / 2 + 1;
@@ -190,7 +205,7 @@ __global__ void tensor_pack_kernel(const double2* G, T* table, int Px, int Py) {
   for (int c = 0; c < 4; ++c) {
     double v = G[c * plane + (long long)ky * Px + kx].x * scale;
     if (c == 3 && (kx == 0 || kx == Px / 2 || ky == 0 || ky == Py / 2)) v = 0.0;
-    table[(long long)idx * 4 + c] = (T)v;
+    tensor_put(table, kx, ky, nky, c, v);
   }
 }
 

@@ -48,7 +48,8 @@ DEFAULT = {"col_lanes": 16, "col_blocks": 2, "adj_blocks": 2, "groups": 2, "adj_
 def test_launch_candidates_are_bit_identical(precision, spec):
     insts = _batch()
     ref = gpu_run(insts, precision, adj_spectral=spec, tune="given", launch=DEFAULT, want_dm0=True)
-    for alt in ({"col_blocks": 1}, {"adj_split": 0}, {"adj_split": 0, "adj_blocks": 1}, {"groups": 1}):
+    for alt in ({"col_blocks": 1}, {"adj_blocks": 3}, {"adj_split": 0}, {"adj_split": 0, "adj_blocks": 1},
+                {"groups": 1}):
         cfg = dict(DEFAULT, **alt)
         g = gpu_run(insts, precision, adj_spectral=spec, tune="given", launch=cfg, want_dm0=True)
         np.testing.assert_array_equal(g["J"], ref["J"])
@@ -73,7 +74,7 @@ def test_measured_configuration_meets_the_oracle_and_is_cached():
     try:
         cfg, ms = s.launch_config()
         assert cfg["col_lanes"] in (8, 16) and cfg["col_blocks"] in (1, 2)
-        assert cfg["adj_blocks"] in (1, 2) and cfg["groups"] in (1, 2) and cfg["adj_split"] in (0, 1)
+        assert cfg["adj_blocks"] in (1, 2, 3) and cfg["groups"] in (1, 2) and cfg["adj_split"] in (0, 1)
     finally:
         s.close()
     s2 = gpu_solver(insts, "fp32", adj_spectral="dfloat", tune="measure")
