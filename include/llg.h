@@ -184,14 +184,19 @@ typedef struct {
                       m|, |psi y5|)))^2)) over nodes and components, accept
                       if err <= 1, h <- h min(5, max(0.2, 0.9 err^-1/5)),
                       the last step shortened to end at T.  At most
-                      seg_len (0: nsteps) accepted steps, one checkpoint of
-                      m each, and 4 nsteps attempts per instance
-                      (LLG_ETIMEOUT beyond).  The gradient is the exact
-                      derivative over the accepted steps (their sizes held
-                      fixed), from a store-all checkpoint of every accepted
-                      step.  Needs the LLG_J_ENERGY_AREA objective and the
-                      sine drive (no drive table); ckpt is ignored,
-                      use_graph replays captured attempts.                   */
+                      seg_len (0: nsteps) accepted steps and 4 nsteps
+                      attempts per instance (LLG_ETIMEOUT beyond).  The
+                      gradient is the exact derivative over the accepted
+                      steps (their sizes held fixed).  Checkpoints:
+                      LLG_CKPT_STORE_ALL keeps m of every accepted step;
+                      otherwise m of every K-th accepted step, K =
+                      ceil(sqrt(seg_len or nsteps)), and the reverse sweep,
+                      in blocks of K steps, first replays each instance's
+                      recorded steps (t_k, h_k) from the checkpoint at or
+                      before its block (bit-identical states; up to 2K - 1
+                      replayed steps per block).  Needs the
+                      LLG_J_ENERGY_AREA objective and the sine drive (no
+                      drive table); use_graph replays captured attempts.   */
   double rtol, atol; /* LLG_INT_DOPRI5 tolerances                            */
   int adj_spectral;  /* frequency domain of the adjoint's demag transpose
                         (the row and column FFTs, the stored spectrum and the

@@ -11,4 +11,6 @@ template void launch_adj_dp<float>(const AdjArgs<float>&, int, size_t, cudaStrea
 template void smem_adj_dp<float>(size_t);
 template void launch_dp_gather<float>(const DevInst*, const RowTile*, int, const float*, long long, const long long*,
                                        float*, cudaStream_t);
+template void launch_dp_push<float>(const DevInst*, const RowTile*, int, const float*, float*, long long, const long long*,
+                                   float*, cudaStream_t);
 }  // namespace llg

@@ -11,4 +11,6 @@ template void launch_adj_dp<double>(const AdjArgs<double>&, int, size_t, cudaStr
 template void smem_adj_dp<double>(size_t);
 template void launch_dp_gather<double>(const DevInst*, const RowTile*, int, const double*, long long, const long long*,
                                        double*, cudaStream_t);
+template void launch_dp_push<double>(const DevInst*, const RowTile*, int, const double*, double*, long long, const long long*,
+                                   double*, cudaStream_t);
 }  // namespace llg

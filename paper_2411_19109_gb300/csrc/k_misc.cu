@@ -164,14 +164,14 @@ void launch_dp_control(const DevInst* inst, int n_inst, const double* eslots, do
 // Reverse step r of the adjoint sweep: each instance reverses its accepted
 // step k = cnt - 1 - r with the recorded (t_k, h_k), or idles (h = 0).
 __global__ void dp_reverse_state_kernel(int n_inst, const double* sched, const int* cnt, const long long* rptr,
-                                        double* hst, long long* slot) {
+                                        double* hst, long long* slot, const long long* base) {
   const long long r = *rptr;
   for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
     const long long k = (long long)cnt[i] - 1 - r;
     if (k >= 0) {
       hst[4 * i] = sched[2 * (k * n_inst + i)];
       hst[4 * i + 1] = sched[2 * (k * n_inst + i) + 1];
-      slot[i] = k;
+      slot[i] = k - (base ? base[i] : 0);
     } else {
       hst[4 * i] = 0.0;
       hst[4 * i + 1] = 0.0;
@@ -181,8 +181,48 @@ __global__ void dp_reverse_state_kernel(int n_inst, const double* sched, const i
 }
 
 void launch_dp_reverse_state(int n_inst, const double* sched, const int* cnt, const long long* rptr, double* hst,
-                             long long* slot, cudaStream_t st) {
-  dp_reverse_state_kernel<<<1, 256, 0, st>>>(n_inst, sched, cnt, rptr, hst, slot);
+                             long long* slot, const long long* base, cudaStream_t st) {
+  dp_reverse_state_kernel<<<1, 256, 0, st>>>(n_inst, sched, cnt, rptr, hst, slot, base);
+}
+
+__global__ void dp_replay_plan_kernel(int n_inst, const int* cnt, long long b, long long K, long long* k0,
+                                      long long* khi, long long* ckslot) {
+  for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+    const long long hi = (long long)cnt[i] - 1 - b * K;
+    if (hi < 0) {
+      k0[i] = 0;
+      khi[i] = 0;
+      ckslot[i] = -1;
+      continue;
+    }
+    const long long lo = max(0LL, (long long)cnt[i] - (b + 1) * K);
+    k0[i] = (lo / K) * K;
+    khi[i] = hi;
+    ckslot[i] = lo / K;
+  }
+}
+void launch_dp_replay_plan(int n_inst, const int* cnt, long long b, long long K, long long* k0, long long* khi,
+                           long long* ckslot, cudaStream_t st) {
+  dp_replay_plan_kernel<<<1, 256, 0, st>>>(n_inst, cnt, b, K, k0, khi, ckslot);
+}
+
+__global__ void dp_replay_state_kernel(int n_inst, const double* sched, const long long* jptr, const long long* k0,
+                                       const long long* khi, double* hst) {
+  const long long j = *jptr;
+  for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+    const long long k = k0[i] + j;
+    if (k < khi[i]) {
+      hst[4 * i] = sched[2 * (k * n_inst + i)];
+      hst[4 * i + 1] = sched[2 * (k * n_inst + i) + 1];
+    } else {
+      hst[4 * i] = 0.0;
+      hst[4 * i + 1] = 0.0;
+    }
+  }
+}
+void launch_dp_replay_state(int n_inst, const double* sched, const long long* jptr, const long long* k0,
+                            const long long* khi, double* hst, cudaStream_t st) {
+  dp_replay_state_kernel<<<1, 256, 0, st>>>(n_inst, sched, jptr, k0, khi, hst);
 }
 
 template <typename T>

@@ -54,7 +54,9 @@ struct RowArgs {
   double* eslots;     // per row tile: sum of the scaled squared errors (stage 7)
   const int* accept;  // ROW_DP_START: per instance, the last attempt was accepted
   const int* cnt;     // ROW_DP_START: per instance, accepted steps so far (checkpoint slot)
-  T* ckall;           // ROW_DP_START: per accepted step, m (slot k at ckall + k * kstride); nullable
+  T* ckall;           // ROW_DP_START: m of every ck_every-th accepted step k (slot k / ck_every at
+                      // ckall + slot * kstride); nullable
+  int ck_every;       // ROW_DP_START: checkpoint period in accepted steps (0 or 1: every step)
   const T* y5;        // ROW_DP_START: the last attempt's fifth-order solution
   // ROW_TERMINAL outputs
   T* lam;             // lambda_N
@@ -208,10 +210,25 @@ void smem_adj_dp(size_t smem);
 template <typename T>
 void launch_dp_gather(const DevInst* inst, const RowTile* tiles, int ntiles, const T* ckall, long long kstride,
                       const long long* slot, T* out, cudaStream_t st);
+template <typename T>
+void launch_dp_push(const DevInst* inst, const RowTile* tiles, int ntiles, const T* src, T* seg, long long kstride,
+                    const long long* jptr, T* mrev, cudaStream_t st);
 void launch_dp_control(const DevInst* inst, int n_inst, const double* eslots, double* hst, int* accept, int* cnt,
                        double* sched, long long max_steps, double T_end, int* overflow, cudaStream_t st);
+// reverse index *rptr: each instance's step k = cnt - 1 - r with its (t, h)
+// into hst and its state slot k - base[i] (base nullable: 0) into slot
 void launch_dp_reverse_state(int n_inst, const double* sched, const int* cnt, const long long* rptr, double* hst,
-                             long long* slot, cudaStream_t st);
+                             long long* slot, const long long* base, cudaStream_t st);
+// periodic checkpoints, reverse block b of K reverse indices: per instance
+// the window's last step khi = cnt - 1 - b K, its first replayed step k0 (a
+// checkpoint, k0 = K floor(max(0, cnt - (b + 1) K) / K)) and that
+// checkpoint's slot (-1: the instance has no step in this block)
+void launch_dp_replay_plan(int n_inst, const int* cnt, long long b, long long K, long long* k0, long long* khi,
+                           long long* ckslot, cudaStream_t st);
+// replay step *jptr of the block: instance i advances its step k0 + j with
+// the recorded (t, h) while k0 + j < khi, else idles with h = 0
+void launch_dp_replay_state(int n_inst, const double* sched, const long long* jptr, const long long* k0,
+                            const long long* khi, double* hst, cudaStream_t st);
 template <typename T>
 void set_smem_limits(size_t stage, size_t misc, size_t cols, size_t adj);
 template <typename T>

@@ -443,7 +443,10 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
   // the first stage input Y_2 = m + h a(2, 1) k_1
   const bool dp_acc = MODE == ROW_DP_START && a.accept[tile.inst] != 0;
   const T dp_h = MODE == ROW_DP_START ? (T)a.hst[4 * tile.inst + 1] : (T)0;
-  const long long dp_slot = MODE == ROW_DP_START && a.ckall ? (long long)a.cnt[tile.inst] * a.kstride : -1;
+  const int dp_every = a.ck_every > 1 ? a.ck_every : 1;
+  const long long dp_slot = MODE == ROW_DP_START && a.ckall && a.cnt[tile.inst] % dp_every == 0
+                                ? (long long)(a.cnt[tile.inst] / dp_every) * a.kstride
+                                : -1;
   double vsum = 0.0;
 #pragma unroll 1
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
@@ -471,7 +474,11 @@ __device__ __forceinline__ void rows_body(const RowArgs<T>& a, const DevInst& I,
           mv = a.m[id];
           k1 = a.kbuf[id];
         }
-        const T y2 = mv + dp_h * a.dpa[0] * k1;
+        // associated as the stage kernel forms Y_{s+1} = m + h (a k), so
+        // that a stage recomputed from m (reverse sweep, replay) repeats
+        // this one bit for bit
+        const T acc2 = a.dpa[0] * k1;
+        const T y2 = mv + dp_h * acc2;
         a.Yout[id] = y2;
         sEr[2 * c * GS + sl] = Ms * p * y2;
       }
@@ -1541,6 +1548,30 @@ template <typename T>
 void launch_dp_gather(const DevInst* inst, const RowTile* tiles, int ntiles, const T* ckall, long long kstride,
                       const long long* slot, T* out, cudaStream_t st) {
   dp_gather_kernel<T><<<ntiles, 256, 0, st>>>(inst, tiles, ckall, kstride, slot, out);
+}
+
+// Dormand-Prince replay: src (the state after replay step *jptr) to segment
+// slot j + 1 and to the working state mrev (src may be mrev itself)
+template <typename T>
+__global__ void dp_push_kernel(const DevInst* inst, const RowTile* tiles, const T* src, T* seg, long long kstride,
+                               const long long* jptr, T* mrev) {
+  const RowTile tile = tiles[blockIdx.x];
+  const DevInst& I = inst[tile.inst];
+  const long long j1 = *jptr + 1;
+  const long long base = tile_base(I, tile);
+  const int cnt = tile.nrows * I.nx;
+  for (int c = 0; c < 3; ++c)
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const long long id = 3 * I.node_off + (long long)c * I.nodes + (base - I.node_off) + e;
+      const T v = src[id];
+      seg[j1 * kstride + id] = v;
+      mrev[id] = v;
+    }
+}
+template <typename T>
+void launch_dp_push(const DevInst* inst, const RowTile* tiles, int ntiles, const T* src, T* seg, long long kstride,
+                    const long long* jptr, T* mrev, cudaStream_t st) {
+  dp_push_kernel<T><<<ntiles, 256, 0, st>>>(inst, tiles, src, seg, kstride, jptr, mrev);
 }
 template <typename T>
 void launch_material_tiles(const DevInst* inst, const RowTile* tiles, int ntiles, const T* phi, T* psi,

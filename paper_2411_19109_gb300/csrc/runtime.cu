@@ -257,6 +257,13 @@ struct Engine final : llg_ctx {
   long long dp_maxK = 0;
   T *dp_k = nullptr, *dp_y5 = nullptr, *dp_ck = nullptr, *dp_recY = nullptr, *dp_recB = nullptr;
   T *dp_eta = nullptr, *dp_mrev = nullptr;
+  // periodic checkpoints of the accepted steps (LLG_CKPT_PERIODIC): m every
+  // dp_K-th accepted step; the reverse sweep replays each block's steps from
+  // the recorded (t, h) into dp_seg (up to 2 dp_K states) before reversing
+  // them.  dp_K = 1: one checkpoint per accepted step, no replay.
+  long long dp_K = 1;
+  T* dp_seg = nullptr;
+  long long *dp_k0 = nullptr, *dp_khi = nullptr, *dp_ckslot = nullptr;
   double *dp_e = nullptr, *dp_hst = nullptr, *dp_sched = nullptr;
   int *dp_acc = nullptr, *dp_cnt = nullptr, *dp_ovf = nullptr;
   long long* dp_slot = nullptr;
@@ -280,7 +287,7 @@ struct Engine final : llg_ctx {
   // ADVANCE_ADJ: recomputation during the reverse sweep (no objective terms).
   // The cache holds at most kMaxGraphs graphs; other shapes run directly.
   enum SegKind { SEG_ADVANCE = 0, SEG_RECORD_FWD = 1, SEG_RECORD_ADJ = 2, SEG_REVERSE = 3, SEG_ADVANCE_ADJ = 4,
-                 SEG_DP_ATTEMPT = 5, SEG_DP_REVERSE = 6 };
+                 SEG_DP_ATTEMPT = 5, SEG_DP_REVERSE = 6, SEG_DP_REPLAY = 7 };
   static constexpr size_t kMaxGraphs = 64;
   std::map<std::pair<int, long long>, std::pair<cudaGraphExec_t, long long>> graphs;
   cudaStream_t cap_st = nullptr;   // private stream the captures are recorded on
@@ -721,15 +728,18 @@ struct Engine final : llg_ctx {
     }
     if (dp_mode) {
       const long long K7 = 7, R6 = 6;
-      dp_maxK = opt.seg_len > 0 ? std::min<long long>(opt.seg_len, N) : N;   // checkpoint slots
-      const bool ok2 = alloc(&dp_k, S * K7) && alloc(&dp_y5, S) && alloc(&dp_ck, S * (dp_maxK + 1)) &&
+      dp_maxK = opt.seg_len > 0 ? std::min<long long>(opt.seg_len, N) : N;   // accepted steps at most
+      dp_K = opt.ckpt == LLG_CKPT_STORE_ALL ? 1 : std::max(1LL, isqrt_ceil(dp_maxK));
+      const bool ok2 = alloc(&dp_k, S * K7) && alloc(&dp_y5, S) && alloc(&dp_ck, S * (dp_maxK / dp_K + 1)) &&
+                       (dp_K == 1 || (alloc(&dp_seg, S * 2 * dp_K) && alloc(&dp_k0, n) && alloc(&dp_khi, n) &&
+                                      alloc(&dp_ckslot, n))) &&
                        alloc(&dp_recY, S * R6) && alloc(&dp_recB, S * R6) && alloc(&dp_eta, S * R6) &&
                        alloc(&dp_mrev, S) && alloc(&dp_e, rt.size()) && alloc(&dp_hst, 4 * (size_t)n) &&
                        alloc(&dp_sched, 2 * (size_t)n * std::max(1LL, dp_maxK)) && alloc(&dp_acc, n) &&
                        alloc(&dp_cnt, n) &&
                        alloc(&dp_ovf, 1) && alloc(&dp_slot, n);
       if (!ok2)
-        return fail(LLG_ENOMEM, "device allocation failed for the adaptive integrator's store-all checkpoints (" +
+        return fail(LLG_ENOMEM, "device allocation failed for the adaptive integrator's checkpoints (" +
                                     std::to_string(bytes >> 20) + " MiB so far)");
     }
 
@@ -1165,7 +1175,7 @@ struct Engine final : llg_ctx {
   // RK4 segments with two instance groups: fork to the second stream, run
   // each group's whole segment on its own stream, join
   void segment_body(int kind, long long len) {
-    if (!two_groups || kind == SEG_DP_ATTEMPT || kind == SEG_DP_REVERSE) {
+    if (!two_groups || kind == SEG_DP_ATTEMPT || kind == SEG_DP_REVERSE || kind == SEG_DP_REPLAY) {
       segment_body_one(kind, len);
       return;
     }
@@ -1190,6 +1200,10 @@ struct Engine final : llg_ctx {
     }
     if (kind == SEG_DP_REVERSE) {
       dp_reverse_step();
+      return;
+    }
+    if (kind == SEG_DP_REPLAY) {
+      dp_replay_step();
       return;
     }
     if (kind == SEG_REVERSE) {
@@ -1347,6 +1361,7 @@ struct Engine final : llg_ctx {
     a.accept = dp_acc;
     a.cnt = dp_cnt;
     a.ckall = dp_ck;
+    a.ck_every = (int)dp_K;
     a.y5 = dp_y5;
     a.m = m;
     a.mout = m;
@@ -1453,8 +1468,8 @@ struct Engine final : llg_ctx {
     auto Yrec = [&](int s) { return dp_recY + (long long)(s - 1) * S; };   // Y_s, s = 2..6 (Y_1 = mrev)
     auto Brec = [&](int s) { return dp_recB + (long long)(s - 1) * S; };
     auto Ys = [&](int s) -> T* { return s == 1 ? dp_mrev : Yrec(s); };
-    launch_dp_reverse_state(n, dp_sched, dp_cnt, step_base, dp_hst, dp_slot, st);
-    launch_dp_gather<T>(dI, dRT, (int)rt.size(), dp_ck, S, dp_slot, dp_mrev, st);
+    launch_dp_reverse_state(n, dp_sched, dp_cnt, step_base, dp_hst, dp_slot, dp_K > 1 ? dp_k0 : nullptr, st);
+    launch_dp_gather<T>(dI, dRT, (int)rt.size(), dp_K > 1 ? dp_seg : dp_ck, S, dp_slot, dp_mrev, st);
     nlaunch += 2;
     fft_only(dp_mrev);
     for (int s = 1; s <= 6; ++s) {
@@ -1501,17 +1516,61 @@ struct Engine final : llg_ctx {
     }
   }
 
+  // replay step *step_base of a reverse block: every instance advances the
+  // state in dp_mrev by its recorded step (or idles with h = 0) through the
+  // six stages; the new state goes to dp_mrev and to segment slot j + 1
+  void dp_replay_step() {
+    const long long S = (long long)slot();
+    auto Yrec = [&](int s) { return dp_recY + (long long)(s - 1) * S; };
+    launch_dp_replay_state(n, dp_sched, step_base, dp_k0, dp_khi, dp_hst, st);
+    ++nlaunch;
+    fft_only(dp_mrev);
+    for (int s = 1; s <= 6; ++s) {
+      cols();
+      RowArgs<T> a = dp_args(s);
+      a.Yin = s == 1 ? dp_mrev : Yrec(s);
+      a.m = dp_mrev;
+      a.Yout = s < 6 ? Yrec(s + 1) : dp_y5;
+      rows(a, ROW_DP_STAGE);
+    }
+    launch_dp_push<T>(dI, dRT, (int)rt.size(), dp_y5, dp_seg, S, step_base, dp_mrev, st);
+    ++nlaunch;
+  }
+
   // reverse sweep over the accepted steps: per reverse index r, instance i
   // reverses its step cnt_i - 1 - r (or idles with h = 0): recompute the six
-  // stages from its checkpoint, seed kappa_6 = h b_6 lambda, then adjoint
-  // stages 6..1 (eta_s kept for the lower stages, lambda += sum eta at 1)
+  // stages from its state, seed kappa_6 = h b_6 lambda, then adjoint stages
+  // 6..1 (eta_s kept for the lower stages, lambda += sum eta at 1).  With
+  // periodic checkpoints the reverse indices go in blocks of dp_K: each block
+  // first replays, per instance, the steps from the checkpoint at or before
+  // its window to the window's end (at most 2 dp_K - 1 steps).
   llg_status adjoint_dp(const double* dw, void* dphi, void* dm0) {
     cudaEventRecord(ev0, st);
     long long Kmax = 0;
     for (int i = 0; i < n; ++i) Kmax = std::max(Kmax, (long long)dp_cnt_h[i]);
-    for (long long r = 0; r < Kmax; ++r) {
-      set_step(r);
-      if (llg_status st2 = run_segment(SEG_DP_REVERSE, 1)) return st2;
+    for (long long b = 0; b * dp_K < Kmax; ++b) {
+      if (dp_K > 1) {
+        long long len = 0;   // replay steps this block needs (host copy of the plan)
+        for (int i = 0; i < n; ++i) {
+          const long long hi = (long long)dp_cnt_h[i] - 1 - b * dp_K;
+          if (hi < 0) continue;
+          const long long lo = std::max(0LL, (long long)dp_cnt_h[i] - (b + 1) * dp_K);
+          len = std::max(len, hi - (lo / dp_K) * dp_K);
+        }
+        launch_dp_replay_plan(n, dp_cnt, b, dp_K, dp_k0, dp_khi, dp_ckslot, st);
+        launch_dp_gather<T>(dI, dRT, (int)rt.size(), dp_ck, (long long)slot(), dp_ckslot, dp_mrev, st);
+        set_step(-1);
+        launch_dp_push<T>(dI, dRT, (int)rt.size(), dp_mrev, dp_seg, (long long)slot(), step_base, dp_mrev, st);
+        nlaunch += 3;
+        for (long long j = 0; j < len; ++j) {
+          set_step(j);
+          if (llg_status st2 = run_segment(SEG_DP_REPLAY, 1)) return st2;
+        }
+      }
+      for (long long r = b * dp_K; r < std::min(Kmax, (b + 1) * dp_K); ++r) {
+        set_step(r);
+        if (llg_status st2 = run_segment(SEG_DP_REVERSE, 1)) return st2;
+      }
     }
     launch_grad_finish_tiles<T>(dI, dRT, (int)rt.size(), dpsi, psib, psic, dw, static_cast<T*>(dphi), lam,
                                 static_cast<T*>(dm0), st);

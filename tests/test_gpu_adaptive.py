@@ -3,7 +3,8 @@ FP64 oracle: in FP64 the step schedule, m_T, J, dJ/dPhi and dJ/dm0 follow
 the oracle's own step control; in FP32 the oracle replays the GPU's accepted
 steps and the gradient over that schedule is compared.  Films of both
 column-kernel families and a 3D grid, a batch of uneven instances against
-single runs, and the argument checks."""
+single runs, periodic checkpoints with schedule replay against one
+checkpoint per accepted step, and the argument checks."""
 import numpy as np
 import pytest
 
@@ -121,3 +122,30 @@ def test_checkpoint_slots_cap_the_accepted_steps():
             s.forward(s.pack_scalar([inst.phi]), s.pack_vector([inst.m0]))
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_periodic_checkpoints_replay_the_accepted_steps(precision):
+    """Periodic checkpoints (m every K = ceil(sqrt(seg_len)) accepted steps,
+    each reverse block replaying the recorded steps) give bit-identical J and
+    gradients to one checkpoint per accepted step, on a batch whose instances
+    accept different numbers of steps, and hold fewer states."""
+    insts = [_case(12, 8, seed=57, N=80), _case(16, 12, seed=58, N=80), _case(8, 6, 2, seed=59, N=80)]
+    ref = _gpu(insts, precision, ckpt="store_all")
+    counts = [len(x[1]) for x in ref["sched"]]
+    assert len(set(counts)) > 1 and max(counts) > 9
+    for seg in (0, max(counts), 2 * max(counts)):      # seg_len caps the accepted steps; K = ceil(sqrt(.))
+        per = _gpu(insts, precision, ckpt="periodic", seg_len=seg)
+        np.testing.assert_array_equal(per["J"], ref["J"])
+        for k in range(len(insts)):
+            np.testing.assert_array_equal(per["sched"][k][1], ref["sched"][k][1])
+            np.testing.assert_array_equal(per["dphi"][k], ref["dphi"][k])
+            np.testing.assert_array_equal(per["dm0"][k], ref["dm0"][k])
+    big = [_case(12, 8, seed=57, N=400)]
+    s_all = gpu_solver(big, precision, integrator="dopri5", rtol=RTOL, atol=ATOL, ckpt="store_all")
+    s_per = gpu_solver(big, precision, integrator="dopri5", rtol=RTOL, atol=ATOL, ckpt="periodic")
+    try:
+        assert s_per.query()[0] < s_all.query()[0]
+    finally:
+        s_all.close()
+        s_per.close()
