@@ -55,6 +55,32 @@ template <typename C> __host__ __device__ __forceinline__ C cscale(C a, decltype
 template <typename C> __host__ __device__ __forceinline__ C mul_mi(C a) { return mk<C>(a.y, -a.x); }
 template <typename C> __host__ __device__ __forceinline__ C mul_pi(C a) { return mk<C>(-a.y, a.x); }
 
+// FP32 complex sums and real scalings as packed FP32x2 operations (one
+// instruction for both parts on sm_100 and later; the same round-to-nearest
+// result per part as two scalar operations).  Declared before the FFT
+// templates so that their calls on float2 resolve here.
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  return __fadd2_rn(a, b);
+#else
+  return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+#else
+  return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  return __fmul2_rn(a, make_float2(s, s));
+#else
+  return make_float2(a.x * s, a.y * s);
+#endif
+}
+
 // Block-wide sum of a double; result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
