@@ -42,6 +42,21 @@ import workloads as W  # noqa: E402
 METRIC = "LLG fwd+adjoint node-steps/s, FP32 batched vs FP64 plain on GB300; % HBM roofline"
 UNIT = "node-steps/s"
 
+# The workloads a timed step can run: instances for N RK4 steps, the adjoint
+# spectrum that meets the gradient bar on them (double-float on the
+# demultiplexer shapes; the nanoparticle meets it in FP32; 3D grids have no
+# double-float spectrum), and a description.
+WORKLOADS = {
+    "batch64": (lambda n: W.batch64(nsteps=n), "dfloat",
+                "batch64: 8 candidates x {128x64,256x64,256x128,512x128} x 2 frequencies (3.0/3.4 GHz), "
+                "YIG demultiplexer, 5 nm cells"),
+    "particle64": (lambda n: [W.particle64(nsteps=n)], "working", "particle64: 64x64 Permalloy nanoparticle, 2 nm"),
+    "demux256": (lambda n: [W.demux256(0, nsteps=n), W.demux256(1, nsteps=n)], "dfloat",
+                 "demux256: 256x64 YIG demultiplexer at 3.0 and 3.4 GHz, 5 nm"),
+    "thick512": (lambda n: [W.thick512(nsteps=n)], "working", "thick512: 512x512x4 YIG film, 3D demag"),
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -50,6 +65,9 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--nsteps", type=int, default=10000, help="RK4 steps per instance")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 and CPU legs")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="batch64",
+                    help="the timed level-set iteration's workload (batch64: the benchmark; the others for "
+                         "profiling and comparison runs)")
     return ap.parse_args()
 
 
@@ -484,9 +502,9 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    SPEC = "dfloat"
-    insts = W.batch64(nsteps=args.nsteps)
-    nodes = sum(i.problem.nx * i.problem.ny for i in insts)
+    make, SPEC, wdesc = WORKLOADS[args.workload]
+    insts = make(args.nsteps)
+    nodes = sum(i.problem.nx * i.problem.ny * i.problem.nz for i in insts)
     node_steps = nodes * args.nsteps
     stream = torch.cuda.current_stream()
     s = Solver([i.problem for i in insts], precision="fp32", ckpt="periodic", use_graph=True, stream=stream,
@@ -571,14 +589,14 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch64: 8 candidates x {128x64,256x64,256x128,512x128} x 2 frequencies "
-                                   "(3.0/3.4 GHz), YIG demultiplexer, 5 nm cells",
+            "config": {"workload": wdesc,
                        "instances": len(insts), "nodes": nodes, "rk4_steps": args.nsteps,
                        "checkpoint": "periodic, K = ceil(sqrt(N))", "precision": "fp32",
-                       "adjoint_spectrum": "double-float (hi + lo FP32 pairs) for the adjoint's demag transpose; "
-                                           "node arrays FP32",
-                       "parity": "dJ/dPhi within 1e-4 of the FP64 oracle on all four shapes (measured <= 2.7e-6 "
-                                 "at 100 steps, tests/test_gpu_fullsize.py)",
+                       "adjoint_spectrum": ("double-float (hi + lo FP32 pairs) for the adjoint's demag transpose; "
+                                            "node arrays FP32") if SPEC == "dfloat" else "FP32",
+                       "parity": ("dJ/dPhi within 1e-4 of the FP64 oracle on all four shapes (measured <= 2.7e-6 "
+                                  "at 100 steps, tests/test_gpu_fullsize.py)") if args.workload == "batch64" else
+                                 "see tests/test_gpu_fullsize.py for this workload's parity",
                        "launch": launch, "launch_tuning_ms": tune_ms,
                        "step": "forward + checkpointed adjoint + level-set update, each timed step "
                                "repeated from the same phi (CUDA-graph replays of every segment)",
@@ -592,7 +610,7 @@ def run_ours(args):
                         for v in kern.values()},
             "peak_mem_bytes": int(mem_bytes)}
 
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and not args.no_extras and args.workload == "batch64":
         # e2e: the same step through the public API with host buffers
         phi_h = phi0.cpu().pin_memory()
         m0_h = m0.cpu().pin_memory()
