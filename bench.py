@@ -89,8 +89,8 @@ def measured_peaks():
 
 
 # the sources the FP32 stage, column and adjoint kernels are compiled from
-KERNEL_SOURCES = ("common.cuh", "kernels.cuh", "kernels_impl.cuh", "regfft.cuh", "tma.cuh", "cols16.cuh",
-                  "k_stage_f32.cu", "k_cols_f32.cu", "k_cols16_f32.cu", "k_adj_f32.cu")
+KERNEL_SOURCES = ("common.cuh", "dfloat.cuh", "kernels.cuh", "kernels_impl.cuh", "regfft.cuh", "tma.cuh", "cols16.cuh",
+                  "k_stage_f32.cu", "k_cols_f32.cu", "k_cols16_f32.cu", "k_adj_f32.cu", "k_adj_df.cu", "k_cols_df.cu")
 
 
 def kernel_source_hash():
@@ -103,16 +103,17 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(family):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def ncu_traffic(family, spec):
+    """DRAM bytes per whole-batch launch of a kernel family in the given
+    adjoint-spectrum configuration, from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
         if d.get("source_hash") != kernel_source_hash():
             return None
-        e = d["families"].get(str(family))
+        e = d["families"].get(f"{spec}:{family}")
         return None if e is None else float(e["dram_bytes_per_full_launch"])
     except Exception:
         return None
@@ -435,7 +436,7 @@ def roofline_of(kern, spec, hbm, peak_kind, sm_mhz, nodes, timing_note):
         # operations), against the FP32 lanes x clock of the device
         peak = SMS * FP32_LANES_PER_SM * (sm_mhz or 2070.0) * 1e6 / 1e12
         return {"bound": "alu", "achieved": k["achieved_tops"], "peak": peak, "unit": "TFLOP/s",
-                "frac": k["achieved_tops"] / peak, "traffic": None, "kernel": name,
+                "frac": k["achieved_tops"] / peak, "traffic": ncu_traffic(dom, spec), "kernel": name,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x the median SM clock under load, one FP32 "
                                "add/multiply/FMA per lane per clock (FP32 operations, an FMA counted once)",
                 "ops_per_launch": k["fp32_ops_per_launch"],
@@ -445,7 +446,7 @@ def roofline_of(kern, spec, hbm, peak_kind, sm_mhz, nodes, timing_note):
                 "kernel_timing": timing_note}
     bpn = k["bytes_per_node"]
     return {"bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-            "frac": k["achieved_gbs"] / hbm, "traffic": ncu_traffic(dom) if spec != "dfloat" else None,
+            "frac": k["achieved_gbs"] / hbm, "traffic": ncu_traffic(dom, spec),
             "kernel": name, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
             "bytes_per_node": bpn, "nodes_per_launch": nodes, "kernel_timing": timing_note}
 
