@@ -427,16 +427,20 @@ def kernel_families(sk, step_fn, insts, nodes, spec, split):
     return kern
 
 
-def roofline_of(kern, spec, hbm, peak_kind, sm_mhz, nodes, timing_note):
+def roofline_of(kern, spec, hbm, peak_kind, sm_mhz, nodes, timing_note, with_traffic=True):
+    """Roofline of the kernel with the largest total time.  `traffic` is the
+    ncu DRAM capture of that kernel on the benchmarked batch; other workloads
+    (with_traffic=False) report null, as no capture covers them."""
     dom = max(kern, key=lambda f: kern[f]["total_ms"])
     k = kern[dom]
     name = k["kernel"]
+    traffic = ncu_traffic(dom, spec) if with_traffic else None
     if k["kind"] == "df":
         # double-float kernels: bound by FP32 arithmetic (the compensated
         # operations), against the FP32 lanes x clock of the device
         peak = SMS * FP32_LANES_PER_SM * (sm_mhz or 2070.0) * 1e6 / 1e12
         return {"bound": "alu", "achieved": k["achieved_tops"], "peak": peak, "unit": "TFLOP/s",
-                "frac": k["achieved_tops"] / peak, "traffic": ncu_traffic(dom, spec), "kernel": name,
+                "frac": k["achieved_tops"] / peak, "traffic": traffic, "kernel": name,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x the median SM clock under load, one FP32 "
                                "add/multiply/FMA per lane per clock (FP32 operations, an FMA counted once)",
                 "ops_per_launch": k["fp32_ops_per_launch"],
@@ -446,16 +450,17 @@ def roofline_of(kern, spec, hbm, peak_kind, sm_mhz, nodes, timing_note):
                 "kernel_timing": timing_note}
     bpn = k["bytes_per_node"]
     return {"bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-            "frac": k["achieved_gbs"] / hbm, "traffic": ncu_traffic(dom, spec),
+            "frac": k["achieved_gbs"] / hbm, "traffic": traffic,
             "kernel": name, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
             "bytes_per_node": bpn, "nodes_per_launch": nodes, "kernel_timing": timing_note}
 
 
 def time_workload(insts, nsteps, precision="fp32", ckpt="periodic", spec="working", reps=1, stream=None,
-                  kernel_steps=None):
+                  kinsts=None):
     """Forward and forward+adjoint node-steps/s of one workload (CUDA graphs,
-    measured launch configuration), its device memory, and optionally the
-    per-kernel roofline from a second pass at `kernel_steps` RK4 steps."""
+    measured launch configuration), its device memory, and, given `kinsts`
+    (the same instances at fewer RK4 steps), the dominant kernel's roofline
+    from a pass with CUDA events around every launch."""
     import torch
     from paper_2411_19109_gb300 import Solver
     nodes = sum(i.problem.nx * i.problem.ny * i.problem.nz for i in insts)
@@ -479,11 +484,33 @@ def time_workload(insts, nsteps, precision="fp32", ckpt="periodic", spec="workin
             tf += e[0].elapsed_time(e[1])
             ta += e[1].elapsed_time(e[2])
         ns = nodes * nsteps * reps
+        cfg = s.launch_config()[0]
         out = {"forward": ns / (tf / 1e3), "forward_adjoint": ns / ((tf + ta) / 1e3), "unit": UNIT,
                "ms_forward": tf / reps, "ms_adjoint": ta / reps, "device_bytes": int(s.query()[0]),
-               "launch": s.launch_config()[0], "nodes": nodes, "rk4_steps": nsteps, "instances": len(insts)}
+               "launch": cfg, "nodes": nodes, "rk4_steps": nsteps, "instances": len(insts)}
     finally:
         s.close()
+    if kinsts is not None:
+        sk = Solver([i.problem for i in kinsts], precision=precision, ckpt=ckpt, use_graph=False, stream=stream,
+                    adj_spectral=spec, tune="given", launch=cfg, time_kernels=True)
+        try:
+            def one(sv):
+                sv.forward(phi, m0)
+                sv.adjoint()
+            one(sk)
+            kern = kernel_families(sk, one, kinsts, nodes, spec, bool(cfg.get("adj_split")))
+        finally:
+            sk.close()
+        if 1 in kern:       # which column kernel family 1 ran on these grids
+            kern[1]["kernel"] = ("cols3_kernel<float> (3D column pass)" if any(i.problem.nz > 1 for i in insts) else
+                                 "cols16_kernel<float> (16-element lanes)" if cfg.get("col_lanes") == 16 else
+                                 "cols_kernel<float> (8-element lanes)")
+        hbm, peak_kind = measured_peaks()
+        out["roofline"] = roofline_of(kern, spec, hbm, peak_kind, None, nodes, with_traffic=False, timing_note=
+                                      f"CUDA events around every launch, a forward + adjoint of "
+                                      f"{kinsts[0].problem.nsteps} RK4 steps without graphs")
+        out["kernels"] = {v["kernel"].split(" ")[0]: {kk: vv for kk, vv in v.items() if kk != "kernel"}
+                          for v in kern.values()}
     return out
 
 
@@ -765,7 +792,7 @@ def other_workloads(stream):
     # config 2: 64 x 64 nanoparticle, 5000 steps, energy + area objective
     # (its FP32 gradient meets 1e-4 with the FP32 adjoint spectrum)
     c2 = [W.particle64(nsteps=5000)]
-    r = time_workload(c2, 5000, spec="working", stream=stream)
+    r = time_workload(c2, 5000, spec="working", stream=stream, kinsts=[W.particle64(nsteps=200)])
     r64 = time_workload(c2, 5000, precision="fp64", ckpt="store_all", stream=stream)
     r["fp64_store_all"] = {"forward_adjoint": r64["forward_adjoint"], "device_bytes": r64["device_bytes"],
                            "steps": 5000}
@@ -774,7 +801,8 @@ def other_workloads(stream):
     # config 3: 256 x 64 demultiplexer, 3.0 and 3.4 GHz runs of one design,
     # 20,000 steps, double-float adjoint spectrum (its gradient parity case)
     c3 = [W.demux256(0, nsteps=20000), W.demux256(1, nsteps=20000)]
-    r = time_workload(c3, 20000, spec="dfloat", stream=stream)
+    r = time_workload(c3, 20000, spec="dfloat", stream=stream,
+                      kinsts=[W.demux256(0, nsteps=200), W.demux256(1, nsteps=200)])
     n64 = 2000
     c3s = [W.demux256(0, nsteps=n64), W.demux256(1, nsteps=n64)]
     r64 = time_workload(c3s, n64, precision="fp64", ckpt="store_all", stream=stream)
@@ -789,7 +817,7 @@ def other_workloads(stream):
     # (50,001 states of 3 x 1,048,576 doubles) does not fit the device
     n5 = 1000
     c5 = [W.thick512(nsteps=n5)]
-    r = time_workload(c5, n5, spec="working", stream=stream)
+    r = time_workload(c5, n5, spec="working", stream=stream, kinsts=[W.thick512(nsteps=50)])
     nn = 512 * 512 * 4
     r["projected_50000"] = {"seconds_forward_adjoint": nn * 50000 / r["forward_adjoint"],
                             "fp64_store_all_bytes": int(50001 * 3 * nn * 8)}

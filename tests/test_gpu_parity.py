@@ -277,3 +277,37 @@ def test_state_records_match_stage_records(precision):
                 np.testing.assert_array_equal(g["dm0"][k], ref["dm0"][k])
         if ckpt == "periodic" and seg == 23:
             assert g["bytes"] < ref["bytes"]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-5)])
+@pytest.mark.parametrize("cells,h", [((64, 16), (3e-9, 4e-9, 2.5e-9)), ((48, 8), (5e-9, 5e-9, 5e-9))])
+def test_film_mean_demag_field_is_the_prism_factor(cells, h, precision, tol):
+    """A check of the GPU-built demag tensor independent of the oracle: the
+    uniformly magnetised film (psi = 1) of 64 x 16 or 48 x 8 cells -- long
+    enough that the tensor's far-field branch carries a share of the sum --
+    has node-averaged demag field -mu0 Ms N_axis m, with N Aharoni's closed
+    form for the prism along each axis (the Newell tensor is the exact
+    cell-pair average)."""
+    from tests.test_oracle_demag import aharoni_factor
+    nx, ny = cells
+    dx, dy, dz = h
+    base = W.random_small(nx, ny, 1, seed=7)
+    p = base.problem.replace(dx=dx, dy=dy, dz=dz)
+    phi = np.ones((1, ny, nx))
+    a, b, c = nx * dx / 2, ny * dy / 2, dz / 2
+    factors = [aharoni_factor(b, c, a), aharoni_factor(c, a, b), aharoni_factor(a, b, c)]
+    for axis in range(3):
+        m = np.zeros((3, 1, ny, nx))
+        m[axis] = 1.0
+        inst = W.Instance(p, phi, m, base.mask, "uniform")
+        s = gpu_solver([inst], precision)
+        try:
+            B = s.unpack_vector(s.field(s.pack_scalar([phi]), s.pack_vector([m]), 0.0, demag_only=True))[0]
+            Bm = B.double().cpu().numpy()
+        finally:
+            s.close()
+        expect = -4e-7 * np.pi * p.Ms * factors[axis]
+        assert abs(Bm[axis].mean() - expect) <= tol * abs(expect)
+        for k in range(3):
+            if k != axis:
+                assert abs(Bm[k].mean()) <= tol * abs(expect)
