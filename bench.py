@@ -427,6 +427,14 @@ def kernel_families(sk, step_fn, insts, nodes, spec, split):
     return kern
 
 
+def name_column_family(kern, insts, cfg):
+    """Name the FP32 column kernel that family 1 ran on these grids."""
+    if 1 in kern:
+        kern[1]["kernel"] = ("cols3_kernel<float> (3D column pass)" if any(i.problem.nz > 1 for i in insts) else
+                             "cols16_kernel<float> (16-element lanes)" if cfg.get("col_lanes") == 16 else
+                             "cols_kernel<float> (8-element lanes)")
+
+
 def roofline_of(kern, spec, hbm, peak_kind, sm_mhz, nodes, timing_note, with_traffic=True):
     """Roofline of the kernel with the largest total time.  `traffic` is the
     ncu DRAM capture of that kernel on the benchmarked batch; other workloads
@@ -501,10 +509,7 @@ def time_workload(insts, nsteps, precision="fp32", ckpt="periodic", spec="workin
             kern = kernel_families(sk, one, kinsts, nodes, spec, bool(cfg.get("adj_split")))
         finally:
             sk.close()
-        if 1 in kern:       # which column kernel family 1 ran on these grids
-            kern[1]["kernel"] = ("cols3_kernel<float> (3D column pass)" if any(i.problem.nz > 1 for i in insts) else
-                                 "cols16_kernel<float> (16-element lanes)" if cfg.get("col_lanes") == 16 else
-                                 "cols_kernel<float> (8-element lanes)")
+        name_column_family(kern, insts, cfg)
         hbm, peak_kind = measured_peaks()
         out["roofline"] = roofline_of(kern, spec, hbm, peak_kind, None, nodes, with_traffic=False, timing_note=
                                       f"CUDA events around every launch, a forward + adjoint of "
@@ -608,10 +613,13 @@ def run_ours(args):
                 use_graph=False, stream=stream, adj_spectral=SPEC, tune="given", launch=launch)
     kern = kernel_families(sk, lambda sv: step(lr, sv), insts, nodes, SPEC, bool(launch.get("adj_split")))
     sk.close()
+    if args.workload != "batch64":
+        name_column_family(kern, insts, launch)
     hbm, peak_kind = measured_peaks()
     roofline = roofline_of(kern, SPEC, hbm, peak_kind, csum.get("sm_mhz"), nodes,
                            "CUDA events around every launch on the solver stream, over one more step of the "
-                           "same workload and launch configuration without graphs")
+                           "same workload and launch configuration without graphs",
+                           with_traffic=args.workload == "batch64")
 
     mem_bytes, _ = s.query()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -42,6 +42,28 @@ __device__ __forceinline__ void load_tensor6(const double* tab, long long rec, d
 // value, 1: its real part only, 2: its imaginary part only); rec0 is the
 // table record of (kz = 0, kx, |ky|), kzrec the record stride between kz
 // planes; sy = -1 when ky is a mirrored (negative) frequency.
+//
+// The frequencies kz and -kz are taken together.  With w_z = W^{z kz} =
+// c_z + i s_z, A = sum_z M_z c_z and B = sum_z M_z s_z give Mhat(+-kz) =
+// A +- iB.  The table holds N(kz) for 0 <= kz <= PZ/2; N(-kz) differs from it
+// only in the sign of the xz and yz components, so N = Ne +- No with No
+// those two.  Then h(+-kz) = (Ne A + No iB) +- (Ne iB + No A) =: S +- D, and
+// the pair's share of the inverse transform is
+//   h(kz) conj(w_z) + h(-kz) w_z = 2 c_z S - 2 i s_z D.
+// kz = 0 and kz = PZ/2 have real w_z = +-1 and enter once.  One tensor
+// record and one pass over the layers per pair: half the work of taking
+// the PZ frequencies one by one.
+template <typename T>
+__device__ __forceinline__ void tensor_apply(const T n[6], T sy, const cplx<T> (&a)[3], const cplx<T> (&b)[3],
+                                             cplx<T> (&h)[3]) {
+  // h = Ne a + No b; Ne: xx, yy, zz, sy xy; No: xz, sy yz
+  using C = cplx<T>;
+  const T nxy = sy * n[3], nxz = n[4], nyz = sy * n[5];
+  h[0] = mk<C>(n[0] * a[0].x + nxy * a[1].x + nxz * b[2].x, n[0] * a[0].y + nxy * a[1].y + nxz * b[2].y);
+  h[1] = mk<C>(nxy * a[0].x + n[1] * a[1].x + nyz * b[2].x, nxy * a[0].y + n[1] * a[1].y + nyz * b[2].y);
+  h[2] = mk<C>(n[2] * a[2].x + nxz * b[0].x + nyz * b[1].x, n[2] * a[2].y + nxz * b[0].y + nyz * b[1].y);
+}
+
 template <typename T, int PZ>
 __device__ __forceinline__ void zconv(const cplx<T>* src, int cstr, int zstr, int part, cplx<T> (&out)[3][PZ / 2],
                                       int nz, const cplx<T>* __restrict__ wz, const T* __restrict__ tab,
@@ -53,8 +75,12 @@ __device__ __forceinline__ void zconv(const cplx<T>* src, int cstr, int zstr, in
 #pragma unroll
     for (int z = 0; z < NZM; ++z) out[c][z] = mk<C>((T)0, (T)0);
 #pragma unroll 1
-  for (int kz = 0; kz < PZ; ++kz) {
-    C mh[3] = {mk<C>((T)0, (T)0), mk<C>((T)0, (T)0), mk<C>((T)0, (T)0)};
+  for (int kz = 0; kz <= NZM; ++kz) {
+    T n[6];
+    load_tensor6(tab, rec0 + (long long)kz * kzrec, n);
+    C A[3], B[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A[c] = B[c] = mk<C>((T)0, (T)0);
 #pragma unroll
     for (int z = 0; z < NZM; ++z) {
       if (z >= nz) break;
@@ -64,24 +90,36 @@ __device__ __forceinline__ void zconv(const cplx<T>* src, int cstr, int zstr, in
         C m = src[c * cstr + z * zstr];
         if (part == 1) m.y = (T)0;
         else if (part == 2) m = mk<C>(m.y, (T)0);
-        mh[c] = cadd(mh[c], cmul(m, w));
+        A[c] = mk<C>(A[c].x + m.x * w.x, A[c].y + m.y * w.x);
+        B[c] = mk<C>(B[c].x + m.x * w.y, B[c].y + m.y * w.y);
       }
     }
-    const bool lo = kz <= PZ / 2;
-    const T sz = lo ? (T)1 : (T)-1;
-    T n[6];
-    load_tensor6(tab, rec0 + (long long)(lo ? kz : PZ - kz) * kzrec, n);
-    const T nxy = sy * n[3], nxz = sz * n[4], nyz = sy * sz * n[5];
-    C h[3];
-    h[0] = cadd(cadd(cscale(mh[0], n[0]), cscale(mh[1], nxy)), cscale(mh[2], nxz));
-    h[1] = cadd(cadd(cscale(mh[0], nxy), cscale(mh[1], n[1])), cscale(mh[2], nyz));
-    h[2] = cadd(cadd(cscale(mh[0], nxz), cscale(mh[1], nyz)), cscale(mh[2], n[2]));
+    if (kz == 0 || kz == NZM) {
+      // w_z = +-1: Mhat = A, h = (Ne + No) A
+      C h[3];
+      tensor_apply(n, sy, A, A, h);
 #pragma unroll
-    for (int z = 0; z < NZM; ++z) {
-      if (z >= nz) break;
-      const C w = cconj(wz[(z * kz) & (PZ - 1)]);
+      for (int z = 0; z < NZM; ++z) {
+        if (z >= nz) break;
+        const T wr = ((z * kz) & (PZ - 1)) ? (T)-1 : (T)1;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) out[c][z] = cadd(out[c][z], cmul(h[c], w));
+        for (int c = 0; c < 3; ++c) out[c][z] = mk<C>(out[c][z].x + wr * h[c].x, out[c][z].y + wr * h[c].y);
+      }
+    } else {
+      C iB[3], S[3], D[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) iB[c] = mk<C>(-B[c].y, B[c].x);
+      tensor_apply(n, sy, A, iB, S);
+      tensor_apply(n, sy, iB, A, D);
+#pragma unroll
+      for (int z = 0; z < NZM; ++z) {
+        if (z >= nz) break;
+        const C w = wz[(z * kz) & (PZ - 1)];
+        const T c2 = w.x + w.x, s2 = w.y + w.y;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          out[c][z] = mk<C>(out[c][z].x + c2 * S[c].x + s2 * D[c].y, out[c][z].y + c2 * S[c].y - s2 * D[c].x);
+      }
     }
   }
 }
@@ -92,7 +130,7 @@ __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I
   using C = cplx<T>;
   constexpr int TT = L / 8;
   constexpr int NG = kColThreads / TT;             // FFT groups working at once
-  constexpr int GSC = rf_padded_len(L) + 1;
+  constexpr int GSC = cols3_stride(L);
   constexpr int NZM = PZ / 2;
   const int tid = threadIdx.x;
   const int nz = I.nz, ny = I.ny, Lx = I.Lx;
@@ -109,7 +147,7 @@ __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I
     const int r3 = e / ncols;
     const int c = r3 % 3, r = r3 / 3;             // r = z ny + y
     const int y = r % ny, z = r / ny;
-    smem[((c * nz + z) * ncols + col) * GSC + rf_pad(y)] = spec[((long long)r * 3 + c) * Lx + col];
+    smem[((c * nz + z) * ncols + col) * GSC + row_pad(L, y)] = spec[((long long)r * 3 + c) * Lx + col];
   }
   __syncthreads();
   const int t = tid % TT, gid = tid / TT;
@@ -123,12 +161,12 @@ __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
         const int y = t + TT * s;
-        v[s] = (s < 4 && y < ny) ? grp[rf_pad(y)] : mk<C>((T)0, (T)0);   // zero padding: s >= 4
+        v[s] = (s < 4 && y < ny) ? grp[row_pad(L, y)] : mk<C>((T)0, (T)0);   // zero padding: s >= 4
       }
       gs();
       fft1<C, L, -1>(v, grp, 1, t, tw1, 1, gs);
 #pragma unroll
-      for (int s = 0; s < 8; ++s) grp[rf_pad(t + TT * s)] = v[s];
+      for (int s = 0; s < 8; ++s) grp[row_pad(L, t + TT * s)] = v[s];
     }
   }
   __syncthreads();
@@ -145,10 +183,10 @@ __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I
     for (int e = tid; e < 3 * nz * (L / 2 - 1); e += kColThreads) {
       const int ky = 1 + e % (L / 2 - 1), cz = e / (L / 2 - 1);
       C* sq = smem + (long long)cz * zstr;        // (c, z) sequence of column 0
-      const C zp = sq[rf_pad(ky)], zm = cconj(sq[rf_pad(L - ky)]);
+      const C zp = sq[row_pad(L, ky)], zm = cconj(sq[row_pad(L, L - ky)]);
       const C s = cadd(zp, zm), d = csub(zp, zm);
-      sq[rf_pad(ky)] = mk<C>((T)0.5 * s.x, (T)0.5 * s.y);             // D(ky)
-      sq[rf_pad(L - ky)] = mk<C>((T)0.5 * d.y, (T)-0.5 * d.x);        // Q(ky) = d / (2i)
+      sq[row_pad(L, ky)] = mk<C>((T)0.5 * s.x, (T)0.5 * s.y);             // D(ky)
+      sq[row_pad(L, L - ky)] = mk<C>((T)0.5 * d.y, (T)-0.5 * d.x);        // Q(ky) = d / (2i)
     }
     __syncthreads();
   }
@@ -160,37 +198,37 @@ __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I
     C out[3][NZM];
     C* base = smem + (long long)col * GSC;
     if (kx != 0) {
-      zconv<T, PZ>(base + rf_pad(ky), cstr, zstr, 0, out, nz, wz, tab, (long long)kx * nky + kyf, kzrec,
+      zconv<T, PZ>(base + row_pad(L, ky), cstr, zstr, 0, out, nz, wz, tab, (long long)kx * nky + kyf, kzrec,
                    lo ? (T)1 : (T)-1);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int z = 0; z < NZM; ++z)
-          if (z < nz) base[c * cstr + z * zstr + rf_pad(ky)] = out[c][z];
+          if (z < nz) base[c * cstr + z * zstr + row_pad(L, ky)] = out[c][z];
     } else if (ky == 0 || ky == L / 2) {
       // D and Q real: HD with the kx = 0 tensor, HQ with the kx = Px/2 one
       C hq[3][NZM];
-      zconv<T, PZ>(base + rf_pad(ky), cstr, zstr, 1, out, nz, wz, tab, (long long)ky, kzrec, (T)1);
-      zconv<T, PZ>(base + rf_pad(ky), cstr, zstr, 2, hq, nz, wz, tab, (long long)Lx * nky + ky, kzrec, (T)1);
+      zconv<T, PZ>(base + row_pad(L, ky), cstr, zstr, 1, out, nz, wz, tab, (long long)ky, kzrec, (T)1);
+      zconv<T, PZ>(base + row_pad(L, ky), cstr, zstr, 2, hq, nz, wz, tab, (long long)Lx * nky + ky, kzrec, (T)1);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int z = 0; z < NZM; ++z)
-          if (z < nz) base[c * cstr + z * zstr + rf_pad(ky)] = mk<C>(out[c][z].x, hq[c][z].x);
+          if (z < nz) base[c * cstr + z * zstr + row_pad(L, ky)] = mk<C>(out[c][z].x, hq[c][z].x);
     } else if (lo) {
       // D(ky) in slot ky -> HD(ky); Q(ky) in slot L - ky -> HQ(ky)
-      zconv<T, PZ>(base + rf_pad(ky), cstr, zstr, 0, out, nz, wz, tab, (long long)ky, kzrec, (T)1);
+      zconv<T, PZ>(base + row_pad(L, ky), cstr, zstr, 0, out, nz, wz, tab, (long long)ky, kzrec, (T)1);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int z = 0; z < NZM; ++z)
-          if (z < nz) base[c * cstr + z * zstr + rf_pad(ky)] = out[c][z];
-      zconv<T, PZ>(base + rf_pad(L - ky), cstr, zstr, 0, out, nz, wz, tab, (long long)Lx * nky + ky, kzrec, (T)1);
+          if (z < nz) base[c * cstr + z * zstr + row_pad(L, ky)] = out[c][z];
+      zconv<T, PZ>(base + row_pad(L, L - ky), cstr, zstr, 0, out, nz, wz, tab, (long long)Lx * nky + ky, kzrec, (T)1);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int z = 0; z < NZM; ++z)
-          if (z < nz) base[c * cstr + z * zstr + rf_pad(L - ky)] = out[c][z];
+          if (z < nz) base[c * cstr + z * zstr + row_pad(L, L - ky)] = out[c][z];
     }
   }
   __syncthreads();
@@ -199,9 +237,9 @@ __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I
     for (int e = tid; e < 3 * nz * (L / 2 - 1); e += kColThreads) {
       const int ky = 1 + e % (L / 2 - 1), cz = e / (L / 2 - 1);
       C* sq = smem + (long long)cz * zstr;
-      const C hd = sq[rf_pad(ky)], hq = sq[rf_pad(L - ky)];
-      sq[rf_pad(ky)] = mk<C>(hd.x - hq.y, hd.y + hq.x);
-      sq[rf_pad(L - ky)] = mk<C>(hd.x + hq.y, hq.x - hd.y);
+      const C hd = sq[row_pad(L, ky)], hq = sq[row_pad(L, L - ky)];
+      sq[row_pad(L, ky)] = mk<C>(hd.x - hq.y, hd.y + hq.x);
+      sq[row_pad(L, L - ky)] = mk<C>(hd.x + hq.y, hq.x - hd.y);
     }
     __syncthreads();
   }
@@ -212,13 +250,13 @@ __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I
       C* grp = smem + (long long)q * GSC;
       C v[8];
 #pragma unroll
-      for (int s = 0; s < 8; ++s) v[s] = grp[rf_pad(t + TT * s)];
+      for (int s = 0; s < 8; ++s) v[s] = grp[row_pad(L, t + TT * s)];
       gs();
       fft1<C, L, 1>(v, grp, 1, t, tw1, 1, gs);
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
         const int y = t + TT * s;
-        if (s < 4 && y < ny) grp[rf_pad(y)] = v[s];
+        if (s < 4 && y < ny) grp[row_pad(L, y)] = v[s];
       }
     }
   }
@@ -228,7 +266,7 @@ __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I
     const int r3 = e / ncols;
     const int c = r3 % 3, r = r3 / 3;
     const int y = r % ny, z = r / ny;
-    spec[((long long)r * 3 + c) * Lx + col] = smem[((c * nz + z) * ncols + col) * GSC + rf_pad(y)];
+    spec[((long long)r * 3 + c) * Lx + col] = smem[((c * nz + z) * ncols + col) * GSC + row_pad(L, y)];
   }
 }
 
@@ -243,7 +281,7 @@ __device__ __forceinline__ void cols3_pz(const ColArgs<T>& a, const DevInst& I, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kColThreads) cols3_kernel(ColArgs<T> a) {
+__global__ void __launch_bounds__(kColThreads, sizeof(T) == 4 ? 2 : 1) cols3_kernel(ColArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ DevInst sI;

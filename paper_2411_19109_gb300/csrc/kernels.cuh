@@ -150,11 +150,16 @@ __host__ __device__ constexpr int cols3_per_tile(int Py, int nz, int Lx) {
   return (1024 / (Py * nz)) < 1 ? 1 : ((1024 / (Py * nz)) > Lx ? Lx : 1024 / (Py * nz));
 }
 
-// Dynamic shared memory: 3 nz ncols sequences of (padded Py + 1), W_Py^k for
-// k < Py and W_Pz^k for k < 16.
+// Sequence stride of the 3D column tile: one pad slot per 16 elements from
+// Py = 128 up (the register FFTs' own exchange layout), made odd.
+__host__ __device__ constexpr int cols3_stride(int L) { return row_padded_len(L) | 1; }
+
+// Dynamic shared memory: 3 nz ncols sequences of cols3_stride(Py), W_Py^k
+// for k < Py and W_Pz^k for k < 16.  In FP32 the largest tile (nz Py =
+// 4096) takes 110 KB, so two blocks share an SM.
 template <typename T>
 __host__ __device__ constexpr size_t cols3_smem_bytes(int Py, int nz, int ncols) {
-  return ((size_t)3 * nz * ncols * (rf_padded_len(Py) + 1) + Py + 16) * sizeof(cplx<T>);
+  return ((size_t)3 * nz * ncols * cols3_stride(Py) + Py + 16) * sizeof(cplx<T>);
 }
 
 template <typename T, typename S = T>
