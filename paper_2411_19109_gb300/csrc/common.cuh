@@ -41,6 +41,27 @@ template <> struct Cplx<double> { using type = double2; };
 template <> struct Cplx<dfloat> { using type = dcplx; };
 template <typename T> using cplx = typename Cplx<T>::type;
 
+// Shared-memory layout of a register-FFT sequence by element type.  FP32 and
+// FP64 take row_pad.  The 16-byte double-float elements take one pad slot per
+// 8 at every length: a quarter-warp's 8 lanes then fill the 32 banks once,
+// for the stride-2/4/8 writes of every pass as for natural order.
+template <typename C> struct SeqPad {
+  __host__ __device__ static constexpr int pad(int L, int i) { return row_pad(L, i); }
+  __host__ __device__ static constexpr int len(int L) { return row_padded_len(L); }
+};
+template <> struct SeqPad<dcplx> {
+  __host__ __device__ static constexpr int pad(int, int i) { return i + (i >> 3); }
+  __host__ __device__ static constexpr int len(int L) { return L + (L >> 3); }
+};
+template <typename C> __host__ __device__ constexpr int seq_pad(int L, int i) { return SeqPad<C>::pad(L, i); }
+// Row-family group stride: the padded length rounded up to even (every
+// sequence starts on a 16-byte boundary).
+template <typename C> __host__ __device__ constexpr int seq_group_stride(int L) { return (SeqPad<C>::len(L) + 1) & ~1; }
+// Entries of the per-pass twiddle table that the double-float (rolled)
+// transforms of length L read after their W table: fewer than L.
+template <typename S> __host__ __device__ constexpr int pass_tw_len(int) { return 0; }
+template <> __host__ __device__ constexpr int pass_tw_len<dfloat>(int L) { return L; }
+
 template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
   C r; r.x = a; r.y = b; return r;
 }
@@ -208,7 +229,7 @@ __host__ __device__ constexpr size_t stage_smem_bytes(int L, int nx) {
 template <typename T, typename S = T>
 __host__ __device__ constexpr size_t adj_smem_bytes(int L, int nx) {
   return (size_t)kExch * sizeof(cplx<S>) + (size_t)7 * (rows_per_tile(L) + 2) * nx * sizeof(T) +
-         (size_t)2 * L * sizeof(cplx<S>);
+         (size_t)(2 * L + pass_tw_len<S>(L)) * sizeof(cplx<S>);
 }
 
 

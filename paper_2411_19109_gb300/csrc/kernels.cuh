@@ -197,7 +197,7 @@ template <typename T, typename S>
 void smem_spec_rows(size_t smem);
 template <typename S>
 __host__ __device__ constexpr size_t spec_rows_smem_bytes(int L) {
-  return (size_t)(kExch + 2 * L) * sizeof(cplx<S>);
+  return (size_t)(kExch + 2 * L + pass_tw_len<S>(L)) * sizeof(cplx<S>);
 }
 template <typename T, int MODE>
 void launch_rows_mode(const RowArgs<T>& a, int ntiles, size_t smem, cudaStream_t st, bool z3);

@@ -152,6 +152,21 @@ __host__ __device__ constexpr int group_stride(int L) { return (row_padded_len(L
 // writes the next FFT's input into the same slots.
 // ---------------------------------------------------------------------------
 
+// Twiddles of a row transform: the W_{2L} table tw2 (stride 2), or for the
+// double-float transforms the per-pass table that follows it.
+template <typename C>
+__device__ __forceinline__ const C* row_fft_tw(const C* tw2, int) { return tw2; }
+template <>
+__device__ __forceinline__ const dcplx* row_fft_tw<dcplx>(const dcplx* tw2, int L) { return tw2 + 2 * L; }
+
+// W_{2L} (and, for double-float, the per-pass table after it) into shared
+// memory; the caller synchronises.
+template <typename C, int L>
+__device__ __forceinline__ void load_row_twiddles(C* tw2, const C* __restrict__ tw4096) {
+  load_twiddles(tw2, tw4096, 2 * L);
+  if constexpr (RolledPasses<C>::value) fill_pass_twiddles<C, L>(tw2 + 2 * L, tw4096, threadIdx.x, blockDim.x);
+}
+
 template <typename T, int L>
 __device__ __forceinline__ void row_inverse_comp(cplx<T> (&v)[8], const cplx<T>* __restrict__ X, bool active,
                                                  cplx<T>* grp, int t, const cplx<T>* __restrict__ tw2) {
@@ -161,9 +176,9 @@ __device__ __forceinline__ void row_inverse_comp(cplx<T> (&v)[8], const cplx<T>*
 #pragma unroll
   for (int s = 0; s < 8; ++s) v[s] = active ? unpack_one(X, t + TT * s, L, tw2) : mk<C>((T)0, (T)0);
   gs();
-  fft1<C, L, 1>(v, grp, 1, t, tw2, 2, gs);
+  fft1<C, L, 1>(v, grp, 1, t, row_fft_tw(tw2, L), 2, gs);
 #pragma unroll
-  for (int s = 0; s < 4; ++s) grp[row_pad(L, t + TT * s)] = v[s];
+  for (int s = 0; s < 4; ++s) grp[seq_pad<C>(L, t + TT * s)] = v[s];
 }
 
 // Forward FFT of the node-phase output left in grp (slots j < npairs), packed
@@ -178,26 +193,26 @@ __device__ __forceinline__ void row_forward_comp(cplx<T>* grp, int npairs, cplx<
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int j = t + TT * s;
-    v[s] = (s < 4 && j < npairs) ? grp[row_pad(L, j)] : mk<C>((T)0, (T)0);
+    v[s] = (s < 4 && j < npairs) ? grp[seq_pad<C>(L, j)] : mk<C>((T)0, (T)0);
   }
   gs();
-  fft1<C, L, -1>(v, grp, 1, t, tw2, 2, gs);
+  fft1<C, L, -1>(v, grp, 1, t, row_fft_tw(tw2, L), 2, gs);
 #pragma unroll
-  for (int s = 0; s < 8; ++s) grp[row_pad(L, t + TT * s)] = v[s];
+  for (int s = 0; s < 8; ++s) grp[seq_pad<C>(L, t + TT * s)] = v[s];
   gs();
   if (!active) return;
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int kk = t + TT * s;
-    const C zm = cconj(grp[row_pad(L, (L - kk) & (L - 1))]);
+    const C zm = cconj(grp[seq_pad<C>(L, (L - kk) & (L - 1))]);
     out[kk] = pack_one(v[s], zm, kk, tw2);
   }
 }
 
-// Node x of a row slot's three sequences: complex slot x/2, real (x even) or
-// imaginary (x odd) part.
+// Node x of a row slot's three sequences of real type T: complex slot x/2,
+// real (x even) or imaginary (x odd) part.
 template <typename T, int L>
-__device__ __forceinline__ int node_slot(int x) { return 2 * row_pad(L, x >> 1) + (x & 1); }
+__device__ __forceinline__ int node_slot(int x) { return 2 * seq_pad<cplx<T>>(L, x >> 1) + (x & 1); }
 
 // ---------------------------------------------------------------------------
 // column pass: FFT_y, product with the tensor spectrum, inverse FFT_y.
@@ -275,7 +290,8 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
     bulk_load(stab, tab + (long long)tile.kx0 * nky * 4, rb, bar);
     if (nb) bulk_load(stab + NC * nky * 4, tab + (long long)Lx * nky * 4, nb, bar);
   }
-  load_twiddles(tw1, a.tw, L);
+  if constexpr (RolledPasses<C>::value) fill_pass_twiddles<C, L>(tw1, a.tw, tid, kColThreads);
+  else load_twiddles(tw1, a.tw, L);
   // coalesced load of the tile (ny rows x 3 components x NC column slots,
   // columns fastest) into the groups; the divisors are compile-time
   for (int e = tid; e < ny * 3 * NC; e += kColThreads) {
@@ -935,7 +951,8 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T, S>& a, const DevInst& 
   using C = cplx<S>;
   using G = RowGeom<L>;
   constexpr int RM = G::RM;
-  constexpr int GS = group_stride(L);
+  constexpr int GS = seq_group_stride<C>(L);
+  static_assert(rows_per_tile(L) * 3 * GS <= kExch, "row slots fit the exchange scratch");
   const G g(threadIdx.x);
   const int tid = threadIdx.x;
   const int nr = tile.nrows;
@@ -990,7 +1007,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T, S>& a, const DevInst& 
     mbar_init(&bars[1], 1);
     mbar_fence_init();
   }
-  if (!SPLIT) load_twiddles(tw2, a.tw, 2 * L);
+  if (!SPLIT) load_row_twiddles<C, L>(tw2, a.tw);
   __syncthreads();
   if (tid == 0) {
     unsigned bytes = 0;
@@ -1024,7 +1041,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs<T, S>& a, const DevInst& 
 #pragma unroll 1
   for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
     const long long n0 = zoff + (long long)y * nx + x;
-    const int sl = node_slot<T, L>(x);
+    const int sl = node_slot<S, L>(x);
     // every pointwise value of this node first, so that the load latencies
     // overlap (these arrays are disjoint from the ones this loop writes)
     T lam[3], gg[3], gsum[3], yp[3], bp[3], dx[3];
@@ -1247,7 +1264,8 @@ __device__ __forceinline__ void spec_rows_body(const SpecRowArgs<T, S>& a, const
                                                unsigned char* smem_raw, uint64_t* bar) {
   using C = cplx<S>;
   using G = RowGeom<L>;
-  constexpr int GS = group_stride(L);
+  constexpr int GS = seq_group_stride<C>(L);
+  static_assert(rows_per_tile(L) * 3 * GS <= kExch, "row slots fit the exchange scratch");
   const G g(threadIdx.x);
   const int nr = tile.nrows;
   const bool active = g.rl < nr;
@@ -1266,7 +1284,7 @@ __device__ __forceinline__ void spec_rows_body(const SpecRowArgs<T, S>& a, const
     mbar_init(bar, 1);
     mbar_fence_init();
   }
-  load_twiddles(tw2, a.tw, 2 * L);
+  load_row_twiddles<C, L>(tw2, a.tw);
   __syncthreads();
   if (DIR > 0) {
     if (threadIdx.x == 0) {
@@ -1282,7 +1300,7 @@ __device__ __forceinline__ void spec_rows_body(const SpecRowArgs<T, S>& a, const
 #pragma unroll 1
     for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
       const long long n0 = zoff + (long long)y * nx + x;
-      const int sl = node_slot<T, L>(x);
+      const int sl = node_slot<S, L>(x);
 #pragma unroll
       for (int c = 0; c < 3; ++c) a.out[off3 + c * nodes + n0] = spec_to<T>(sEr[2 * c * GS + sl]);
     }
@@ -1290,7 +1308,7 @@ __device__ __forceinline__ void spec_rows_body(const SpecRowArgs<T, S>& a, const
 #pragma unroll 1
     for (int x = g.tr; active && x < nx; x += 3 * G::TT) {
       const long long n0 = zoff + (long long)y * nx + x;
-      const int sl = node_slot<T, L>(x);
+      const int sl = node_slot<S, L>(x);
 #pragma unroll
       for (int c = 0; c < 3; ++c) sEr[2 * c * GS + sl] = spec_from<S>(a.src[off3 + c * nodes + n0]);
     }

@@ -6,13 +6,15 @@
 // stores of consecutive t are coalesced and no bit reversal is needed).
 // The schedule is Stockham's auto-sort: one radix-2 or radix-4 pass first
 // when m is not a multiple of 3, then radix-8 passes.  Between passes the
-// data goes through shared memory, where index i lives at i + i/8 (one pad
-// slot per eight) to spread the scattered writes over the banks; the last
-// pass leaves its output in registers.
+// data goes through shared memory, where index i lives at seq_pad(L, i) (pad
+// slots spread the scattered writes over the banks); the last pass leaves
+// its output in registers.
 //
 // Twiddles: W_L^m = tw[m * tws] for a table the caller provides (a copy of
 // the FP64-computed W_4096^k table in shared memory, or the global table
-// itself).  DIR = -1 is the forward transform, +1 the unnormalised inverse.
+// itself).  The double-float transforms instead read the per-pass table of
+// fill_pass_twiddles (tws unused).  DIR = -1 is the forward transform, +1 the
+// unnormalised inverse.
 #pragma once
 
 #include "common.cuh"
@@ -129,22 +131,47 @@ __host__ __device__ __forceinline__ void rf_pass(C v[8], int t, int Ns, const C*
   }
 }
 
+__host__ __device__ constexpr int log2_len(int L) {
+  return (L == 8) ? 3 : (L == 16) ? 4 : (L == 32) ? 5 : (L == 64) ? 6 : (L == 128) ? 7 : (L == 256) ? 8
+       : (L == 512) ? 9 : (L == 1024) ? 10 : 11;
+}
+// log2 of the stage size after the first pass of a length-L transform.
+__host__ __device__ constexpr int first_pass_lns(int L) { return log2_len(L) % 3 == 1 ? 1 : (log2_len(L) % 3 == 2 ? 2 : 3); }
+
+// Per-pass twiddles of the rolled radix-8 passes.  The pass of stage size
+// Ns = 2^lns multiplies input r of butterfly k = t mod Ns by W_L^{r k L/(8 Ns)},
+// r = 1..7; its table holds these at [7 k + r - 1].  Lanes with distinct k
+// then read 16-byte entries 7 apart (distinct bank groups), lanes with equal
+// k one address.  The tables of the passes follow each other, first pass
+// excluded (no twiddles at Ns = 1): 7 (Ns_1 + Ns_2 + ...) < L entries.
+// Entries i0, i0 + di, ... are filled (one call per thread of a block, or a
+// single host call with i0 = 0, di = 1).
+template <typename C, int L>
+__host__ __device__ __forceinline__ void fill_pass_twiddles(C* dst, const C* __restrict__ tw4096, int i0, int di) {
+  constexpr int M = log2_len(L);
+  int off = 0;
+  for (int lns = first_pass_lns(L); lns < M; lns += 3) {
+    const int n = 7 << lns;
+    for (int i = i0; i < n; i += di) {
+      const int k = i / 7, r = i - 7 * k + 1;
+      dst[off + i] = tw4096[(r * (k << (M - lns - 3))) * (kTwiddleN / L)];
+    }
+    off += n;
+  }
+}
+
 // A radix-8 Stockham pass with the stage size Ns = 2^lns a run-time value
 // (shifts in place of the divisions by Ns), for the rolled pass loop of the
 // double-float transforms; same data movement as rf_pass<C, L, 8, DIR> at
-// Ns > 1.
+// Ns > 1, twiddles from this pass's table twp of fill_pass_twiddles.
 template <typename C, int L, int DIR>
-__host__ __device__ __forceinline__ void rf_pass8_rt(C v[8], int t, int lns, const C* __restrict__ tw, int tws,
-                                                     int dst[8]) {
-  constexpr int LOGL = (L == 8) ? 3 : (L == 16) ? 4 : (L == 32) ? 5 : (L == 64) ? 6 : (L == 128) ? 7
-                     : (L == 256) ? 8 : (L == 512) ? 9 : (L == 1024) ? 10 : 11;
+__host__ __device__ __forceinline__ void rf_pass8_rt(C v[8], int t, int lns, const C* __restrict__ twp, int dst[8]) {
   const int k = t & ((1 << lns) - 1);
-  const int step = k << (LOGL - lns - 3);         // twiddle W_L^{r*step}
   C x[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) x[r] = v[r];
 #pragma unroll
-  for (int r = 1; r < 8; ++r) x[r] = cmul(x[r], rf_tw<C, DIR>(tw, r * step, tws));
+  for (int r = 1; r < 8; ++r) x[r] = cmul(x[r], rf_tw<C, DIR>(twp, 7 * k + r - 1, 1));
   rf_dft8<C, DIR>(x);
   const int base = ((t >> lns) << (lns + 3)) + k;
 #pragma unroll
@@ -213,22 +240,24 @@ __device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int
     // in a rolled loop (a double-float butterfly is ~10x the code of an FP32
     // one, and the unrolled passes overflowed the instruction cache)
 #pragma unroll
-    for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, R0, DIR>(v[c], t, 1, tw, tws, dst);
-    int lns = R0 == 2 ? 1 : (R0 == 4 ? 2 : 3);
+    for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, R0, DIR>(v[c], t, 1, tw, tws, dst);   // Ns = 1: no twiddles
+    int lns = first_pass_lns(L);
+    const C* twp = tw;
 #pragma unroll 1
     for (int p = 1; p < NPASS; ++p) {
 #pragma unroll
       for (int c = 0; c < NCOMP; ++c)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) sm[(c * sstride + row_pad(L, dst[s])) * estride] = v[c][s];
+        for (int s = 0; s < 8; ++s) sm[(c * sstride + seq_pad<C>(L, dst[s])) * estride] = v[c][s];
       sync();
 #pragma unroll
       for (int c = 0; c < NCOMP; ++c)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) v[c][s] = sm[(c * sstride + row_pad(L, t + TT * s)) * estride];
+        for (int s = 0; s < 8; ++s) v[c][s] = sm[(c * sstride + seq_pad<C>(L, t + TT * s)) * estride];
       sync();
 #pragma unroll
-      for (int c = 0; c < NCOMP; ++c) rf_pass8_rt<C, L, DIR>(v[c], t, lns, tw, tws, dst);
+      for (int c = 0; c < NCOMP; ++c) rf_pass8_rt<C, L, DIR>(v[c], t, lns, twp, dst);
+      twp += 7 << lns;
       lns += 3;
     }
     return;
@@ -241,12 +270,12 @@ __device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int
 #pragma unroll
       for (int c = 0; c < NCOMP; ++c)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) sm[(c * sstride + row_pad(L, dst[s])) * estride] = v[c][s];
+        for (int s = 0; s < 8; ++s) sm[(c * sstride + seq_pad<C>(L, dst[s])) * estride] = v[c][s];
       sync();
 #pragma unroll
       for (int c = 0; c < NCOMP; ++c)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) v[c][s] = sm[(c * sstride + row_pad(L, t + TT * s)) * estride];
+        for (int s = 0; s < 8; ++s) v[c][s] = sm[(c * sstride + seq_pad<C>(L, t + TT * s)) * estride];
       sync();
     }
     if (p == 0 && R0 == 2) {

@@ -42,16 +42,24 @@ constexpr int log2i(int L) { return L <= 1 ? 0 : 1 + log2i(L / 2); }
 // Runs one pass of radix RP over all threads; returns false if the
 // destinations are not a permutation of [0, L).
 // (the double-float transforms run their radix-8 passes after the first
-// through rf_pass8_rt, with the stage size as a run-time shift)
+// through rf_pass8_rt, with the stage size as a run-time shift and the
+// twiddles from the per-pass table of fill_pass_twiddles)
 template <typename C, int L, int W, int RP, int DIR>
 static bool pass(std::vector<C>& v, std::vector<int>& dst, int Ns, const C* tw, const C* tw4) {
   constexpr int TT = L / W;
   int lns = 0;
   while ((1 << lns) < Ns) ++lns;
+  std::vector<C> ptab;
+  int poff = 0;
+  if constexpr (W == 8 && RP == 8 && RolledPasses<C>::value) {
+    ptab.resize(L);
+    fill_pass_twiddles<C, L>(ptab.data(), tw, 0, 1);
+    for (int l = first_pass_lns(L); l < lns; l += 3) poff += 7 << l;
+  }
   for (int t = 0; t < TT; ++t) {
     if constexpr (W == 8 && RP == 8 && RolledPasses<C>::value) {
       if (Ns > 1) {
-        rf_pass8_rt<C, L, DIR>(&v[t * W], t, lns, tw, kTwiddleN / L, &dst[t * W]);
+        rf_pass8_rt<C, L, DIR>(&v[t * W], t, lns, ptab.data() + poff, &dst[t * W]);
         continue;
       }
     }
