@@ -124,11 +124,22 @@ __device__ __forceinline__ void zconv(const cplx<T>* src, int cstr, int zstr, in
   }
 }
 
+// Element i of a 3D column sequence sits at row_pad(L, i) (the exchange
+// layout of both register FFTs).
+template <int L>
+struct SeqMap {
+  __device__ __forceinline__ int operator()(int i) const { return row_pad(L, i); }
+};
+
 template <typename T, int L, int PZ>
 __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I, const ColTile& tile,
                                            cplx<T>* smem) {
   using C = cplx<T>;
-  constexpr int TT = L / 8;
+  // y transforms: 16 elements per lane at Py = 1024 in FP32 (radix-16
+  // passes: two exchanges instead of three, and twice the sequences per
+  // round), 8 elsewhere
+  constexpr int W = (sizeof(T) == 4 && L == 1024) ? 16 : 8;
+  constexpr int TT = L / W;
   constexpr int NG = kColThreads / TT;             // FFT groups working at once
   constexpr int GSC = cols3_stride(L);
   constexpr int NZM = PZ / 2;
@@ -157,16 +168,17 @@ __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I
     const int q = q0 + gid;
     if (q < nseq) {
       C* grp = smem + (long long)q * GSC;
-      C v[8];
+      C v[W];
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
+      for (int s = 0; s < W; ++s) {
         const int y = t + TT * s;
-        v[s] = (s < 4 && y < ny) ? grp[row_pad(L, y)] : mk<C>((T)0, (T)0);   // zero padding: s >= 4
+        v[s] = (s < W / 2 && y < ny) ? grp[row_pad(L, y)] : mk<C>((T)0, (T)0);   // zero padding: s >= W/2
       }
       gs();
-      fft1<C, L, -1>(v, grp, 1, t, tw1, 1, gs);
+      if constexpr (W == 16) regfft16<C, L, -1>(v, grp, t, tw1, 1, nullptr, SeqMap<L>{}, gs);
+      else fft1<C, L, -1>(v, grp, 1, t, tw1, 1, gs);
 #pragma unroll
-      for (int s = 0; s < 8; ++s) grp[row_pad(L, t + TT * s)] = v[s];
+      for (int s = 0; s < W; ++s) grp[row_pad(L, t + TT * s)] = v[s];
     }
   }
   __syncthreads();
@@ -248,15 +260,16 @@ __device__ __forceinline__ void cols3_body(const ColArgs<T>& a, const DevInst& I
     const int q = q0 + gid;
     if (q < nseq) {
       C* grp = smem + (long long)q * GSC;
-      C v[8];
+      C v[W];
 #pragma unroll
-      for (int s = 0; s < 8; ++s) v[s] = grp[row_pad(L, t + TT * s)];
+      for (int s = 0; s < W; ++s) v[s] = grp[row_pad(L, t + TT * s)];
       gs();
-      fft1<C, L, 1>(v, grp, 1, t, tw1, 1, gs);
+      if constexpr (W == 16) regfft16<C, L, 1>(v, grp, t, tw1, 1, nullptr, SeqMap<L>{}, gs);
+      else fft1<C, L, 1>(v, grp, 1, t, tw1, 1, gs);
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
+      for (int s = 0; s < W; ++s) {
         const int y = t + TT * s;
-        if (s < 4 && y < ny) grp[row_pad(L, y)] = v[s];
+        if (s < W / 2 && y < ny) grp[row_pad(L, y)] = v[s];
       }
     }
   }
