@@ -327,15 +327,18 @@ def run_reference(args):
 
 # FP32 operations of the double-float (compensated) arithmetic, as the kernels
 # implement it: a complex add 16, a complex product 32, a real product 5.
-def _df_fft_ops(L):
+def _df_fft_ops(L, half_in=False):
     """FP32 operations of one double-float register FFT of length L
     (8-element lanes: a first pass of radix R0 without twiddles, then radix-8
-    passes with 7 twiddle products per butterfly)."""
+    passes with 7 twiddle products per butterfly).  half_in: the forward
+    transform of zero-padded data, whose first pass leaves out the zero upper
+    half of every butterfly's inputs (radix 2: a copy; radix 4: 4 complex sums
+    of 8; radix 8: 16 of 24)."""
     m = int(np.log2(L))
     r0 = 2 if m % 3 == 1 else (4 if m % 3 == 2 else 8)
     npass = m // 3 if m % 3 == 0 else m // 3 + 1
-    dft = {2: 32, 4: 128, 8: 436}
-    return (L // r0) * dft[r0] + (npass - 1) * (L // 8) * (dft[8] + 7 * 32)
+    dft = {2: 0, 4: 64, 8: 308} if half_in else {2: 32, 4: 128, 8: 436}
+    return (L // r0) * dft[r0] + (npass - 1) * (L // 8) * (436 + 7 * 32)
 
 
 def df_ops_per_launch(insts, family):
@@ -345,8 +348,9 @@ def df_ops_per_launch(insts, family):
     and pack (90)), family 4 (one row transform of the split adjoint stage,
     inverse or forward: half of that), family 3 (column pass: forward and
     inverse FFT of length Py per column kx < Px/2 and component, and the
-    tensor product, about 27 per point).  Node-phase arithmetic is not
-    counted."""
+    tensor product, about 27 per point).  The forward transforms take
+    zero-padded inputs (half-input first pass).  Node-phase arithmetic is
+    not counted."""
     tot = 0.0
     for i in insts:
         p = i.problem
@@ -354,11 +358,11 @@ def df_ops_per_launch(insts, family):
         Py = max(8, 1 << (2 * p.ny - 1).bit_length())
         Lx = Px // 2
         if family == 2:
-            tot += p.ny * p.nz * 3 * (2 * _df_fft_ops(Lx) + Lx * (80 + 90))
+            tot += p.ny * p.nz * 3 * (_df_fft_ops(Lx) + _df_fft_ops(Lx, True) + Lx * (80 + 90))
         elif family == 4:
-            tot += p.ny * p.nz * 3 * (_df_fft_ops(Lx) + Lx * 85)
+            tot += p.ny * p.nz * 3 * ((_df_fft_ops(Lx) + _df_fft_ops(Lx, True)) / 2 + Lx * 85)
         else:
-            tot += Lx * 3 * (2 * _df_fft_ops(Py) + Py * 27)
+            tot += Lx * 3 * (_df_fft_ops(Py) + _df_fft_ops(Py, True) + Py * 27)
     return tot
 
 

@@ -128,11 +128,12 @@ __device__ __forceinline__ C pack_one(C zk, C zm_conj, int kk, const C* __restri
 }
 
 // One component's FFT: v[s] holds element t + (L/8)s of the sequence whose
-// element i is exchanged through grp[pad(i) * estride].
-template <typename C, int L, int DIR>
+// element i is exchanged through grp[pad(i) * estride].  HALF_IN: v[s] == 0
+// for s >= 4 (zero-padded input; see regfft).
+template <typename C, int L, int DIR, bool HALF_IN = false>
 __device__ __forceinline__ void fft1(C (&v)[8], C* grp, int estride, int t, const C* __restrict__ tw, int tws,
                                      GroupSync sync) {
-  regfft<C, L, DIR, 1>(*reinterpret_cast<C(*)[1][8]>(&v), grp, 0, estride, t, tw, tws, sync);
+  regfft<C, L, DIR, 1, HALF_IN>(*reinterpret_cast<C(*)[1][8]>(&v), grp, 0, estride, t, tw, tws, sync);
 }
 
 // Row-kernel group stride: the padded length rounded up to even, so that
@@ -196,7 +197,7 @@ __device__ __forceinline__ void row_forward_comp(cplx<T>* grp, int npairs, cplx<
     v[s] = (s < 4 && j < npairs) ? grp[seq_pad<C>(L, j)] : mk<C>((T)0, (T)0);
   }
   gs();
-  fft1<C, L, -1>(v, grp, 1, t, row_fft_tw(tw2, L), 2, gs);
+  fft1<C, L, -1, true>(v, grp, 1, t, row_fft_tw(tw2, L), 2, gs);
 #pragma unroll
   for (int s = 0; s < 8; ++s) grp[seq_pad<C>(L, t + TT * s)] = v[s];
   gs();
@@ -309,7 +310,7 @@ __device__ __forceinline__ void cols_body(const ColArgs<T>& a, const DevInst& I,
     v[s] = (s < 4 && active && y < ny) ? grp[rf_pad(y)] : mk<C>((T)0, (T)0);
   }
   gs();
-  fft1<C, L, -1>(v, grp, 1, t, tw1, 1, gs);
+  fft1<C, L, -1, true>(v, grp, 1, t, tw1, 1, gs);
   // publish every component at every ky for the 3x3 product
 #pragma unroll
   for (int s = 0; s < 8; ++s) grp[rf_pad(t + TT * s)] = v[s];

@@ -76,6 +76,77 @@ __host__ __device__ __forceinline__ void rf_dft8(C x[8]) {
   x[7] = csub(e3, o3);
 }
 
+// DFTs of 4 and 8 points whose upper half of inputs is zero (x2 = x3 = 0,
+// x4..x7 = 0): the first pass of a forward transform of zero-padded data.
+// Same values as rf_dft4 / rf_dft8 on those inputs, up to the sign of zero
+// results; the additions of the zeros are left out.  The double-float passes
+// need this spelled out: a compensated sum with a zero operand is not
+// something the compiler may fold (it could change the sign of a zero).
+template <typename C, int DIR>
+__host__ __device__ __forceinline__ void rf_dft4_half(C& x0, C& x1, C& x2, C& x3) {
+  const C a = x0, c = x1;
+  const C d = (DIR < 0) ? mul_mi(c) : mul_pi(c);
+  x0 = cadd(a, c);
+  x2 = csub(a, c);
+  x1 = cadd(a, d);
+  x3 = csub(a, d);
+}
+template <typename C, int DIR>
+__host__ __device__ __forceinline__ void rf_dft8_half(C x[8]) {
+  using R = decltype(C::x);
+  const R h = (R)0.70710678118654752440;
+  C e0 = x[0], e1 = x[2], e2, e3;
+  C o0 = x[1], o1 = x[3], o2, o3;
+  rf_dft4_half<C, DIR>(e0, e1, e2, e3);
+  rf_dft4_half<C, DIR>(o0, o1, o2, o3);
+  if (DIR < 0) {
+    o1 = mk<C>(h * (o1.x + o1.y), h * (o1.y - o1.x));
+    o2 = mul_mi(o2);
+    o3 = mk<C>(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+  } else {
+    o1 = mk<C>(h * (o1.x - o1.y), h * (o1.x + o1.y));
+    o2 = mul_pi(o2);
+    o3 = mk<C>(-h * (o3.x + o3.y), h * (o3.x - o3.y));
+  }
+  x[0] = cadd(e0, o0);
+  x[4] = csub(e0, o0);
+  x[1] = cadd(e1, o1);
+  x[5] = csub(e1, o1);
+  x[2] = cadd(e2, o2);
+  x[6] = csub(e2, o2);
+  x[3] = cadd(e3, o3);
+  x[7] = csub(e3, o3);
+}
+
+// First pass (stage size 1, no twiddles) of radix RP when the inputs of
+// slots s >= 4 are zero: butterfly b takes v[b + r*(8/RP)], which is zero
+// exactly for r >= RP/2.  Same outputs and destinations as
+// rf_pass<C, L, RP, DIR>(v, t, 1, ...) on such inputs.
+template <typename C, int L, int RP, int DIR>
+__host__ __device__ __forceinline__ void rf_pass_half(C v[8], int t, int dst[8]) {
+  constexpr int TT = L / 8;
+  constexpr int NB = 8 / RP;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = t + TT * b;
+    C x[RP];
+#pragma unroll
+    for (int r = 0; r < RP / 2; ++r) x[r] = v[b + r * NB];
+    if constexpr (RP == 2) {
+      x[1] = x[0];
+    } else if constexpr (RP == 4) {
+      rf_dft4_half<C, DIR>(x[0], x[1], x[2], x[3]);
+    } else {
+      rf_dft8_half<C, DIR>(x);
+    }
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+      v[b + r * NB] = x[r];
+      dst[b + r * NB] = j * RP + r;
+    }
+  }
+}
+
 // One Stockham pass of radix RP on the eight registers of thread t.
 // Butterfly b of the thread is j = t + TT*b (b < 8/RP); its inputs are
 // v[b + r*(8/RP)], r < RP.  Returns the outputs in the same slots; `dst`
@@ -225,7 +296,9 @@ __device__ __forceinline__ GroupSync group_sync(int TT) {
 // contiguous, estride = G interleaves G groups element by element (lanes of
 // consecutive groups then touch consecutive banks).  Every thread of the
 // block must call it (it synchronises the block between passes).
-template <typename C, int L, int DIR, int NCOMP>
+// HALF_IN: the caller guarantees v[c][s] == 0 for s >= 4 (the upper half of a
+// zero-padded sequence); the double-float first pass then skips the zeros.
+template <typename C, int L, int DIR, int NCOMP, bool HALF_IN = false>
 __device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int estride, int t,
                                        const C* __restrict__ tw, int tws, GroupSync sync = GroupSync{0, 0}) {
   constexpr int M = (L == 8) ? 3 : (L == 16) ? 4 : (L == 32) ? 5 : (L == 64) ? 6 : (L == 128) ? 7
@@ -240,7 +313,10 @@ __device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int
     // in a rolled loop (a double-float butterfly is ~10x the code of an FP32
     // one, and the unrolled passes overflowed the instruction cache)
 #pragma unroll
-    for (int c = 0; c < NCOMP; ++c) rf_pass<C, L, R0, DIR>(v[c], t, 1, tw, tws, dst);   // Ns = 1: no twiddles
+    for (int c = 0; c < NCOMP; ++c) {   // Ns = 1: no twiddles
+      if constexpr (HALF_IN) rf_pass_half<C, L, R0, DIR>(v[c], t, dst);
+      else rf_pass<C, L, R0, DIR>(v[c], t, 1, tw, tws, dst);
+    }
     int lns = first_pass_lns(L);
     const C* twp = tw;
 #pragma unroll 1

@@ -27,16 +27,24 @@ def cases(tmp_path_factory):
                     os.path.join(ROOT, "tests", "host_fft_passes.cu"), "-o", str(exe)],
                    check=True, capture_output=True, timeout=600)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=600).stdout
-    rows = []
+    rows, half = [], []
     for line in out.split("\n"):
-        if line.strip():
+        if line.startswith("half "):
+            _, prec, L, d, ok = line.split()
+            half.append((prec, int(L), int(d), int(ok)))
+        elif line.strip():
             prec, w, L, d, t4, err, perm = line.split()
             rows.append((prec, int(w), int(L), int(d), int(t4), float(err), int(perm)))
-    return rows
+    return rows, half
 
 
-def test_every_length_and_width_is_covered(cases):
-    got = {(p, w, L, d) for p, w, L, d, *_ in cases}
+@pytest.fixture(scope="module")
+def passes(cases):
+    return cases[0]
+
+
+def test_every_length_and_width_is_covered(passes):
+    got = {(p, w, L, d) for p, w, L, d, *_ in passes}
     for p in ("f32", "f64", "df"):
         for d in (-1, 1):
             for k in range(3, 12):
@@ -45,13 +53,24 @@ def test_every_length_and_width_is_covered(cases):
                 assert (p, 16, 2 ** k, d) in got
 
 
-def test_every_pass_scatters_to_a_permutation(cases):
-    assert all(c[6] == 1 for c in cases)
+def test_every_pass_scatters_to_a_permutation(passes):
+    assert all(c[6] == 1 for c in passes)
 
 
-def test_passes_compute_the_dft(cases):
+def test_passes_compute_the_dft(passes):
     # FP32: a few ulp per pass (the twiddle powers are formed by products);
     # FP64: rounding only; double-float: a few 2^-48 = 3.6e-15 per pass
     bound = {"f32": 5e-7, "f64": 1e-15, "df": 2e-14}
-    for prec, w, L, d, t4, err, _ in cases:
+    for prec, w, L, d, t4, err, _ in passes:
         assert err < bound[prec], (prec, w, L, d, t4, err)
+
+
+def test_half_input_first_pass_equals_the_full_pass(cases):
+    """The forward transforms of zero-padded data (column pass, row
+    transforms) run their double-float first pass without the zero upper
+    half of the inputs; every length and precision must give the full
+    pass's values and destinations."""
+    half = cases[1]
+    assert {(p, L) for p, L, d, _ in half if d == -1} == {(p, 2 ** k) for p in ("f32", "f64", "df")
+                                                         for k in range(3, 12)}
+    assert all(ok == 1 for *_, ok in half), [h for h in half if h[3] != 1]
