@@ -47,7 +47,8 @@ __host__ __device__ __forceinline__ void rf_dft4(C& x0, C& x1, C& x2, C& x3) {
   x3 = csub(b, d);
 }
 
-// 8-point DFT in place: x[k] <- sum_j x[j] W_8^{jk}
+// 8-point DFT in place: x[k] <- sum_j x[j] W_8^{jk} (the four sums, then
+// the four differences: in the double-float passes this order spilled less)
 template <typename C, int DIR>
 __host__ __device__ __forceinline__ void rf_dft8(C x[8]) {
   using R = decltype(C::x);
@@ -67,12 +68,12 @@ __host__ __device__ __forceinline__ void rf_dft8(C x[8]) {
     o3 = mk<C>(-h * (o3.x + o3.y), h * (o3.x - o3.y));     // (-1 + i)/sqrt2
   }
   x[0] = cadd(e0, o0);
-  x[4] = csub(e0, o0);
   x[1] = cadd(e1, o1);
-  x[5] = csub(e1, o1);
   x[2] = cadd(e2, o2);
-  x[6] = csub(e2, o2);
   x[3] = cadd(e3, o3);
+  x[4] = csub(e0, o0);
+  x[5] = csub(e1, o1);
+  x[6] = csub(e2, o2);
   x[7] = csub(e3, o3);
 }
 
@@ -252,6 +253,21 @@ __host__ __device__ __forceinline__ void rf_pass8_rt(C v[8], int t, int lns, con
   }
 }
 
+// Where slot s of thread t goes after pass p - 1 of a rolled transform: after
+// the first pass (radix R0 = 8 / NB, stage size 1) butterfly t + TT (s mod NB)
+// writes its output s / NB to (t + TT (s mod NB)) R0 + s / NB; after a rolled
+// radix-8 pass of stage size 2^pl butterfly t writes output s to
+// rf_pass8_rt's destination.  pl is the stage size's log2 of pass p - 1 for
+// p >= 2 (unused for p == 1).
+template <int L>
+__host__ __device__ __forceinline__ int rolled_exchange_dst(int p, int pl, int t, int s) {
+  constexpr int TT = L / 8;
+  constexpr int R0 = 1 << first_pass_lns(L);
+  constexpr int NB0 = 8 / R0;
+  if (p == 1) return (t + TT * (s % NB0)) * R0 + s / NB0;
+  return (((t >> pl) << (pl + 3)) | (t & ((1 << pl) - 1))) + (s << pl);
+}
+
 template <typename C> struct RolledPasses { static constexpr bool value = false; };
 template <> struct RolledPasses<dcplx> { static constexpr bool value = true; };
 
@@ -317,6 +333,9 @@ __device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int
       if constexpr (HALF_IN) rf_pass_half<C, L, R0, DIR>(v[c], t, dst);
       else rf_pass<C, L, R0, DIR>(v[c], t, 1, tw, tws, dst);
     }
+    // The exchange recomputes each slot's write index from t
+    // (rolled_exchange_dst) rather than carrying the eight indices across the
+    // pass in registers.
     int lns = first_pass_lns(L);
     const C* twp = tw;
 #pragma unroll 1
@@ -324,7 +343,8 @@ __device__ __forceinline__ void regfft(C (&v)[NCOMP][8], C* sm, int sstride, int
 #pragma unroll
       for (int c = 0; c < NCOMP; ++c)
 #pragma unroll
-        for (int s = 0; s < 8; ++s) sm[(c * sstride + seq_pad<C>(L, dst[s])) * estride] = v[c][s];
+        for (int s = 0; s < 8; ++s)
+          sm[(c * sstride + seq_pad<C>(L, rolled_exchange_dst<L>(p, lns - 3, t, s))) * estride] = v[c][s];
       sync();
 #pragma unroll
       for (int c = 0; c < NCOMP; ++c)

@@ -72,6 +72,14 @@ static bool pass(std::vector<C>& v, std::vector<int>& dst, int Ns, const C* tw, 
   for (int i = 0; i < L; ++i) {
     if (dst[i] < 0 || dst[i] >= L || seen[dst[i]]++) return false;
   }
+  // the double-float transforms recompute these destinations at the next
+  // exchange (rolled_exchange_dst) instead of keeping them
+  if constexpr (W == 8) {
+    const int p = Ns == 1 ? 1 : 2;
+    for (int t = 0; t < TT; ++t)
+      for (int s = 0; s < W; ++s)
+        if (rolled_exchange_dst<L>(p, lns, t, s) != dst[t * W + s]) return false;
+  }
   return true;
 }
 
