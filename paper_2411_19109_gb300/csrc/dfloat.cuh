@@ -33,6 +33,17 @@
 
 #include <cuda_runtime.h>
 
+// A host build that defines LLG_HOST_COUNT_OPS (and the counter) counts
+// every FP32 operation of the double-float arithmetic; a test compares the
+// count of whole transforms with the benchmark's operation model.  Device
+// code and the library's host code are unaffected.
+#if defined(LLG_HOST_COUNT_OPS) && !defined(__CUDA_ARCH__)
+extern unsigned long long llg_host_fp32_ops;
+#define LLG_HOST_OP() (++llg_host_fp32_ops)
+#else
+#define LLG_HOST_OP() ((void)0)
+#endif
+
 namespace llg {
 
 namespace dw {
@@ -41,6 +52,7 @@ __host__ __device__ __forceinline__ float add(float a, float b) {
 #ifdef __CUDA_ARCH__
   return __fadd_rn(a, b);
 #else
+  LLG_HOST_OP();
   return a + b;
 #endif
 }
@@ -48,6 +60,7 @@ __host__ __device__ __forceinline__ float sub(float a, float b) {
 #ifdef __CUDA_ARCH__
   return __fsub_rn(a, b);
 #else
+  LLG_HOST_OP();
   return a - b;
 #endif
 }
@@ -55,6 +68,7 @@ __host__ __device__ __forceinline__ float mul(float a, float b) {
 #ifdef __CUDA_ARCH__
   return __fmul_rn(a, b);
 #else
+  LLG_HOST_OP();
   return a * b;
 #endif
 }
@@ -62,6 +76,7 @@ __host__ __device__ __forceinline__ float fma(float a, float b, float c) {
 #ifdef __CUDA_ARCH__
   return __fmaf_rn(a, b, c);
 #else
+  LLG_HOST_OP();
   return std::fma(a, b, c);
 #endif
 }

@@ -16,6 +16,10 @@
 
 using namespace llg;
 
+// FP32 operations of the double-float arithmetic (dfloat.cuh counts them in
+// this host build, compiled with LLG_HOST_COUNT_OPS)
+unsigned long long llg_host_fp32_ops = 0;
+
 // value of a real part as long double, for the comparison
 static long double to_ld(float v) { return v; }
 static long double to_ld(double v) { return v; }
@@ -234,7 +238,63 @@ static void half_all(const char* name) {
   half_check<C, 512, +1>(name);
 }
 
+// FP32 operations of one whole double-float transform of length L in the
+// kernels' schedule (first pass -- in its half-input form when HALF, the
+// inputs of slots s >= 4 then zero -- and the rolled radix-8 passes; the
+// exchanges move data only).  Prints "ops <L> <DIR> <HALF> <count>".
+template <int L, int DIR, bool HALF>
+static void count_ops() {
+  using C = dcplx;
+  constexpr int W = 8, TT = L / 8, M = log2i(L);
+  constexpr int R0 = (M % 3 == 0) ? 8 : (1 << (M % 3));
+  constexpr int NPASS = (M % 3 == 0) ? M / 3 : M / 3 + 1;
+  const std::vector<C> tw = twiddles<C>();
+  unsigned long long seed = 0xD1B54A32D192ED03ULL ^ (unsigned long long)L;
+  std::vector<C> v(L);
+  for (int i = 0; i < L; ++i) {
+    const bool zero = HALF && i / TT >= 4;
+    v[(i % TT) * W + i / TT].x = dfloat(zero ? 0.0 : lcg_unit(seed));
+    v[(i % TT) * W + i / TT].y = dfloat(zero ? 0.0 : lcg_unit(seed));
+  }
+  std::vector<int> dst(L);
+  llg_host_fp32_ops = 0;
+  int Ns = 1;
+  for (int p = 0; p < NPASS; ++p) {
+    if (p > 0) {
+      std::vector<C> sm(L);
+      for (int i = 0; i < L; ++i) sm[dst[i]] = v[i];
+      for (int t = 0; t < TT; ++t)
+        for (int s = 0; s < W; ++s) v[t * W + s] = sm[t + TT * s];
+      pass<C, L, W, 8, DIR>(v, dst, Ns, tw.data(), nullptr);
+      Ns *= 8;
+    } else {
+      for (int t = 0; t < TT; ++t) {
+        if constexpr (HALF) rf_pass_half<C, L, R0, DIR>(&v[t * W], t, &dst[t * W]);
+        else rf_pass<C, L, R0, DIR>(&v[t * W], t, 1, tw.data(), kTwiddleN / L, &dst[t * W]);
+      }
+      Ns *= R0;
+    }
+  }
+  std::printf("ops %d %d %d %llu\n", L, DIR, HALF ? 1 : 0, llg_host_fp32_ops);
+}
+
+template <int L>
+static void count_all() {
+  count_ops<L, -1, false>();
+  count_ops<L, -1, true>();
+  count_ops<L, +1, false>();
+}
+
 int main() {
+  count_all<8>();
+  count_all<16>();
+  count_all<32>();
+  count_all<64>();
+  count_all<128>();
+  count_all<256>();
+  count_all<512>();
+  count_all<1024>();
+  count_all<2048>();
   half_all<float2>("f32");
   half_all<double2>("f64");
   half_all<dcplx>("df");

@@ -23,19 +23,22 @@ def cases(tmp_path_factory):
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not found")
     exe = tmp_path_factory.mktemp("fft") / "fft_passes"
-    subprocess.run([nvcc, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_2411_19109_gb300", "csrc"),
+    subprocess.run([nvcc, "-std=c++17", "-O1", "-DLLG_HOST_COUNT_OPS", "-I", os.path.join(ROOT, "paper_2411_19109_gb300", "csrc"),
                     os.path.join(ROOT, "tests", "host_fft_passes.cu"), "-o", str(exe)],
                    check=True, capture_output=True, timeout=600)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=600).stdout
-    rows, half = [], []
+    rows, half, ops = [], [], []
     for line in out.split("\n"):
         if line.startswith("half "):
             _, prec, L, d, ok = line.split()
             half.append((prec, int(L), int(d), int(ok)))
+        elif line.startswith("ops "):
+            _, L, d, h, n = line.split()
+            ops.append((int(L), int(d), int(h), int(n)))
         elif line.strip():
             prec, w, L, d, t4, err, perm = line.split()
             rows.append((prec, int(w), int(L), int(d), int(t4), float(err), int(perm)))
-    return rows, half
+    return rows, half, ops
 
 
 @pytest.fixture(scope="module")
@@ -74,3 +77,16 @@ def test_half_input_first_pass_equals_the_full_pass(cases):
     assert {(p, L) for p, L, d, _ in half if d == -1} == {(p, 2 ** k) for p in ("f32", "f64", "df")
                                                          for k in range(3, 12)}
     assert all(ok == 1 for *_, ok in half), [h for h in half if h[3] != 1]
+
+
+def test_operation_model_counts_the_transforms(cases):
+    """The ALU roofline of the double-float kernels divides an operation
+    model (bench._df_fft_ops) by the measured time; the host build counts
+    the FP32 operations the transform code performs (every compensated sum,
+    product and fused multiply-add of dfloat.cuh), which must equal the model
+    at every length, forward (full and half-input first pass) and inverse."""
+    import bench
+    ops = cases[2]
+    assert {L for L, *_ in ops} == {2 ** k for k in range(3, 12)}
+    for L, d, h, n in ops:
+        assert n == bench._df_fft_ops(L, half_in=bool(h)), (L, d, h, n, bench._df_fft_ops(L, half_in=bool(h)))
